@@ -1,0 +1,222 @@
+"""TEST INFRASTRUCTURE ONLY: Python face of the FP64 CPU oracle.
+
+Only the test suite, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this module.  It shares no code with the GPU library and never
+imports it.
+
+Contents, each written from the paper (Schwarz & Kjelgaard Mikkelsen 2019):
+  * ``trsyl``      -- Algorithm 2 (robust, global scale) / Algorithm 1 (plain) in C
+                      (``sylv_oracle.c``), with op(A)/op(B) transposes reduced to
+                      the untransposed problem by index reversal.
+  * ``small_solve``, ``protect_update``, ``protect_division`` -- the Sec. 2.1
+                      building blocks, exposed for the pins.
+  * ``kron_solve`` -- the textbook Kronecker form of eq. (2),
+                      (I_n (x) A + B^T (x) I_m) vec(X) = vec(C), by dense LU.
+  * ``residual``   -- the relative residual of eq. (9), evaluated with a common
+                      power-of-two shift so that tiny alpha or huge Y cannot
+                      under/overflow it.
+  * ``smin_of``    -- the pivot floor for near-singular small systems.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sylv_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+OMEGA = 2.0 ** 1020  # overflow threshold: 2^1020 leaves x16 headroom below the largest double
+EPS = 2.0 ** -52
+SMALLNUM = 2.0 ** -1022
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C source into ``oracle/_build/liboracle.so`` with gcc."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        # -ffp-contract=off: no fused multiply-add contraction, so x86 and Arm
+        # hosts round every product and sum the same way.
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        d, i, i64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64
+        pd = ctypes.POINTER(ctypes.c_double)
+        L.oracle_protect_update.argtypes = [d, d, d, d]
+        L.oracle_protect_update.restype = i
+        L.oracle_protect_division.argtypes = [d, d, d]
+        L.oracle_protect_division.restype = i
+        L.oracle_small_solve.argtypes = [i, i, pd, i, pd, i, pd, i, d, d, i, ctypes.POINTER(i)]
+        L.oracle_small_solve.restype = i
+        L.oracle_blocks.argtypes = [i64, pd, i64, ctypes.POINTER(i64)]
+        L.oracle_blocks.restype = i
+        L.oracle_trsyl.argtypes = [i64, i64, pd, i64, pd, i64, pd, i64, d, d, i,
+                                   ctypes.POINTER(i64), pd, ctypes.POINTER(i)]
+        L.oracle_trsyl.restype = i
+        _lib = L
+    return _lib
+
+
+def _pd(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _fortran(a) -> np.ndarray:
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def protect_update(c: float, t: float, x: float, omega: float = OMEGA) -> int:
+    """log2 of ProtectUpdate's power-of-two factor (Sec. 2.1)."""
+    return lib().oracle_protect_update(float(c), float(t), float(x), float(omega))
+
+
+def protect_division(b: float, d: float, omega: float = OMEGA) -> int:
+    """log2 of ProtectDivision's power-of-two factor (Sec. 2.1)."""
+    return lib().oracle_protect_division(float(b), float(d), float(omega))
+
+
+def quasi_tri(T) -> np.ndarray:
+    """The part of T the solver reads: upper triangle plus first subdiagonal."""
+    return np.triu(np.asarray(T, dtype=np.float64), -1)
+
+
+def smin_of(A, B) -> float:
+    """Pivot floor for the small solves: max(2^-52 * largest |entry| of A and B, 2^-1022)."""
+    amax = float(np.max(np.abs(quasi_tri(A)))) if np.size(A) else 0.0
+    bmax = float(np.max(np.abs(quasi_tri(B)))) if np.size(B) else 0.0
+    return max(EPS * max(amax, bmax), SMALLNUM)
+
+
+def small_solve(A11, B11, R, smin: float = SMALLNUM, omega: float = OMEGA, robust: bool = True):
+    """Robust <=2x2 by <=2x2 Sylvester solve A11 Z + Z B11 = beta R (Sec. 2.1).
+
+    Returns (Z, log2beta, info)."""
+    A11 = _fortran(A11)
+    B11 = _fortran(B11)
+    Z = np.array(R, dtype=np.float64, order="F", copy=True)
+    ma, nb = A11.shape[0], B11.shape[0]
+    lb = ctypes.c_int(0)
+    info = lib().oracle_small_solve(ma, nb, _pd(A11), max(ma, 1), _pd(B11), max(nb, 1), _pd(Z),
+                                    max(ma, 1), float(smin), float(omega), int(robust),
+                                    ctypes.byref(lb))
+    return Z, lb.value, info
+
+
+def blocks(T) -> list[int] | None:
+    """Start indices of the 1x1/2x2 diagonal blocks (plus the end), or None if T is not
+    quasi-triangular."""
+    T = _fortran(T)
+    n = T.shape[0]
+    starts = (ctypes.c_int64 * (n + 1))()
+    nb = lib().oracle_blocks(n, _pd(T), max(n, 1), starts)
+    if nb < 0:
+        return None
+    return [int(starts[i]) for i in range(nb + 1)]
+
+
+def anti_transpose(T) -> np.ndarray:
+    """J T^T J with J the reversal permutation; upper quasi-triangular if T is."""
+    return np.ascontiguousarray(np.flip(np.asarray(T).T, (0, 1)))
+
+
+def trsyl(A, B, C, robust: bool = True, transa: bool = False, transb: bool = False,
+          omega: float = OMEGA, smin: float | None = None):
+    """Solve op(A) Y + Y op(B) = alpha C with Algorithm 2 (robust) or Algorithm 1.
+
+    op(A)^T cases are reduced to the untransposed one: with J the reversal
+    permutation, A^T Y + Y B = C  <=>  (J A^T J)(J Y) + (J Y) B = J C, and likewise
+    on the right for B.
+
+    Returns a dict with Y, log2scale (alpha = 2^log2scale), info, peak (largest
+    magnitude Y ever held) and nan_seen.
+    """
+    A = quasi_tri(A)
+    B = quasi_tri(B)
+    C = np.asarray(C, dtype=np.float64)
+    m, n = C.shape
+    if smin is None:
+        smin = smin_of(A, B)
+    if transa:
+        A = anti_transpose(A)
+        C = np.flip(C, 0)
+    if transb:
+        B = anti_transpose(B)
+        C = np.flip(C, 1)
+    Af, Bf = _fortran(A), _fortran(B)
+    Y = np.array(C, dtype=np.float64, order="F", copy=True)
+    e = ctypes.c_int64(0)
+    peak = ctypes.c_double(0.0)
+    nan_seen = ctypes.c_int(0)
+    info = lib().oracle_trsyl(m, n, _pd(Af), max(m, 1), _pd(Bf), max(n, 1), _pd(Y), max(m, 1),
+                              float(smin), float(omega), int(robust), ctypes.byref(e),
+                              ctypes.byref(peak), ctypes.byref(nan_seen))
+    if transa:
+        Y = np.flip(Y, 0)
+    if transb:
+        Y = np.flip(Y, 1)
+    return {"Y": np.ascontiguousarray(Y), "log2scale": int(e.value), "info": int(info),
+            "peak": float(peak.value), "nan_seen": bool(nan_seen.value)}
+
+
+def kron_solve(A, B, C, transa: bool = False, transb: bool = False) -> np.ndarray:
+    """X with op(A) X + X op(B) = C from the Kronecker form of eq. (2):
+    (I_n (x) op(A) + op(B)^T (x) I_m) vec(X) = vec(C), vec stacking columns."""
+    A = quasi_tri(A)
+    B = quasi_tri(B)
+    if transa:
+        A = A.T
+    if transb:
+        B = B.T
+    C = np.asarray(C, dtype=np.float64)
+    m, n = C.shape
+    K = np.kron(np.eye(n), A) + np.kron(B.T, np.eye(m))
+    x = np.linalg.solve(K, C.reshape(-1, order="F"))
+    return x.reshape((m, n), order="F")
+
+
+def _shift_for(Y: np.ndarray) -> int:
+    amax = float(np.max(np.abs(Y))) if Y.size else 0.0
+    if amax == 0.0 or not np.isfinite(amax):
+        return 0
+    return -int(np.frexp(amax)[1])
+
+
+def residual(A, B, Y, C, log2scale: int, transa: bool = False, transb: bool = False) -> float:
+    """Eq. (9): ||alpha C - (op(A) Y + Y op(B))||_F / ((||A||_F + ||B||_F) ||Y||_F + ||alpha C||_F).
+
+    Numerator and denominator are both homogeneous of degree one in (Y, alpha C), so
+    both are multiplied by a common power of two 2^s that brings max|Y| to [1/2, 1);
+    alpha C is formed as ldexp(C, log2scale + s), which may underflow harmlessly."""
+    A = quasi_tri(A)
+    B = quasi_tri(B)
+    opA = A.T if transa else A
+    opB = B.T if transb else B
+    Y = np.asarray(Y, dtype=np.float64)
+    s = _shift_for(Y)
+    Ys = np.ldexp(Y, s)
+    aC = np.ldexp(np.asarray(C, dtype=np.float64), int(log2scale) + s)
+    R = aC - (opA @ Ys + Ys @ opB)
+    den = (np.linalg.norm(A) + np.linalg.norm(B)) * np.linalg.norm(Ys) + np.linalg.norm(aC)
+    if den == 0.0:
+        return 0.0 if np.linalg.norm(R) == 0.0 else float("inf")
+    return float(np.linalg.norm(R) / den)
+
+
+def scaled_solution(Y, log2scale: int) -> np.ndarray:
+    """Y / alpha = Y * 2^-log2scale (the solution X of the unscaled equation)."""
+    return np.ldexp(np.asarray(Y, dtype=np.float64), -int(log2scale))

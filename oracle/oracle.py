@@ -220,3 +220,45 @@ def residual(A, B, Y, C, log2scale: int, transa: bool = False, transb: bool = Fa
 def scaled_solution(Y, log2scale: int) -> np.ndarray:
     """Y / alpha = Y * 2^-log2scale (the solution X of the unscaled equation)."""
     return np.ldexp(np.asarray(Y, dtype=np.float64), -int(log2scale))
+
+
+def quasi_mask(T) -> np.ndarray:
+    """Entries the solver reads: upper triangle plus nonzero first-subdiagonal entries."""
+    T = np.asarray(T, dtype=np.float64)
+    n = T.shape[0]
+    r, c = np.indices((n, n))
+    return (r <= c) | ((r == c + 1) & (T != 0.0))
+
+
+def kron_grad(A, B, C, W, transa: bool = False, transb: bool = False):
+    """Gradients of L = sum(W * X), op(A) X + X op(B) = C, from the Kronecker form
+    K vec(X) = vec(C), K = I_n (x) op(A) + op(B)^T (x) I_m (eq. (2) vectorised).
+
+    dL/dvec(C) = K^-T vec(W) =: lam and dL/dK = -lam vec(X)^T.  op(A)[i,k] sits in K
+    at (i + m j, k + m j) for every j; op(B)[k,j] sits at (i + m j, i + m k) for every
+    i; the gradient of an entry is the sum of dL/dK over its positions.  Gradients
+    of A (B) are those of op(A) (op(B)), transposed back when op = T, and restricted
+    to the entries the solver reads.  Returns (dA, dB, dC, X)."""
+    A = quasi_tri(A)
+    B = quasi_tri(B)
+    opA = A.T if transa else A
+    opB = B.T if transb else B
+    C = np.asarray(C, dtype=np.float64)
+    m, n = C.shape
+    K = np.kron(np.eye(n), opA) + np.kron(opB.T, np.eye(m))
+    x = np.linalg.solve(K, C.reshape(-1, order="F"))
+    lam = np.linalg.solve(K.T, np.asarray(W, dtype=np.float64).reshape(-1, order="F"))
+    GK = -np.outer(lam, x)
+    dopA = np.zeros((m, m))
+    for i in range(m):
+        for k in range(m):
+            dopA[i, k] = sum(GK[i + m * j, k + m * j] for j in range(n))
+    dopB = np.zeros((n, n))
+    for k in range(n):
+        for j in range(n):
+            dopB[k, j] = sum(GK[i + m * j, i + m * k] for i in range(m))
+    dA = dopA.T if transa else dopA
+    dB = dopB.T if transb else dopB
+    dA = np.where(quasi_mask(A), dA, 0.0)
+    dB = np.where(quasi_mask(B), dB, 0.0)
+    return dA, dB, lam.reshape((m, n), order="F"), x.reshape((m, n), order="F")

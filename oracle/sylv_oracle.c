@@ -50,24 +50,26 @@ static int ceil_log2(double v) {
 /*
  * ProtectUpdate (Sec. 2.1): given upper bounds c = ||C||, t = ||A||, x = ||Y||, all
  * in [0, omega], return the base-2 exponent z <= 0 of a scale factor zeta = 2^z
- * such that zeta*(c + t*x) <= omega holds exactly; no intermediate overflows.
- *   x <= 1: t*x <= omega, so zeta = 1/2 gives (c + t*x)/2 <= omega.
- *   x >  1: zeta <= 1/(2x) gives zeta*c + zeta*t*x <= c/2 + t/2 <= omega.
- * The test for zeta = 1 compares against (omega - c) shrunk by 4 units of
- * roundoff, which covers the rounding of the product/quotient and of omega - c,
- * so a pass implies the exact inequality (also when t*x underflows: c == omega
- * then leaves no room and any nonzero t*x forces a scaling).
+ * with zeta*(c + t*x) <= omega exactly; no intermediate overflows.  zeta is the
+ * largest power of two the contract allows, up to rounding: 2^-ceil(log2 u) with
+ * u = (c + t*x)/omega, evaluated as c/omega + (t/omega)*x (omega is a power of two,
+ * so both quotients are exact and nothing overflows) and enlarged by 2^-50 to
+ * cover the two roundings.  The first test returns 1 when c + t*x <= omega holds
+ * with a margin of four units of roundoff (a pass implies the exact inequality;
+ * c == omega leaves no room for any nonzero t*x).
  */
 int oracle_protect_update(double c, double t, double x, double omega) {
   const double shrink = 1.0 - 0x1p-51;
   if (t == 0.0 || x == 0.0) return 0; /* no update term: c <= omega already */
   if (x <= 1.0) {
     double lim = (omega - c) * shrink;
-    if (lim <= 0.0 || t * x > lim) return -1; /* lim == 0 means c == omega */
-    return 0;
+    if (lim > 0.0 && t * x <= lim) return 0;
+  } else {
+    if (t <= ((omega - c) / x) * shrink) return 0;
   }
-  if (t > ((omega - c) / x) * shrink) return -(1 + ceil_log2(x));
-  return 0;
+  double u = c / omega + (t / omega) * x;
+  int z = -ceil_log2(u * (1.0 + 0x1p-50));
+  return z < 0 ? z : 0;
 }
 
 /*

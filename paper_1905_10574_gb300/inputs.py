@@ -113,3 +113,24 @@ def problem(m: int, n: int, seed: int, kind: str = "benign", upper: float = 1.0)
     B = quasi_triangular(n, 3 * seed + 1, kind, upper)
     C = rhs(m, n, 3 * seed + 2)
     return A, B, C
+
+
+# Named workloads (shapes and generator settings of the benchmark configurations).
+# "overflow_4000": robust vs non-robust FP64 at m = n = 4000.  The strictly-upper
+# scale 4.1 was chosen with the FP64 oracle (tests/golden/calibrate_overflow.py):
+# the unscaled growth log2 max|X| is ~353 bits at m = n = 1000 and grows linearly
+# with the order, ~1400 bits at 4000: past the binary64 range (1024), so the
+# non-robust solve overflows, while alpha = 2^-(growth - 1020) stays representable.
+WORKLOADS = {
+    "benign_256": dict(m=256, n=256, seed=0, kind="benign", upper=1.0, tile=64),
+    "overflow_4000": dict(m=4000, n=4000, seed=0, kind="growth", upper=4.1, tile=64),
+    "benign_8000": dict(m=8000, n=8000, seed=0, kind="benign", upper=1.0, tile=64),
+    "wellcond_8000": dict(m=8000, n=8000, seed=0, kind="wellcond", upper=1.0, tile=64),
+}
+
+
+def workload(name: str):
+    """(A, B, C, settings) of a named workload."""
+    w = WORKLOADS[name]
+    A, B, C = problem(w["m"], w["n"], w["seed"], kind=w["kind"], upper=w["upper"])
+    return A, B, C, w

@@ -27,8 +27,8 @@ def _edge_values():
 
 def test_protect_update_contract(orc):
     """Sec. 2.1: zeta in (0,1], a power of two, zeta*(c + t*x) <= Omega (checked in exact
-    rational arithmetic); no scaling when c + t*x <= Omega/2; never more than the
-    1/(4 max(1,x)) that the contract can require."""
+    rational arithmetic); no scaling when c + t*x <= Omega/2; and zeta is the largest
+    power of two allowed, up to rounding: 2*zeta*(c + t*x) > Omega*(1 - 2^-48)."""
     vals = _edge_values()
     rng = np.random.default_rng(1)
     triples = [(c, t, x) for c in vals[::3] for t in vals[::2] for x in vals]
@@ -44,7 +44,8 @@ def test_protect_update_contract(orc):
         assert zeta * tot <= Fraction(OMEGA), (c, t, x, z)
         if tot <= Fraction(OMEGA) / 2:
             assert z == 0, (c, t, x, z)
-        assert zeta >= Fraction(1, 4) / max(Fraction(1), Fraction(x)), (c, t, x, z)
+        if z < 0:
+            assert 2 * zeta * tot > Fraction(OMEGA) * (1 - Fraction(1, 2 ** 48)), (c, t, x, z)
 
 
 def test_protect_division_contract(orc):
@@ -266,3 +267,35 @@ def test_lyapunov_symmetry(orc):
     assert np.linalg.norm(Y - Y.T) <= 1e-13 * np.linalg.norm(Y)
     ref = orc.kron_solve(A, A, C, False, True)
     assert np.linalg.norm(Y - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("transa,transb", [(False, False), (True, False), (False, True)])
+def test_kron_grad_matches_finite_differences(orc, transa, transb):
+    """The Kronecker-form gradients against central differences of the Kronecker solve."""
+    m, n = 5, 4
+    A, B, C = inputs.problem(m, n, 21, kind="wellcond")
+    W = inputs.rhs(m, n, 99)
+    dA, dB, dC, _ = orc.kron_grad(A, B, C, W, transa, transb)
+    h = 1e-6
+
+    def loss(A_, B_, C_):
+        return float(np.sum(W * orc.kron_solve(A_, B_, C_, transa, transb)))
+
+    maskA, maskB = orc.quasi_mask(A), orc.quasi_mask(B)
+    for (i, j) in [(0, 0), (0, 3), (1, 2), (3, 4), (4, 4)]:
+        E = np.zeros_like(A)
+        E[i, j] = h
+        fd = (loss(A + E, B, C) - loss(A - E, B, C)) / (2 * h)
+        want = fd if maskA[i, j] else 0.0
+        assert abs(dA[i, j] - want) <= 1e-7 * max(1.0, abs(fd)), (i, j, dA[i, j], fd)
+    for (i, j) in [(0, 1), (2, 3), (1, 1)]:
+        E = np.zeros_like(B)
+        E[i, j] = h
+        fd = (loss(A, B + E, C) - loss(A, B - E, C)) / (2 * h)
+        assert abs(dB[i, j] - fd) <= 1e-7 * max(1.0, abs(fd)), (i, j, dB[i, j], fd)
+        assert maskB[i, j]
+    for (i, j) in [(0, 0), (4, 3), (2, 1)]:
+        E = np.zeros_like(C)
+        E[i, j] = h
+        fd = (loss(A, B, C + E) - loss(A, B, C - E)) / (2 * h)
+        assert abs(dC[i, j] - fd) <= 1e-7 * max(1.0, abs(fd))

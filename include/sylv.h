@@ -1,0 +1,215 @@
+/*
+ * sylv.h -- C ABI of the GB300 (sm_103a) solver for the triangular Sylvester
+ * equation
+ *
+ *        op(A) * Y + Y * op(B) = alpha * C,      op(X) = X or X^T,
+ *
+ * with A (m x m) and B (n x n) upper quasi-triangular (real Schur form: upper
+ * triangular except for 2x2 diagonal blocks, each marked by a nonzero entry on
+ * the first subdiagonal; Schwarz & Kjelgaard Mikkelsen 2019, Sec. 1, eq. (4)).
+ * The method is the paper's tiled robust solver (Algorithm 4, "drsylv"): tiles of
+ * Y carry local power-of-two scale factors (augmented tiles, Sec. 2.2, Def. 1),
+ * diagonal tiles are solved by the robust scalar algorithm (Algorithm 2, with the
+ * 1x1/2x2 block solves of Sec. 2.1), off-diagonal tiles are updated with the
+ * robust tile update (Algorithm 3), and a final consistency scaling brings every
+ * tile to the global factor alpha = min alpha_kl.  alpha is in (0, 1] and is an
+ * exact power of two; no entry of Y ever exceeds the overflow threshold Omega.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are column-major with the given leading dimensions (>= max(1, rows)).
+ *   - Matrix pointers are DEVICE pointers (cudaMalloc'd or torch CUDA memory) on
+ *     the current CUDA device; they stay owned by the caller.  C is overwritten by
+ *     Y (the LAPACK convention).
+ *   - Only the upper triangle and the first subdiagonal of A and B are read.  Two
+ *     consecutive nonzero subdiagonal entries make the input invalid
+ *     (SYLV_ERR_STRUCTURE_A / _B).
+ *   - Inputs must be finite; every tile of A, B, C must have infinity norm
+ *     <= Omega (the precondition of Algorithms 2-4).
+ *   - The solve runs on opts->stream (the legacy default stream when NULL).  With
+ *     opts->sync != 0 the call waits for the GPU and fills a HOST sylv_result;
+ *     with opts->sync == 0 it only enqueues work and writes the sylv_result to the
+ *     DEVICE address given, so the call can be captured in a CUDA graph (pass a
+ *     caller-owned workspace in that case).
+ *   - Return value: a SYLV_* code below.  Negative values -i name the invalid
+ *     argument i (1-based, LAPACK style); such calls enqueue no GPU work.
+ */
+#ifndef SYLV_H
+#define SYLV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes (return values and sylv_result.info) ------------------ */
+#define SYLV_OK 0
+#define SYLV_NEAR_SINGULAR 1   /* a 1x1/2x2 block system was near singular (lambda_i(A) +
+                                  lambda_j(B) ~ 0, eq. (1)'s uniqueness condition);
+                                  its pivot was raised to smin and the solve went on */
+#define SYLV_SCALE_UNDERFLOW 2 /* alpha < 2^-1074: the double `scale` is 0, use log2scale */
+#define SYLV_NOT_CONVERGED 3   /* FP32 + refinement did not reach opts->tol */
+#define SYLV_OVERFLOWED 4      /* non-robust mode only: Y holds Inf/NaN (Algorithm 1 overflowed) */
+#define SYLV_ERR_STRUCTURE_A 101 /* A has two consecutive nonzero subdiagonal entries */
+#define SYLV_ERR_STRUCTURE_B 102 /* B has two consecutive nonzero subdiagonal entries */
+#define SYLV_ERR_NONFINITE 103   /* NaN or Inf in A, B or C */
+#define SYLV_ERR_RANGE 104       /* an input tile's infinity norm exceeds Omega */
+#define SYLV_ERR_TIMEOUT 105     /* a device-side wait exceeded opts->timeout_ms */
+#define SYLV_ERR_CUDA 106        /* a CUDA runtime call failed */
+#define SYLV_ERR_WORKSPACE 107   /* caller-provided workspace too small or misaligned */
+#define SYLV_ERR_UNSUPPORTED 108 /* option combination not built (e.g. tile size) */
+
+/* ---- precisions ------------------------------------------------------------ */
+#define SYLV_FP64 0            /* robust tiled solve in binary64 (Algorithm 4) */
+#define SYLV_FP64_NONROBUST 1  /* same tiling, no scaling at all (Algorithm 1 per tile) */
+#define SYLV_FP32_REFINE 2     /* robust solve in binary32 + residual refinement in
+                                  binary64-accurate arithmetic (not in the paper) */
+
+typedef struct sylv_opts {
+  int32_t transa;          /* 0: op(A) = A, 1: op(A) = A^T */
+  int32_t transb;          /* 0: op(B) = B, 1: op(B) = B^T */
+  int32_t precision;       /* SYLV_FP64, SYLV_FP64_NONROBUST or SYLV_FP32_REFINE */
+  int32_t tile;            /* nominal tile size t (Sec. 2.2); 0 = automatic.  Tiles
+                              hold t or t-1 rows so that no 2x2 block is split */
+  double omega;            /* overflow threshold Omega; 0 = 2^1020 (2^124 for binary32) */
+  double tol;              /* refinement: stop when max|dY| <= tol * max|Y|; 0 = 2^-46 */
+  int32_t maxit;           /* refinement: at most this many correction solves; 0 = 6 */
+  int32_t sync;            /* 1: wait, host result; 0: asynchronous, device result */
+  int64_t timeout_ms;      /* bound on each device-side wait; 0 = 20000 */
+  void* stream;            /* cudaStream_t; NULL = legacy default stream */
+  void* workspace;         /* device memory for the solver's scratch, or NULL to let
+                              the library allocate (and cache) it */
+  size_t workspace_bytes;  /* size of `workspace` */
+} sylv_opts;
+
+typedef struct sylv_result {
+  int64_t log2scale;  /* alpha = 2^log2scale (exact; never underflows) */
+  double scale;       /* alpha as a double (0 when alpha < 2^-1074) */
+  int32_t info;       /* SYLV_OK, SYLV_NEAR_SINGULAR, SYLV_SCALE_UNDERFLOW, ... */
+  int32_t iters;      /* refinement corrections applied (FP32_REFINE), else 0 */
+  double last_update; /* FP32_REFINE: max|dY| / max|Y| of the last correction */
+  int32_t scale_events; /* number of scaling decisions taken (Sec. 4's "amount of scaling") */
+  int32_t min_tile_exp; /* smallest local exponent before consistency scaling */
+} sylv_result;
+
+/* Fill *opts with the defaults described above (all zero except sync = 1). */
+void sylv_default_opts(sylv_opts* opts);
+
+/*
+ * sylv_tri_solve -- robust FP64 solve of A*Y + Y*B = alpha*C (Algorithm 4).
+ *   m, n       orders of A and B (m, n >= 0)
+ *   A, lda     device, m x m upper quasi-triangular, read only
+ *   B, ldb     device, n x n upper quasi-triangular, read only
+ *   C, ldc     device, m x n; on exit Y
+ *   tile       nominal tile size, 0 = automatic
+ *   scale      HOST pointer; receives alpha (0 if it underflows)
+ * Synchronous on the legacy default stream, library-managed workspace.
+ * Returns SYLV_OK, SYLV_NEAR_SINGULAR, SYLV_SCALE_UNDERFLOW or an error code.
+ */
+int sylv_tri_solve(int64_t m, int64_t n, const double* A, int64_t lda, const double* B,
+                   int64_t ldb, double* C, int64_t ldc, int64_t tile, double* scale);
+
+/*
+ * sylv_tri_solve_ex -- the same solve with options: op(A)/op(B) transposes,
+ * precision mode (robust FP64 / non-robust FP64 / FP32 + refinement), stream,
+ * workspace and asynchronous results.  `result` is a HOST pointer when
+ * opts->sync != 0 and a DEVICE pointer otherwise (may be NULL: no result).
+ * opts == NULL means sylv_default_opts.
+ */
+int sylv_tri_solve_ex(int64_t m, int64_t n, const double* A, int64_t lda, const double* B,
+                      int64_t ldb, double* C, int64_t ldc, const sylv_opts* opts,
+                      sylv_result* result);
+
+/* Bytes of device workspace sylv_tri_solve_ex needs for these sizes and options
+ * (opts may be NULL).  Workspace passed by the caller must be 256-byte aligned. */
+size_t sylv_workspace_size(int64_t m, int64_t n, const sylv_opts* opts);
+
+/*
+ * Batched solves: `count` independent equations op(A_i) Y_i + Y_i op(B_i) =
+ * alpha_i C_i of individual sizes, solved together by one persistent launch
+ * whose task list interleaves the tiles of all equations level by level (a tile
+ * of one equation only ever waits on tiles of the same equation, Sec. 2.2's task
+ * dependences).  Not in the paper.
+ *
+ * sylv_batch_create builds a plan: it validates the HOST arrays m[i], n[i],
+ * lda[i], ldb[i], ldc[i] and the device pointers A[i], B[i], C[i] (HOST arrays of
+ * device pointers), picks each equation's tile size (opts->tile, or the built-in
+ * size table when 0), allocates the plan's device workspace and uploads the
+ * descriptors (one host-to-device copy, then a stream synchronize).
+ * sylv_batch_execute only enqueues kernels on `stream` (capturable in a CUDA
+ * graph; replays re-solve in place, so C_i must be refilled by the caller between
+ * replays).  sylv_batch_results waits for the stream and copies `count` results
+ * to the HOST array `results`.  The plan's matrices must stay allocated while it
+ * is used.  Returns SYLV_OK or an error code; per-equation status is in
+ * results[i].info.
+ */
+typedef struct sylv_batch_plan sylv_batch_plan;
+int sylv_batch_create(sylv_batch_plan** plan, int32_t count, const int64_t* m, const int64_t* n,
+                      const double* const* A, const int64_t* lda, const double* const* B,
+                      const int64_t* ldb, double* const* C, const int64_t* ldc,
+                      const sylv_opts* opts);
+int sylv_batch_execute(sylv_batch_plan* plan, void* stream);
+int sylv_batch_results(sylv_batch_plan* plan, sylv_result* results);
+void sylv_batch_destroy(sylv_batch_plan* plan);
+
+/* One-call form of the above: create, execute on opts->stream, wait, fill the
+ * HOST array results[count], destroy. */
+int sylv_tri_solve_batched(int32_t count, const int64_t* m, const int64_t* n,
+                           const double* const* A, const int64_t* lda, const double* const* B,
+                           const int64_t* ldb, double* const* C, const int64_t* ldc,
+                           const sylv_opts* opts, sylv_result* results);
+
+/*
+ * sylv_tri_solve_backward -- adjoint of the FP64 solve for reverse-mode
+ * differentiation (not in the paper).  The forward solve returned Y = alpha*X
+ * with op(A) X + X op(B) = C, alpha a power of two held fixed (it is piecewise
+ * constant in the inputs).  Given G = dL/dY (device, m x n, ldg) this computes
+ *   Gamma   solving  op(A)^T Gamma + Gamma op(B)^T = G  (the same robust tiled
+ *           solver with both transposes flipped; Y, A, B unchanged),
+ *   dL/dC = alpha * Gamma                     -> written over G,
+ *   dL/dA = -Gamma Y^T  (op(A) = A)  or  -Y Gamma^T  (op(A) = A^T)   -> dA (m x m, ldda),
+ *   dL/dB = -Y^T Gamma  (op(B) = B)  or  -Gamma^T Y  (op(B) = B^T)   -> dB (n x n, lddb),
+ * since dL/dX = alpha*G and X = Y/alpha.  dA and dB are masked to the entries the
+ * solver reads (upper triangle plus the nonzero subdiagonal entries that mark 2x2
+ * blocks); all other entries are set to 0.  dA or dB may be NULL to skip them.
+ * log2scale is the forward result's exponent (alpha = 2^log2scale).  If the adjoint
+ * solve has to scale (its own factor alpha_G = 2^result->log2scale < 1), all three
+ * outputs are returned multiplied by alpha_G.  Y and G are device pointers.
+ */
+int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, const double* B,
+                            int64_t ldb, const double* Y, int64_t ldy, int64_t log2scale,
+                            double* G, int64_t ldg, double* dA, int64_t ldda, double* dB,
+                            int64_t lddb, const sylv_opts* opts, sylv_result* result);
+
+/*
+ * sylv_diag_wait_timeout -- diagnostic of the solver's bounded waits (not in the
+ * paper).  Launches one CTA that waits, with the same bounded wait the tile-DAG
+ * kernel uses for its ready flags, on a flag that nothing ever sets, and returns
+ * the status the kernel recorded: SYLV_ERR_TIMEOUT once timeout_ms has passed
+ * (the GPU context stays usable), or an error code if the launch failed.  It
+ * allocates a few bytes of device memory and synchronizes `stream`.
+ */
+int sylv_diag_wait_timeout(int64_t timeout_ms, void* stream);
+
+/*
+ * Kernel timing for benchmarks (not in the paper).  While enabled, every launch of
+ * the tile-DAG kernel (the solver's dominant kernel) is bracketed by CUDA events
+ * recorded on the stream it is launched on.  sylv_profile_read waits for those
+ * events, returns the summed kernel time in milliseconds and the number of
+ * launches since the last read, and releases the events.  Host-side state, not
+ * thread-safe; sylv_profile(0) disables recording.
+ */
+int sylv_profile(int enable);
+int sylv_profile_read(double* dag_ms, int64_t* dag_launches);
+
+/* Static description of a status code. */
+const char* sylv_error_string(int code);
+
+/* Library version string. */
+const char* sylv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SYLV_H */

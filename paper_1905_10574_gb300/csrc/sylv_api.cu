@@ -1,0 +1,818 @@
+// sylv_api.cu -- host side of the C ABI declared in include/sylv.h: argument
+// checking, workspace layout, the launch sequence of one (batched) solve, the
+// transposed forms, the FP32 + refinement loop, the adjoint, and batch plans.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "sylv_gemm.cuh"
+#include "sylv_internal.cuh"
+#include "sylv_launch.h"
+#include "sylv_prep.cuh"
+
+using namespace sylv;
+
+namespace {
+
+struct Profiler {
+  bool on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  cudaEvent_t pending = nullptr;
+};
+Profiler& profiler() {
+  static Profiler p;
+  return p;
+}
+
+}  // namespace
+
+namespace sylv {
+void profile_begin(cudaStream_t s) {
+  Profiler& p = profiler();
+  if (!p.on) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, s);
+  p.pending = e;
+}
+void profile_end(cudaStream_t s) {
+  Profiler& p = profiler();
+  if (!p.on || !p.pending) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, s);
+  p.ev.emplace_back(p.pending, e);
+  p.pending = nullptr;
+}
+}  // namespace sylv
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxScanN = 1 << 20;  // largest order the structure scan holds in shared memory
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct Shape {
+  int64_t m, n;
+  int t;
+  int pmax, qmax;
+};
+
+// Tile capacity of a ragged partition: tiles hold t or t-1 rows except the last.
+int tile_cap(int64_t N, int t) {
+  if (N <= 0) return 0;
+  const int64_t d = t > 2 ? t - 1 : 1;
+  return static_cast<int>((N + d - 1) / d);
+}
+
+// Built-in tile choice: t = 64 (the largest capacity built) unless the problem is
+// small, where shorter tiles shorten the chain of diagonal solves.
+int auto_tile(int64_t m, int64_t n) {
+  const int64_t mn = m < n ? m : n;
+  return mn <= 192 ? 32 : 64;
+}
+
+// Byte offsets of the tile workspace of one launch (FP64 or FP32 solve).
+struct Layout {
+  // zero-initialised region [zero_lo, zero_hi)
+  size_t ctrl, st, lvl_cnt, lvl_cur, tflag, zero_lo, zero_hi;
+  size_t lvl_off, inst, res, tasks, ibuf, texp, tnorm, dbuf;
+  size_t total;
+  int nlevels_max;
+  int max_tiles;  // max pmax*qmax over equations
+  int64_t sum_tiles;
+};
+
+Layout make_layout(const std::vector<Shape>& sh, size_t base) {
+  Layout L{};
+  int64_t tiles = 0, ib = 0, db = 0;
+  int nlev = 1, mt = 0;
+  for (const Shape& s : sh) {
+    tiles += static_cast<int64_t>(s.pmax) * s.qmax;
+    ib += s.pmax + 1 + s.qmax + 1;
+    db += static_cast<int64_t>(s.pmax) * s.pmax + static_cast<int64_t>(s.qmax) * s.qmax;
+    nlev = std::max(nlev, s.pmax + s.qmax);
+    mt = std::max(mt, s.pmax * s.qmax);
+  }
+  const size_t count = sh.size();
+  size_t o = align_up(base);
+  L.zero_lo = o;
+  L.ctrl = o;
+  o = align_up(o + sizeof(Ctrl));
+  L.st = o;
+  o = align_up(o + count * sizeof(InstState));
+  L.lvl_cnt = o;
+  o = align_up(o + nlev * sizeof(int32_t));
+  L.lvl_cur = o;
+  o = align_up(o + nlev * sizeof(int32_t));
+  L.tflag = o;
+  o = align_up(o + tiles * sizeof(int32_t));
+  L.zero_hi = o;
+  L.lvl_off = o;
+  o = align_up(o + nlev * sizeof(int32_t));
+  L.inst = o;
+  o = align_up(o + count * sizeof(Inst));
+  L.res = o;
+  o = align_up(o + count * sizeof(sylv_result));
+  L.tasks = o;
+  o = align_up(o + tiles * sizeof(Task));
+  L.ibuf = o;
+  o = align_up(o + ib * sizeof(int32_t));
+  L.texp = o;
+  o = align_up(o + tiles * sizeof(int32_t));
+  L.tnorm = o;
+  o = align_up(o + tiles * sizeof(double));
+  L.dbuf = o;
+  o = align_up(o + db * sizeof(double));
+  L.total = o;
+  L.nlevels_max = nlev;
+  L.max_tiles = mt;
+  L.sum_tiles = tiles;
+  return L;
+}
+
+// Descriptors for each equation (host copies) given the layout.
+std::vector<Inst> make_insts(const std::vector<Shape>& sh, const Layout& L, const std::vector<const void*>& A,
+                             const std::vector<int64_t>& lda, const std::vector<const void*>& B,
+                             const std::vector<int64_t>& ldb, const std::vector<void*>& C,
+                             const std::vector<int64_t>& ldc, int robust, double omega) {
+  std::vector<Inst> v(sh.size());
+  int64_t tile = 0, ib = 0, db = 0;
+  for (size_t i = 0; i < sh.size(); ++i) {
+    Inst& I = v[i];
+    I.m = sh[i].m;
+    I.n = sh[i].n;
+    I.lda = lda[i];
+    I.ldb = ldb[i];
+    I.ldc = ldc[i];
+    I.A = A[i];
+    I.B = B[i];
+    I.C = C[i];
+    I.t = sh[i].t;
+    I.pmax = sh[i].pmax;
+    I.qmax = sh[i].qmax;
+    I.robust = robust;
+    I.rb = ib;
+    I.cb = ib + sh[i].pmax + 1;
+    ib += sh[i].pmax + 1 + sh[i].qmax + 1;
+    I.tile = tile;
+    tile += static_cast<int64_t>(sh[i].pmax) * sh[i].qmax;
+    I.an = db;
+    I.bn = db + static_cast<int64_t>(sh[i].pmax) * sh[i].pmax;
+    db += static_cast<int64_t>(sh[i].pmax) * sh[i].pmax + static_cast<int64_t>(sh[i].qmax) * sh[i].qmax;
+    I.omega = omega;
+  }
+  (void)L;
+  return v;
+}
+
+Work make_work(char* ws, const Layout& L, int count, int64_t timeout_ns) {
+  Work w{};
+  w.inst = reinterpret_cast<Inst*>(ws + L.inst);
+  w.st = reinterpret_cast<InstState*>(ws + L.st);
+  w.count = count;
+  w.nlevels_max = L.nlevels_max;
+  w.tasks = reinterpret_cast<Task*>(ws + L.tasks);
+  w.ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
+  w.lvl_cnt = reinterpret_cast<int32_t*>(ws + L.lvl_cnt);
+  w.lvl_off = reinterpret_cast<int32_t*>(ws + L.lvl_off);
+  w.lvl_cur = reinterpret_cast<int32_t*>(ws + L.lvl_cur);
+  w.ibuf = reinterpret_cast<int32_t*>(ws + L.ibuf);
+  w.texp = reinterpret_cast<int32_t*>(ws + L.texp);
+  w.tflag = reinterpret_cast<int32_t*>(ws + L.tflag);
+  w.tnorm = reinterpret_cast<double*>(ws + L.tnorm);
+  w.dbuf = reinterpret_cast<double*>(ws + L.dbuf);
+  w.res = reinterpret_cast<sylv_result*>(ws + L.res);
+  w.skip = nullptr;
+  w.timeout_ns = timeout_ns;
+  w.max_tiles = L.max_tiles;
+  return w;
+}
+
+__global__ void k_set_inst(Inst* dst, Inst src) { *dst = src; }
+
+// One thread waits on a flag nothing sets; the bounded wait records the timeout.
+__global__ void k_wait_nothing(int* flag, Ctrl* ctrl, long long timeout_ns) {
+  if (threadIdx.x == 0) wait_flag(flag, ctrl, timeout_ns);
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? SYLV_OK : SYLV_ERR_CUDA; }
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <typename T>
+cudaError_t set_scan_smem() {
+  static bool done = false;
+  if (!done) {
+    cudaError_t e = cudaFuncSetAttribute(k_scan<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kMaxScanN / 8));
+    if (e != cudaSuccess) return e;
+    done = true;
+  }
+  return cudaSuccess;
+}
+
+// Preparation kernels of a launch: structure scan + partition, tile norms, task list.
+template <typename T>
+cudaError_t run_prep(const Work& w, const Layout& L, int count, int64_t maxN, int pmax_all, cudaStream_t s) {
+  cudaError_t e = set_scan_smem<T>();
+  if (e != cudaSuccess) return e;
+  const size_t scan_smem = ((maxN + 31) / 32) * sizeof(unsigned) + 16;
+  k_scan<T><<<dim3(count, 2), 512, scan_smem, s>>>(w);
+  k_norms<T><<<dim3(count, std::max(pmax_all, 1), 2), 256, 0, s>>>(w);
+  k_level_count<<<count, 256, 0, s>>>(w);
+  k_level_scan<<<1, 32, 0, s>>>(w);
+  k_level_scatter<<<count, 256, 0, s>>>(w);
+  (void)L;
+  return cudaGetLastError();
+}
+
+// Library-managed workspace (one cached buffer per device, grown on demand).
+struct WsCache {
+  std::mutex mu;
+  void* ptr[64] = {};
+  size_t bytes[64] = {};
+};
+WsCache& ws_cache() {
+  static WsCache c;
+  return c;
+}
+int get_workspace(size_t need, void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SYLV_ERR_CUDA;
+  WsCache& c = ws_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  if (c.bytes[dev] < need) {
+    if (c.ptr[dev]) cudaFree(c.ptr[dev]);
+    c.ptr[dev] = nullptr;
+    c.bytes[dev] = 0;
+    size_t want = need + need / 4;
+    if (cudaMalloc(&c.ptr[dev], want) != cudaSuccess) {
+      cudaGetLastError();
+      if (cudaMalloc(&c.ptr[dev], need) != cudaSuccess) {
+        cudaGetLastError();
+        return SYLV_ERR_CUDA;
+      }
+      want = need;
+    }
+    c.bytes[dev] = want;
+  }
+  *out = c.ptr[dev];
+  return SYLV_OK;
+}
+
+struct Opts {
+  int transa, transb, precision, tile, maxit, sync;
+  double omega, tol;
+  int64_t timeout_ns;
+  cudaStream_t stream;
+  void* ws;
+  size_t ws_bytes;
+};
+
+int read_opts(const sylv_opts* o, Opts* out) {
+  sylv_opts d;
+  sylv_default_opts(&d);
+  if (!o) o = &d;
+  if (o->transa < 0 || o->transa > 1 || o->transb < 0 || o->transb > 1) return SYLV_ERR_UNSUPPORTED;
+  if (o->precision < SYLV_FP64 || o->precision > SYLV_FP32_REFINE) return SYLV_ERR_UNSUPPORTED;
+  if (o->tile < 0 || o->tile == 1 || o->tile > 64) return SYLV_ERR_UNSUPPORTED;
+  out->transa = o->transa;
+  out->transb = o->transb;
+  out->precision = o->precision;
+  out->tile = o->tile;
+  out->maxit = o->maxit > 0 ? o->maxit : 6;
+  out->sync = o->sync;
+  out->omega = o->omega > 0 ? o->omega : (o->precision == SYLV_FP32_REFINE ? 0x1p124 : 0x1p1020);
+  out->tol = o->tol > 0 ? o->tol : 0x1p-46;
+  out->timeout_ns = (o->timeout_ms > 0 ? o->timeout_ms : 20000) * 1000000LL;
+  out->stream = static_cast<cudaStream_t>(o->stream);
+  out->ws = o->workspace;
+  out->ws_bytes = o->workspace_bytes;
+  return SYLV_OK;
+}
+
+// ---- single-equation solve: sizes of the pieces of the workspace
+struct SolvePlan {
+  Shape shape;
+  Layout L;            // tile workspace (FP64 solve, or the FP32 correction solves)
+  size_t off_at, off_bt;  // anti-transposed A, B (FP64) when transposed
+  size_t off_a32, off_b32, off_rf, off_r, off_x, off_slots, off_rs;  // FP32 + refinement
+  size_t total;
+};
+
+SolvePlan plan_solve(int64_t m, int64_t n, const Opts& o) {
+  SolvePlan P{};
+  const int t = o.tile ? o.tile : auto_tile(m, n);
+  P.shape = Shape{m, n, t, tile_cap(m, t), tile_cap(n, t)};
+  size_t off = 0;
+  P.off_at = off;
+  if (o.transa) off = align_up(off + sizeof(double) * m * m);
+  P.off_bt = off;
+  if (o.transb) off = align_up(off + sizeof(double) * n * n);
+  if (o.precision == SYLV_FP32_REFINE) {
+    P.off_a32 = off;
+    off = align_up(off + sizeof(float) * m * m);
+    P.off_b32 = off;
+    off = align_up(off + sizeof(float) * n * n);
+    P.off_rf = off;
+    off = align_up(off + sizeof(float) * m * n);
+    P.off_r = off;
+    off = align_up(off + sizeof(double) * m * n);
+    P.off_x = off;
+    off = align_up(off + sizeof(double) * m * n);
+    P.off_slots = off;  // amax, bmax, then rmax/dmax/xmax per iteration
+    off = align_up(off + sizeof(unsigned long long) * (2 + 3 * (o.maxit + 1)));
+    P.off_rs = off;
+    off = align_up(off + sizeof(RefineState));
+  }
+  P.L = make_layout({P.shape}, off);
+  P.total = P.L.total;
+  return P;
+}
+
+int check_args(int64_t m, int64_t n, const void* A, int64_t lda, const void* B, int64_t ldb, const void* C,
+               int64_t ldc) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (m > 0 && !A) return -3;
+  if (lda < (m > 1 ? m : 1)) return -4;
+  if (n > 0 && !B) return -5;
+  if (ldb < (n > 1 ? n : 1)) return -6;
+  if (m > 0 && n > 0 && !C) return -7;
+  if (ldc < (m > 1 ? m : 1)) return -8;
+  if (m > kMaxScanN || n > kMaxScanN) return SYLV_ERR_UNSUPPORTED;
+  return SYLV_OK;
+}
+
+int grid_for(int64_t elems) {
+  int64_t g = (elems + 255) / 256;
+  const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
+  if (g > cap) g = cap;
+  return static_cast<int>(g < 1 ? 1 : g);
+}
+
+// Enqueue one FP64 (robust or not) tiled solve of an untransposed problem.
+int enqueue_fp64(const SolvePlan& P, char* ws, const double* A, int64_t lda, const double* B, int64_t ldb,
+                 double* C, int64_t ldc, const Opts& o, bool robust, sylv_result* dres) {
+  const Layout& L = P.L;
+  cudaStream_t s = o.stream;
+  Work w = make_work(ws, L, 1, o.timeout_ns);
+  if (cudaMemsetAsync(ws + L.zero_lo, 0, L.zero_hi - L.zero_lo, s) != cudaSuccess) return SYLV_ERR_CUDA;
+  std::vector<Inst> I = make_insts({P.shape}, L, {A}, {lda}, {B}, {ldb}, {C}, {ldc}, robust ? 1 : 0, o.omega);
+  k_set_inst<<<1, 1, 0, s>>>(w.inst, I[0]);
+  cudaError_t e = run_prep<double>(w, L, 1, std::max(P.shape.m, P.shape.n), std::max(P.shape.pmax, P.shape.qmax), s);
+  if (e != cudaSuccess) return SYLV_ERR_CUDA;
+  e = launch_dag_f64(P.shape.t, robust, w, L.max_tiles, s);
+  if (e != cudaSuccess) return SYLV_ERR_CUDA;
+  k_consistency<double><<<grid_for(static_cast<int64_t>(L.max_tiles) * 256), 256, 0, s>>>(w);
+  k_results<<<1, 32, 0, s>>>(w);
+  if (dres && cudaMemcpyAsync(dres, w.res, sizeof(sylv_result), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return SYLV_ERR_CUDA;
+  return cuda_status(cudaGetLastError());
+}
+
+// Enqueue the FP32 + refinement solve of an untransposed problem:
+//   X = 0, R = C;  repeat: solve A D + D B = R in FP32 (robust, scaled to FP32
+//   range), X += D, R = C - A X - X B in FP64, until max|D| <= tol max|X|.
+int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, const double* B, int64_t ldb,
+                   double* C, int64_t ldc, const Opts& o, sylv_result* dres) {
+  const int64_t m = P.shape.m, n = P.shape.n;
+  cudaStream_t s = o.stream;
+  float* A32 = reinterpret_cast<float*>(ws + P.off_a32);
+  float* B32 = reinterpret_cast<float*>(ws + P.off_b32);
+  float* Rf = reinterpret_cast<float*>(ws + P.off_rf);
+  double* R = reinterpret_cast<double*>(ws + P.off_r);
+  double* X = reinterpret_cast<double*>(ws + P.off_x);
+  unsigned long long* slots = reinterpret_cast<unsigned long long*>(ws + P.off_slots);
+  unsigned long long* amax = slots + 0;
+  unsigned long long* bmax = slots + 1;
+  RefineState* rs = reinterpret_cast<RefineState*>(ws + P.off_rs);
+  const Layout& L = P.L;
+  Work w = make_work(ws, L, 1, o.timeout_ns);
+  w.skip = &rs->conv;
+
+  if (cudaMemsetAsync(slots, 0, sizeof(unsigned long long) * (2 + 3 * (o.maxit + 1)), s) != cudaSuccess)
+    return SYLV_ERR_CUDA;
+  if (cudaMemsetAsync(rs, 0, sizeof(RefineState), s) != cudaSuccess) return SYLV_ERR_CUDA;
+  if (cudaMemsetAsync(X, 0, sizeof(double) * m * n, s) != cudaSuccess) return SYLV_ERR_CUDA;
+  if (cudaMemsetAsync(ws + L.zero_lo, 0, L.zero_hi - L.zero_lo, s) != cudaSuccess) return SYLV_ERR_CUDA;
+  // A and B scaled by one common power of two into FP32 (the solution is unchanged).
+  k_maxabs_quasi<<<grid_for(m * m), 256, 0, s>>>(A, lda, m, amax);
+  k_maxabs_quasi<<<grid_for(n * n), 256, 0, s>>>(B, ldb, n, bmax);
+  k_to_float<<<grid_for(m * m), 256, 0, s>>>(A, lda, A32, m, m, m, amax, bmax, 1, nullptr);
+  k_to_float<<<grid_for(n * n), 256, 0, s>>>(B, ldb, B32, n, n, n, amax, bmax, 1, nullptr);
+  std::vector<Inst> I = make_insts({P.shape}, L, {A32}, {m}, {B32}, {n}, {Rf}, {m}, 1, o.omega);
+  k_set_inst<<<1, 1, 0, s>>>(w.inst, I[0]);
+  cudaError_t e = run_prep<float>(w, L, 1, std::max(m, n), std::max(P.shape.pmax, P.shape.qmax), s);
+  if (e != cudaSuccess) return SYLV_ERR_CUDA;
+  for (int it = 0; it < o.maxit; ++it) {
+    unsigned long long* rmax = slots + 2 + 3 * it;
+    unsigned long long* dmax = rmax + 1;
+    unsigned long long* xmax = rmax + 2;
+    if (it == 0)
+      k_copy_max<<<grid_for(m * n), 256, 0, s>>>(C, ldc, R, m, m, n, rmax);
+    else
+      k_residual<<<dim3((m + GT - 1) / GT, (n + GT - 1) / GT), 256, 0, s>>>(A, lda, B, ldb, C, ldc, X, m, R, m, m,
+                                                                             n, rmax, &rs->conv);
+    k_to_float<<<grid_for(m * n), 256, 0, s>>>(R, m, Rf, m, m, n, rmax, nullptr, 0, &rs->conv);
+    if (it > 0) {
+      if (cudaMemsetAsync(w.tflag, 0, sizeof(int32_t) * L.sum_tiles, s) != cudaSuccess) return SYLV_ERR_CUDA;
+      if (cudaMemsetAsync(&w.ctrl->ticket, 0, sizeof(int32_t), s) != cudaSuccess) return SYLV_ERR_CUDA;
+    }
+    e = launch_dag_f32(P.shape.t, w, L.max_tiles, s);
+    if (e != cudaSuccess) return SYLV_ERR_CUDA;
+    k_accumulate<<<grid_for(static_cast<int64_t>(L.max_tiles) * 256), 256, 0, s>>>(w, X, m, rmax, amax, bmax, dmax,
+                                                                                   xmax, &rs->conv);
+    k_refine_check<<<1, 1, 0, s>>>(rs, dmax, xmax, o.tol, w);
+  }
+  k_copy<<<grid_for(m * n), 256, 0, s>>>(X, m, C, ldc, m, n);
+  k_refine_result<<<1, 1, 0, s>>>(rs, w.res, o.maxit);
+  if (dres && cudaMemcpyAsync(dres, w.res, sizeof(sylv_result), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return SYLV_ERR_CUDA;
+  return cuda_status(cudaGetLastError());
+}
+
+// Solve with options on device pointers; the result goes to dres (device) and,
+// when o.sync, to hres (host).
+int solve_impl(int64_t m, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+               int64_t ldc, const Opts& o, sylv_result* hres, sylv_result* dres) {
+  if (m == 0 || n == 0) {
+    sylv_result r{};
+    r.scale = 1.0;
+    if (hres) *hres = r;
+    if (dres && cudaMemcpyAsync(dres, &r, sizeof(r), cudaMemcpyHostToDevice, o.stream) != cudaSuccess)
+      return SYLV_ERR_CUDA;
+    if (dres && o.sync && cudaStreamSynchronize(o.stream) != cudaSuccess) return SYLV_ERR_CUDA;
+    return SYLV_OK;
+  }
+  const SolvePlan P = plan_solve(m, n, o);
+  char* ws = nullptr;
+  if (o.ws) {
+    if (o.ws_bytes < P.total || (reinterpret_cast<uintptr_t>(o.ws) & (kAlign - 1))) return SYLV_ERR_WORKSPACE;
+    ws = static_cast<char*>(o.ws);
+  } else {
+    void* p = nullptr;
+    const int rc = get_workspace(P.total, &p);
+    if (rc) return rc;
+    ws = static_cast<char*>(p);
+  }
+  cudaStream_t s = o.stream;
+  const double* Ae = A;
+  const double* Be = B;
+  int64_t ldae = lda, ldbe = ldb;
+  if (o.transa) {
+    double* At = reinterpret_cast<double*>(ws + P.off_at);
+    k_anti_transpose<double><<<dim3((m + 31) / 32, (m + 31) / 32), 256, 0, s>>>(A, lda, At, m, m);
+    k_flip<double><<<grid_for(m * n / 2 + 1), 256, 0, s>>>(C, ldc, m, n, 0);
+    Ae = At;
+    ldae = m;
+  }
+  if (o.transb) {
+    double* Bt = reinterpret_cast<double*>(ws + P.off_bt);
+    k_anti_transpose<double><<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, s>>>(B, ldb, Bt, n, n);
+    k_flip<double><<<grid_for(m * n / 2 + 1), 256, 0, s>>>(C, ldc, m, n, 1);
+    Be = Bt;
+    ldbe = n;
+  }
+  sylv_result* res_dev = reinterpret_cast<sylv_result*>(ws + P.L.res);
+  int rc;
+  if (o.precision == SYLV_FP32_REFINE)
+    rc = enqueue_refine(P, ws, Ae, ldae, Be, ldbe, C, ldc, o, nullptr);
+  else
+    rc = enqueue_fp64(P, ws, Ae, ldae, Be, ldbe, C, ldc, o, o.precision == SYLV_FP64, nullptr);
+  if (rc) return rc;
+  if (o.transa) k_flip<double><<<grid_for(m * n / 2 + 1), 256, 0, s>>>(C, ldc, m, n, 0);
+  if (o.transb) k_flip<double><<<grid_for(m * n / 2 + 1), 256, 0, s>>>(C, ldc, m, n, 1);
+  if (dres && cudaMemcpyAsync(dres, res_dev, sizeof(sylv_result), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return SYLV_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return SYLV_ERR_CUDA;
+  if (o.sync) {
+    sylv_result r{};
+    if (cudaMemcpyAsync(&r, res_dev, sizeof(r), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SYLV_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SYLV_ERR_CUDA;
+    if (hres) *hres = r;
+    return r.info;
+  }
+  return SYLV_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+void sylv_default_opts(sylv_opts* opts) {
+  if (!opts) return;
+  std::memset(opts, 0, sizeof(*opts));
+  opts->sync = 1;
+}
+
+const char* sylv_version(void) { return "sylv-gb300 0.1 (sm_103a)"; }
+
+int sylv_profile(int enable) {
+  profiler().on = enable != 0;
+  return SYLV_OK;
+}
+
+int sylv_profile_read(double* dag_ms, int64_t* dag_launches) {
+  Profiler& p = profiler();
+  double tot = 0.0;
+  int rc = SYLV_OK;
+  for (auto& pr : p.ev) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(pr.second) != cudaSuccess || cudaEventElapsedTime(&ms, pr.first, pr.second) != cudaSuccess)
+      rc = SYLV_ERR_CUDA;
+    tot += ms;
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  if (dag_ms) *dag_ms = tot;
+  if (dag_launches) *dag_launches = static_cast<int64_t>(p.ev.size());
+  p.ev.clear();
+  return rc;
+}
+
+int sylv_diag_wait_timeout(int64_t timeout_ms, void* stream) {
+  if (timeout_ms <= 0) return -1;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* p = nullptr;
+  if (cudaMalloc(&p, 256) != cudaSuccess) return SYLV_ERR_CUDA;
+  int* flag = static_cast<int*>(p);
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(static_cast<char*>(p) + 64);
+  int rc = SYLV_OK;
+  if (cudaMemsetAsync(p, 0, 256, s) != cudaSuccess) rc = SYLV_ERR_CUDA;
+  if (!rc) {
+    k_wait_nothing<<<1, 32, 0, s>>>(flag, ctrl, timeout_ms * 1000000LL);
+    Ctrl h{};
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&h, ctrl, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = SYLV_ERR_CUDA;
+    else
+      rc = h.err;
+  }
+  cudaFree(p);
+  return rc;
+}
+
+const char* sylv_error_string(int code) {
+  switch (code) {
+    case SYLV_OK: return "ok";
+    case SYLV_NEAR_SINGULAR: return "near-singular block system perturbed (lambda(A)+lambda(B) ~ 0)";
+    case SYLV_SCALE_UNDERFLOW: return "scale factor underflows double precision; use log2scale";
+    case SYLV_NOT_CONVERGED: return "FP32 + refinement did not reach the tolerance";
+    case SYLV_OVERFLOWED: return "non-robust solve overflowed (Inf/NaN in Y)";
+    case SYLV_ERR_STRUCTURE_A: return "A is not upper quasi-triangular (consecutive nonzero subdiagonal entries)";
+    case SYLV_ERR_STRUCTURE_B: return "B is not upper quasi-triangular (consecutive nonzero subdiagonal entries)";
+    case SYLV_ERR_NONFINITE: return "NaN or Inf in the input";
+    case SYLV_ERR_RANGE: return "an input tile's infinity norm exceeds Omega";
+    case SYLV_ERR_TIMEOUT: return "a device-side wait timed out";
+    case SYLV_ERR_CUDA: return "CUDA runtime error";
+    case SYLV_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case SYLV_ERR_UNSUPPORTED: return "unsupported option or size";
+    default: return code < 0 ? "invalid argument" : "unknown status";
+  }
+}
+
+size_t sylv_workspace_size(int64_t m, int64_t n, const sylv_opts* opts) {
+  Opts o{};
+  if (read_opts(opts, &o) || m < 0 || n < 0) return 0;
+  if (m == 0 || n == 0) return 0;
+  return plan_solve(m, n, o).total;
+}
+
+int sylv_tri_solve_ex(int64_t m, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                      int64_t ldc, const sylv_opts* opts, sylv_result* result) {
+  const int ac = check_args(m, n, A, lda, B, ldb, C, ldc);
+  if (ac) return ac;
+  Opts o{};
+  const int oc = read_opts(opts, &o);
+  if (oc) return oc;
+  if (o.sync) return solve_impl(m, n, A, lda, B, ldb, C, ldc, o, result, nullptr);
+  return solve_impl(m, n, A, lda, B, ldb, C, ldc, o, nullptr, result);
+}
+
+int sylv_tri_solve(int64_t m, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                   int64_t ldc, int64_t tile, double* scale) {
+  if (tile < 0 || tile == 1 || tile > 64) return -9;
+  sylv_opts op;
+  sylv_default_opts(&op);
+  op.tile = static_cast<int32_t>(tile);
+  sylv_result r{};
+  const int rc = sylv_tri_solve_ex(m, n, A, lda, B, ldb, C, ldc, &op, &r);
+  if (scale) *scale = r.scale;
+  return rc;
+}
+
+// ---------------------------------------------------------------- batched
+struct sylv_batch_plan {
+  int count = 0;
+  int tt = 32;
+  int precision = SYLV_FP64;
+  char* ws = nullptr;
+  Layout L{};
+  Work w{};
+  int64_t maxN = 0;
+  int pmax_all = 0;
+};
+
+int sylv_batch_create(sylv_batch_plan** plan, int32_t count, const int64_t* m, const int64_t* n,
+                      const double* const* A, const int64_t* lda, const double* const* B, const int64_t* ldb,
+                      double* const* C, const int64_t* ldc, const sylv_opts* opts) {
+  if (!plan) return -1;
+  *plan = nullptr;
+  if (count < 0) return -2;
+  if (count > 0 && (!m || !n || !A || !lda || !B || !ldb || !C || !ldc)) return -3;
+  Opts o{};
+  int rc = read_opts(opts, &o);
+  if (rc) return rc;
+  if (o.precision == SYLV_FP32_REFINE || o.transa || o.transb) return SYLV_ERR_UNSUPPORTED;
+  std::vector<Shape> sh;
+  std::vector<const void*> Av, Bv;
+  std::vector<void*> Cv;
+  std::vector<int64_t> la, lb, lc;
+  int64_t maxN = 0;
+  int pmax_all = 0, tt = 32;
+  for (int i = 0; i < count; ++i) {
+    rc = check_args(m[i], n[i], A[i], lda[i], B[i], ldb[i], C[i], ldc[i]);
+    if (rc) return rc;
+    const int t = o.tile ? o.tile : auto_tile(m[i], n[i]);
+    if (t > 32) tt = 64;
+    Shape s{m[i], n[i], t, tile_cap(m[i], t), tile_cap(n[i], t)};
+    sh.push_back(s);
+    Av.push_back(A[i]);
+    Bv.push_back(B[i]);
+    Cv.push_back(C[i]);
+    la.push_back(lda[i]);
+    lb.push_back(ldb[i]);
+    lc.push_back(ldc[i]);
+    maxN = std::max(maxN, std::max(m[i], n[i]));
+    pmax_all = std::max(pmax_all, std::max(s.pmax, s.qmax));
+  }
+  sylv_batch_plan* P = new (std::nothrow) sylv_batch_plan();
+  if (!P) return SYLV_ERR_CUDA;
+  P->count = count;
+  P->tt = tt;
+  P->precision = o.precision;
+  P->L = make_layout(sh, 0);
+  P->maxN = maxN;
+  P->pmax_all = pmax_all;
+  if (count > 0) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, P->L.total) != cudaSuccess) {
+      cudaGetLastError();
+      delete P;
+      return SYLV_ERR_CUDA;
+    }
+    P->ws = static_cast<char*>(p);
+    P->w = make_work(P->ws, P->L, count, o.timeout_ns);
+    std::vector<Inst> I = make_insts(sh, P->L, Av, la, Bv, lb, Cv, lc, o.precision == SYLV_FP64 ? 1 : 0, o.omega);
+    if (cudaMemcpy(P->w.inst, I.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(P->ws);
+      delete P;
+      return SYLV_ERR_CUDA;
+    }
+  }
+  *plan = P;
+  return SYLV_OK;
+}
+
+int sylv_batch_execute(sylv_batch_plan* P, void* stream) {
+  if (!P) return -1;
+  if (P->count == 0) return SYLV_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Layout& L = P->L;
+  if (cudaMemsetAsync(P->ws + L.zero_lo, 0, L.zero_hi - L.zero_lo, s) != cudaSuccess) return SYLV_ERR_CUDA;
+  cudaError_t e = run_prep<double>(P->w, L, P->count, P->maxN, P->pmax_all, s);
+  if (e != cudaSuccess) return SYLV_ERR_CUDA;
+  e = launch_dag_f64(P->tt, P->precision == SYLV_FP64, P->w, static_cast<int>(std::min<int64_t>(L.sum_tiles, 1 << 30)), s);
+  if (e != cudaSuccess) return SYLV_ERR_CUDA;
+  k_consistency<double><<<grid_for(L.sum_tiles * 256), 256, 0, s>>>(P->w);
+  k_results<<<(P->count + 255) / 256, 256, 0, s>>>(P->w);
+  return cuda_status(cudaGetLastError());
+}
+
+int sylv_batch_results(sylv_batch_plan* P, sylv_result* results) {
+  if (!P) return -1;
+  if (P->count == 0) return SYLV_OK;
+  if (!results) return -2;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SYLV_ERR_CUDA;
+  if (cudaMemcpy(results, P->w.res, sizeof(sylv_result) * P->count, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SYLV_ERR_CUDA;
+  int worst = SYLV_OK;
+  for (int i = 0; i < P->count; ++i)
+    if (results[i].info > worst) worst = results[i].info;
+  return worst >= 100 ? worst : SYLV_OK;
+}
+
+void sylv_batch_destroy(sylv_batch_plan* P) {
+  if (!P) return;
+  if (P->ws) cudaFree(P->ws);
+  delete P;
+}
+
+int sylv_tri_solve_batched(int32_t count, const int64_t* m, const int64_t* n, const double* const* A,
+                           const int64_t* lda, const double* const* B, const int64_t* ldb, double* const* C,
+                           const int64_t* ldc, const sylv_opts* opts, sylv_result* results) {
+  sylv_batch_plan* P = nullptr;
+  int rc = sylv_batch_create(&P, count, m, n, A, lda, B, ldb, C, ldc, opts);
+  if (rc) return rc;
+  rc = sylv_batch_execute(P, opts ? opts->stream : nullptr);
+  if (!rc) rc = sylv_batch_results(P, results);
+  sylv_batch_destroy(P);
+  return rc;
+}
+
+// ---------------------------------------------------------------- adjoint
+int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb,
+                            const double* Y, int64_t ldy, int64_t log2scale, double* G, int64_t ldg, double* dA,
+                            int64_t ldda, double* dB, int64_t lddb, const sylv_opts* opts, sylv_result* result) {
+  const int ac = check_args(m, n, A, lda, B, ldb, G, ldg);
+  if (ac) return ac;
+  if (m > 0 && n > 0 && !Y) return -7;
+  if (ldy < (m > 1 ? m : 1)) return -8;
+  if (dA && ldda < (m > 1 ? m : 1)) return -13;
+  if (dB && lddb < (n > 1 ? n : 1)) return -15;
+  Opts o{};
+  int rc = read_opts(opts, &o);
+  if (rc) return rc;
+  if (o.precision == SYLV_FP32_REFINE) o.precision = SYLV_FP64;
+  if (m == 0 || n == 0) {
+    if (result && o.sync) {
+      *result = sylv_result{};
+      result->scale = 1.0;
+    }
+    return SYLV_OK;
+  }
+  Opts oa = o;
+  oa.transa ^= 1;
+  oa.transb ^= 1;
+  const bool sync = o.sync != 0;
+  oa.sync = 0;
+  // The adjoint solve; its result stays on the device until the end.
+  const SolvePlan P = plan_solve(m, n, oa);
+  char* ws = nullptr;
+  if (oa.ws) {
+    if (oa.ws_bytes < P.total) return SYLV_ERR_WORKSPACE;
+    ws = static_cast<char*>(oa.ws);
+  } else {
+    void* p = nullptr;
+    rc = get_workspace(P.total, &p);
+    if (rc) return rc;
+    ws = static_cast<char*>(p);
+    oa.ws = p;
+    oa.ws_bytes = P.total;
+  }
+  rc = solve_impl(m, n, A, lda, B, ldb, G, ldg, oa, nullptr, nullptr);
+  if (rc) return rc;
+  cudaStream_t s = o.stream;
+  const int64_t e = log2scale;
+  // dA, dB from alpha_G * Gamma (G now), before G is turned into dL/dC.
+  if (dA) {
+    // op(A) = A: dA = -Gamma Y^T: P(i,c) = G[i + c ldg], Q(j,c) = Y[j + c ldy]
+    // op(A) = A^T: dA = -Y Gamma^T: P(i,c) = Y[i + c ldy], Q(j,c) = G[j + c ldg]
+    const double* Pp = o.transa ? Y : G;
+    const double* Qp = o.transa ? G : Y;
+    const int64_t lp = o.transa ? ldy : ldg, lq = o.transa ? ldg : ldy;
+    k_grad_product<<<dim3((m + GT - 1) / GT, (m + GT - 1) / GT), 256, 0, s>>>(Pp, 1, lp, Qp, 1, lq, m, n, A, lda,
+                                                                                dA, ldda);
+  }
+  if (dB) {
+    // op(B) = B: dB = -Y^T Gamma: P(i,r) = Y[r + i ldy], Q(j,r) = G[r + j ldg]
+    // op(B) = B^T: dB = -Gamma^T Y: P(i,r) = G[r + i ldg], Q(j,r) = Y[r + j ldy]
+    const double* Pp = o.transb ? G : Y;
+    const double* Qp = o.transb ? Y : G;
+    const int64_t lp = o.transb ? ldg : ldy, lq = o.transb ? ldy : ldg;
+    k_grad_product<<<dim3((n + GT - 1) / GT, (n + GT - 1) / GT), 256, 0, s>>>(Pp, lp, 1, Qp, lq, 1, n, m, B, ldb,
+                                                                                dB, lddb);
+  }
+  if (e != 0) k_scale_pow2<<<grid_for(m * n), 256, 0, s>>>(G, ldg, m, n, static_cast<int>(e));
+  if (cudaGetLastError() != cudaSuccess) return SYLV_ERR_CUDA;
+  sylv_result* res_dev = reinterpret_cast<sylv_result*>(ws + P.L.res);
+  if (sync) {
+    sylv_result r{};
+    if (cudaMemcpyAsync(&r, res_dev, sizeof(r), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SYLV_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SYLV_ERR_CUDA;
+    if (result) *result = r;
+    return r.info;
+  }
+  if (result && cudaMemcpyAsync(result, res_dev, sizeof(sylv_result), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return SYLV_ERR_CUDA;
+  return SYLV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,14 @@
+// sylv_dag_f32.cu -- FP32 instantiations of the tile-DAG kernel, used for the
+// correction solves of the FP32 + refinement mode (robust, with FP64 small
+// solves and FP64 bound arithmetic).
+#include "sylv_dag_common.cuh"
+#include "sylv_launch.h"
+
+namespace sylv {
+
+cudaError_t launch_dag_f32(int tt, const Work& w, int max_tasks, cudaStream_t stream) {
+  if (tt <= 32) return launch_dag_impl<32, float, true>(w, max_tasks, stream);
+  return launch_dag_impl<64, float, true>(w, max_tasks, stream);
+}
+
+}  // namespace sylv

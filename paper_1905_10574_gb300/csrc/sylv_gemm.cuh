@@ -1,0 +1,304 @@
+// sylv_gemm.cuh -- dense FP64 kernels around the solver: the residual
+// R = C - A X - X B of the refinement loop, the gradient products of the adjoint,
+// and the elementwise helpers of the FP32 + refinement mode.
+#pragma once
+
+#include "sylv_internal.cuh"
+
+namespace sylv {
+
+// Register-tiled FP64 tile: 64 x 64 outputs per CTA, 256 threads, 4 x 4 each,
+// k-chunks of 16 staged in shared memory (k-major rows, 16-byte aligned).
+constexpr int GT = 64, GK = 16, GLD = GT + 2;
+
+// R = C - A X - X B for upper quasi-triangular A (m x m), B (n x n): only A[r,c]
+// with r <= c+1 and B[r,c] with r <= c+1 take part (the entries the solver reads).
+// Also records max |R| (bit pattern of a non-negative double) in *rmax.
+// If *skip != 0 the kernel does nothing (the refinement has converged).
+__global__ void __launch_bounds__(256) k_residual(const double* __restrict__ A, int64_t lda,
+                                                  const double* __restrict__ B, int64_t ldb,
+                                                  const double* __restrict__ C, int64_t ldc,
+                                                  const double* __restrict__ X, int64_t ldx,
+                                                  double* __restrict__ R, int64_t ldr, int64_t m, int64_t n,
+                                                  unsigned long long* rmax, const int* skip) {
+  if (skip && ld_volatile(skip)) return;
+  __shared__ __align__(16) double Ls[GK * GLD];
+  __shared__ __align__(16) double Rs[GK * GLD];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * GT, j0 = static_cast<int64_t>(blockIdx.y) * GT;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t r = i0 + tx * 4 + i, c = j0 + ty * 4 + j;
+      acc[i][j] = (r < m && c < n) ? C[r + c * ldc] : 0.0;
+    }
+  // A X: k runs over columns of A that rows i0.. can touch: k >= i0 - 1.
+  const int64_t ka = i0 > 0 ? i0 - 1 : 0;
+  for (int64_t k0 = ka; k0 < m; k0 += GK) {
+    for (int idx = tid; idx < GK * GT; idx += 256) {
+      const int r = idx % GT, kk = idx / GT;
+      const int64_t gr = i0 + r, gk = k0 + kk;
+      Ls[kk * GLD + r] = (gr < m && gk < m && gr <= gk + 1) ? A[gr + gk * lda] : 0.0;
+      const int kk2 = idx % GK, c = idx / GK;
+      const int64_t gk2 = k0 + kk2, gc = j0 + c;
+      Rs[kk2 * GLD + c] = (gk2 < m && gc < n) ? X[gk2 + gc * ldx] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = Ls[kk * GLD + tx * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Rs[kk * GLD + ty * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(-a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  // X B: k runs over rows of B that columns j0.. can touch: k <= j0 + GT.
+  const int64_t kb_end = (j0 + GT + 1 < n) ? j0 + GT + 1 : n;
+  for (int64_t k0 = 0; k0 < kb_end; k0 += GK) {
+    for (int idx = tid; idx < GK * GT; idx += 256) {
+      const int r = idx % GT, kk = idx / GT;
+      const int64_t gr = i0 + r, gk = k0 + kk;
+      Ls[kk * GLD + r] = (gr < m && gk < n) ? X[gr + gk * ldx] : 0.0;
+      const int kk2 = idx % GK, c = idx / GK;
+      const int64_t gk2 = k0 + kk2, gc = j0 + c;
+      Rs[kk2 * GLD + c] = (gk2 < n && gc < n && gk2 <= gc + 1) ? B[gk2 + gc * ldb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = Ls[kk * GLD + tx * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Rs[kk * GLD + ty * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(-a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double mx = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t r = i0 + tx * 4 + i, c = j0 + ty * 4 + j;
+      if (r < m && c < n) {
+        R[r + c * ldr] = acc[i][j];
+        mx = fmax(mx, fabs(acc[i][j]));
+      }
+    }
+  mx = warp_max(mx);
+  if ((tid & 31) == 0 && rmax) atomic_max_nonneg(rmax, mx);
+}
+
+// D = -P Q^T-like products for the adjoint: D[i,j] = -sum_c P(i,c) Q(j,c) with
+// P(i,c) = P[i*psi + c*psc], Q(j,c) = Q[j*qsj + c*qsc] (element strides, so the
+// same kernel serves Gamma Y^T, Y Gamma^T, Y^T Gamma and Gamma^T Y), masked to
+// the entries a quasi-triangular operand T (N x N, ldt) exposes: i <= j, or
+// i == j + 1 with T[i, j] != 0.  Other entries of D are set to 0.
+__global__ void __launch_bounds__(256) k_grad_product(const double* __restrict__ P, int64_t psi, int64_t psc,
+                                                      const double* __restrict__ Q, int64_t qsj, int64_t qsc,
+                                                      int64_t N, int64_t K, const double* __restrict__ T,
+                                                      int64_t ldt, double* __restrict__ D, int64_t ldd) {
+  __shared__ __align__(16) double Ls[GK * GLD];
+  __shared__ __align__(16) double Rs[GK * GLD];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * GT, j0 = static_cast<int64_t>(blockIdx.y) * GT;
+  const bool active = i0 <= j0 + GT;  // tile touches the upper quasi-triangle
+  double acc[4][4] = {};
+  if (active) {
+    for (int64_t k0 = 0; k0 < K; k0 += GK) {
+      for (int idx = tid; idx < GK * GT; idx += 256) {
+        const int r = idx % GT, kk = idx / GT;
+        const int64_t gi = i0 + r, gk = k0 + kk;
+        Ls[kk * GLD + r] = (gi < N && gk < K) ? P[gi * psi + gk * psc] : 0.0;
+        const int64_t gj = j0 + r;
+        Rs[kk * GLD + r] = (gj < N && gk < K) ? Q[gj * qsj + gk * qsc] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < GK; ++kk) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = Ls[kk * GLD + tx * 4 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Rs[kk * GLD + ty * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(-a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t r = i0 + tx * 4 + i, c = j0 + ty * 4 + j;
+      if (r < N && c < N) {
+        const bool keep = (r <= c) || (r == c + 1 && T[r + c * ldt] != 0.0);
+        D[r + c * ldd] = keep ? acc[i][j] : 0.0;
+      }
+    }
+}
+
+// ---------------------------------------------------------------- refinement helpers
+// max |T[r,c]| over the quasi-triangular part (r <= c+1) of an N x N matrix.
+__global__ void k_maxabs_quasi(const double* __restrict__ T, int64_t ldt, int64_t N, unsigned long long* out) {
+  double mx = 0.0;
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < N * N;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t % N, c = t / N;
+    if (r <= c + 1) mx = fmax(mx, fabs(T[r + c * ldt]));
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, mx);
+}
+
+// Exponent s with max|.| * 2^-s in [1, 2): s = floor(log2(max)), 0 for a zero max.
+__device__ __forceinline__ int norm_exp(const unsigned long long* slot) {
+  const double v = __longlong_as_double(static_cast<long long>(*slot));
+  return (v > 0.0 && v <= 1.7976931348623157e308) ? floor_log2(v) : 0;
+}
+
+// dst (float) = src * 2^-s, s from the larger of slot_a/slot_b (null = 0);
+// quasi != 0 keeps only r <= c+1 (other entries 0).
+__global__ void k_to_float(const double* __restrict__ src, int64_t lds, float* __restrict__ dst, int64_t ldd,
+                           int64_t rows, int64_t cols, const unsigned long long* slot_a,
+                           const unsigned long long* slot_b, int quasi, const int* skip) {
+  if (skip && ld_volatile(skip)) return;
+  int s = 0;
+  if (slot_a) {
+    const unsigned long long a = *slot_a, b = slot_b ? *slot_b : 0ull;
+    s = norm_exp(a > b ? slot_a : slot_b);
+  }
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < rows * cols;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t % rows, c = t / rows;
+    const double v = (!quasi || r <= c + 1) ? src[r + c * lds] : 0.0;
+    dst[r + c * ldd] = static_cast<float>(mul2(v, -s));
+  }
+}
+
+// R = C (first refinement right-hand side, X = 0) and max |C|.
+__global__ void k_copy_max(const double* __restrict__ C, int64_t ldc, double* __restrict__ R, int64_t ldr,
+                           int64_t m, int64_t n, unsigned long long* rmax) {
+  double mx = 0.0;
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < m * n;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t % m, c = t / m;
+    const double v = C[r + c * ldc];
+    R[r + c * ldr] = v;
+    mx = fmax(mx, fabs(v));
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(rmax, mx);
+}
+
+// X += D where the FP32 correction solve left tile (k,l) of D' = 2^(sa-sr) D as
+// 2^e_kl-scaled floats in Rf: D = Rf * 2^(sr - sa - e_kl).  Records max|D|, max|X|.
+__global__ void k_accumulate(Work wf, double* __restrict__ X, int64_t ldx, const unsigned long long* slot_r,
+                             const unsigned long long* slot_a, const unsigned long long* slot_b,
+                             unsigned long long* dmax, unsigned long long* xmax, const int* skip) {
+  if (skip && ld_volatile(skip)) return;
+  const int sr = norm_exp(slot_r);
+  const unsigned long long a = *slot_a, b = *slot_b;
+  const int sa = norm_exp(a > b ? slot_a : slot_b);
+  const int ntasks = wf.ctrl->ntasks;
+  double md = 0.0, mxv = 0.0;
+  for (int idx = blockIdx.x; idx < ntasks; idx += gridDim.x) {
+    const Task tk = wf.tasks[idx];
+    const Inst I = wf.inst[tk.inst];
+    const int e = wf.texp[I.tile + tk.tile];
+    const int k = tk.tile / I.qmax, l = tk.tile % I.qmax;
+    const int32_t* rb = wf.ibuf + I.rb;
+    const int32_t* cb = wf.ibuf + I.cb;
+    const int r0 = rb[k], mt = rb[k + 1] - r0, c0 = cb[l], nt = cb[l + 1] - c0;
+    const float* Rf = static_cast<const float*>(I.C);
+    for (int i = threadIdx.x; i < mt * nt; i += blockDim.x) {
+      const int64_t r = r0 + i % mt, c = c0 + i / mt;
+      const double dv = mul2(static_cast<double>(Rf[r + c * I.ldc]), sr - sa - e);
+      const double xv = X[r + c * ldx] + dv;
+      X[r + c * ldx] = xv;
+      md = fmax(md, fabs(dv));
+      mxv = fmax(mxv, fabs(xv));
+    }
+  }
+  md = warp_max(md);
+  mxv = warp_max(mxv);
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(dmax, md);
+    atomic_max_nonneg(xmax, mxv);
+  }
+}
+
+// After correction `it`: converged when max|D| <= tol * max|X| (or the FP32
+// solve failed).  Updates the iteration count and the last ratio.
+struct RefineState {
+  int conv;
+  int iters;
+  int err;
+  int pad;
+  double last;
+};
+__global__ void k_refine_check(RefineState* rs, const unsigned long long* dmax, const unsigned long long* xmax,
+                               double tol, const Work wf) {
+  if (rs->conv) return;
+  const double d = __longlong_as_double(static_cast<long long>(*dmax));
+  const double x = __longlong_as_double(static_cast<long long>(*xmax));
+  rs->iters += 1;
+  rs->last = (x > 0.0) ? d / x : (d > 0.0 ? 1.0 : 0.0);
+  int e = wf.ctrl->err ? wf.ctrl->err : wf.st[0].err;
+  if (e) {
+    rs->err = e;
+    rs->conv = 1;
+  } else if (!(d <= tol * x)) {
+    rs->conv = 0;
+  } else {
+    rs->conv = 1;
+  }
+}
+
+__global__ void k_refine_result(const RefineState* rs, sylv_result* res, int maxit) {
+  sylv_result r;
+  r.log2scale = 0;
+  r.scale = 1.0;
+  r.iters = rs->iters;
+  r.last_update = rs->last;
+  r.scale_events = 0;
+  r.min_tile_exp = 0;
+  r.info = rs->err ? rs->err : (rs->conv ? SYLV_OK : SYLV_NOT_CONVERGED);
+  *res = r;
+}
+
+// Y (m x n, ldy) <- X.
+__global__ void k_copy(const double* __restrict__ X, int64_t ldx, double* __restrict__ Y, int64_t ldy, int64_t m,
+                       int64_t n) {
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < m * n;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t % m, c = t / m;
+    Y[r + c * ldy] = X[r + c * ldx];
+  }
+}
+
+// M *= 2^e (in place).
+__global__ void k_scale_pow2(double* M, int64_t ld, int64_t m, int64_t n, int e) {
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < m * n;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t % m, c = t / m;
+    M[r + c * ld] = mul2(M[r + c * ld], e);
+  }
+}
+
+}  // namespace sylv

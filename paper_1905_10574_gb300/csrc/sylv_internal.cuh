@@ -1,0 +1,229 @@
+// sylv_internal.cuh -- device-side data structures and helpers shared by the
+// kernels of the GB300 triangular Sylvester solver (C ABI in include/sylv.h).
+//
+// Method: Schwarz & Kjelgaard Mikkelsen 2019, "Robust Task-Parallel Solution of
+// the Triangular Sylvester Equation".  Tiles of Y are augmented tiles <alpha, X>
+// (Sec. 2.2, Def. 1) whose scale alpha = 2^e is kept as an integer exponent e <= 0.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sylv.h"
+
+namespace sylv {
+
+constexpr int kThreads = 256;  // threads per CTA of every tile kernel
+
+// Per-equation status bits (InstState::flags).
+constexpr int kFlagNearSingular = 1;  // a small system's pivot was raised to smin
+constexpr int kFlagNonfiniteOut = 2;  // a solved tile holds Inf/NaN (non-robust overflow)
+
+// One equation of a (possibly batched) solve.  Element type of A, B, C is the
+// kernel's T (double for the FP64 paths, float for the FP32 correction solves).
+struct Inst {
+  int64_t m, n;
+  int64_t lda, ldb, ldc;
+  const void* A;
+  const void* B;
+  void* C;
+  int32_t t;           // nominal tile size
+  int32_t pmax, qmax;  // capacity of the tile arrays (>= actual tile counts)
+  int32_t robust;      // 1: Algorithm 4 with scaling; 0: no scaling (Algorithm 1 per tile)
+  int64_t rb, cb;      // offsets (ints) of the row/column tile boundaries in Work::ibuf
+  int64_t tile;        // offset (elements) of this equation's per-tile arrays
+  int64_t an, bn;      // offsets (doubles) of the tile-norm tables in Work::dbuf
+  double omega;        // overflow threshold
+};
+
+// Per-equation results and bookkeeping, written by the kernels.
+struct InstState {
+  int32_t p, q;        // actual tile counts
+  int32_t minexp;      // min over tiles of the local exponent (atomicMin)
+  int32_t flags;       // kFlag* bits (atomicOr)
+  int32_t err;         // first SYLV_ERR_* of this equation (atomicCAS from 0)
+  int32_t nscale;      // scaling decisions taken (atomicAdd)
+  unsigned long long amax, bmax;  // max |A|, |B| as binary64 bit patterns (atomicMax)
+  double smin;         // pivot floor of the small solves
+};
+
+struct Task {
+  int32_t inst;
+  int32_t tile;  // k * qmax + l
+};
+
+struct Ctrl {
+  int32_t ticket;   // next task of the persistent kernel
+  int32_t ntasks;   // tasks in Work::tasks
+  int32_t err;      // first launch-wide error (timeout)
+  int32_t nlevels;  // anti-diagonal levels in use
+};
+
+struct Work {
+  Inst* inst;
+  InstState* st;
+  int32_t count;        // equations
+  int32_t nlevels_max;  // capacity of the level arrays
+  Task* tasks;
+  Ctrl* ctrl;
+  int32_t* lvl_cnt;
+  int32_t* lvl_off;
+  int32_t* lvl_cur;
+  int32_t* ibuf;    // tile boundaries
+  int32_t* texp;    // local exponent per tile
+  int32_t* tflag;   // 1 once a tile is final (release/acquire)
+  double* tnorm;    // infinity norm of each final tile (as stored, i.e. scaled)
+  double* dbuf;     // off-diagonal tile norms of A and B
+  sylv_result* res; // per-equation results
+  const int* skip;  // if non-null and nonzero, the DAG kernel returns at once
+  int64_t timeout_ns;
+  int32_t max_tiles;  // max over equations of pmax * qmax
+  int32_t pad;
+};
+
+// ---------------------------------------------------------------- power-of-two scaling
+// 2^e as binary64 for e in [-1022, 1023]: biased exponent e + 1023, zero fraction.
+__device__ __forceinline__ double pow2d(int e) {
+  return __longlong_as_double(static_cast<long long>(e + 1023) << 52);
+}
+// 2^e as binary32 for e in [-126, 127].
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+// x * 2^e: exact whenever the result is a normal number (multiplication by a power
+// of two only changes the exponent); very negative e is applied in normal-range steps.
+__device__ __forceinline__ double mul2(double x, int e) {
+  if (e == 0) return x;
+  if (e < -2200) return x * 0.0;
+  while (e < -1022) {
+    x *= pow2d(-1022);
+    e += 1022;
+  }
+  while (e > 1023) {
+    x *= pow2d(1023);
+    e -= 1023;
+  }
+  return x * pow2d(e);
+}
+__device__ __forceinline__ float mul2(float x, int e) {
+  if (e == 0) return x;
+  if (e < -400) return x * 0.0f;
+  while (e < -126) {
+    x *= pow2f(-126);
+    e += 126;
+  }
+  while (e > 127) {
+    x *= pow2f(127);
+    e -= 127;
+  }
+  return x * pow2f(e);
+}
+
+// floor(log2 x) for finite x > 0, from the binary64 exponent field (subnormals via
+// the position of the leading fraction bit).
+__device__ __forceinline__ int floor_log2(double x) {
+  const long long b = __double_as_longlong(x);
+  const int be = static_cast<int>((b >> 52) & 0x7ff);
+  if (be) return be - 1023;
+  const long long frac = b & 0xFFFFFFFFFFFFFLL;
+  return (63 - __clzll(frac)) - 1074;
+}
+// ceil(log2 x) for finite x > 0.
+__device__ __forceinline__ int ceil_log2(double x) {
+  const long long b = __double_as_longlong(x);
+  const int be = static_cast<int>((b >> 52) & 0x7ff);
+  const long long frac = b & 0xFFFFFFFFFFFFFLL;
+  if (be) return frac ? be - 1022 : be - 1023;
+  const int f = (63 - __clzll(frac)) - 1074;
+  return (__popcll(frac) == 1) ? f : f + 1;
+}
+
+// ProtectUpdate (Sec. 2.1).  c, t, x are upper bounds of ||C||, ||A||, ||Y|| in
+// [0, omega]; returns z <= 0 such that 2^z (c + t x) <= omega holds exactly.  The
+// factor is the largest power of two the bound allows (up to rounding):
+// z = -ceil(log2 u), u = (c + t x)/omega computed as c/omega + (t/omega) x -- omega
+// is a power of two, so the quotients are exact and the sum cannot overflow --
+// and enlarged by 2^-50 to absorb the two roundings.  A cheaper test first
+// returns 0 when c + t x <= omega holds with a four-ulp margin.
+__device__ __forceinline__ int protect_update(double c, double t, double x, double omega) {
+  const double shrink = 1.0 - 0x1p-51;
+  if (t == 0.0 || x == 0.0) return 0;
+  if (x <= 1.0) {
+    const double lim = (omega - c) * shrink;
+    if (lim > 0.0 && t * x <= lim) return 0;
+  } else if (t <= ((omega - c) / x) * shrink) {
+    return 0;
+  }
+  const double u = c / omega + (t / omega) * x;
+  const int z = -ceil_log2(u * (1.0 + 0x1p-50));
+  return z < 0 ? z : 0;
+}
+
+// ProtectDivision (Sec. 2.1) for |b| <= omega and divisor magnitude d > 0: returns
+// z <= 0 with 2^z |b| / d <= omega, the largest such power of two.  d*omega and
+// |b|*2^z are exact (omega is a power of two), so the estimate from the rounded
+// quotient is corrected by exact comparisons.
+__device__ __forceinline__ int protect_division(double b, double d, double omega) {
+  b = fabs(b);
+  d = fabs(d);
+  if (d < 1.0 && b > d * omega) {
+    const double lim = d * omega;
+    int z = floor_log2(lim / b);
+    while (z < 0 && mul2(b, z + 1) <= lim) ++z;
+    while (mul2(b, z) > lim) --z;
+    return z;
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------- inter-CTA signalling
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+// Wait (thread-level) until *flag != 0.  Bounded: gives up after timeout_ns of
+// global time or as soon as another CTA has recorded a launch-wide error, and
+// then records SYLV_ERR_TIMEOUT (first error wins) and returns false.
+__device__ __forceinline__ bool wait_flag(const int* flag, Ctrl* ctrl, long long timeout_ns) {
+  if (ld_acquire(flag)) return true;
+  const unsigned long long t0 = global_ns();
+  unsigned ns = 32;
+  for (;;) {
+    __nanosleep(ns);
+    if (ns < 512) ns <<= 1;
+    if (ld_acquire(flag)) return true;
+    if (ld_volatile(&ctrl->err)) return false;
+    if (static_cast<long long>(global_ns() - t0) > timeout_ns) {
+      atomicCAS(&ctrl->err, 0, SYLV_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+// Non-negative doubles order like their bit patterns (NaN above +Inf).
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* p, double v) {
+  atomicMax(p, static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_min(int v) {
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ void set_err(InstState* st, int code) { atomicCAS(&st->err, 0, code); }
+
+}  // namespace sylv

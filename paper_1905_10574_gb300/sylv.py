@@ -1,0 +1,373 @@
+"""Thin Python binding of the CUDA library (C ABI of include/sylv.h).
+
+Functions named like the C entry points (``sylv_tri_solve``, ``sylv_tri_solve_ex``,
+``sylv_tri_solve_batched``, ``sylv_batch_*``, ``sylv_tri_solve_backward``,
+``sylv_workspace_size``, ``sylv_error_string``) only marshal arguments: device
+pointers, sizes, options.  Every step of the solve runs in the library's CUDA
+kernels.  ``solve``/``batch_solve``/``SylvesterSolve`` are conveniences on torch
+CUDA tensors (float64); they lay matrices out column-major, allocate the
+workspace through torch (so calls can be captured in CUDA graphs) and call the
+same entry points.  There is no CPU path: if the library is missing, loading
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libsylv.so")
+
+SYLV_OK = 0
+SYLV_NEAR_SINGULAR = 1
+SYLV_SCALE_UNDERFLOW = 2
+SYLV_NOT_CONVERGED = 3
+SYLV_OVERFLOWED = 4
+SYLV_ERR_STRUCTURE_A = 101
+SYLV_ERR_STRUCTURE_B = 102
+SYLV_ERR_NONFINITE = 103
+SYLV_ERR_RANGE = 104
+SYLV_ERR_TIMEOUT = 105
+SYLV_ERR_CUDA = 106
+SYLV_ERR_WORKSPACE = 107
+SYLV_ERR_UNSUPPORTED = 108
+
+SYLV_FP64 = 0
+SYLV_FP64_NONROBUST = 1
+SYLV_FP32_REFINE = 2
+PRECISIONS = {"fp64": SYLV_FP64, "fp64_nonrobust": SYLV_FP64_NONROBUST, "fp32_refine": SYLV_FP32_REFINE}
+
+
+class sylv_opts(ctypes.Structure):
+    _fields_ = [("transa", ctypes.c_int32), ("transb", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("omega", ctypes.c_double), ("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int32), ("sync", ctypes.c_int32), ("timeout_ms", ctypes.c_int64),
+                ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+class sylv_result(ctypes.Structure):
+    _fields_ = [("log2scale", ctypes.c_int64), ("scale", ctypes.c_double), ("info", ctypes.c_int32),
+                ("iters", ctypes.c_int32), ("last_update", ctypes.c_double),
+                ("scale_events", ctypes.c_int32), ("min_tile_exp", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# Every symbol include/sylv.h declares, with its ctypes signature.
+_i64, _i32, _pd, _vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p
+_P64 = ctypes.POINTER(ctypes.c_int64)
+_PP = ctypes.POINTER(ctypes.c_void_p)
+SIGNATURES = {
+    "sylv_default_opts": (None, [ctypes.POINTER(sylv_opts)]),
+    "sylv_tri_solve": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _i64,
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "sylv_tri_solve_ex": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, _pd, _i64,
+                                         ctypes.POINTER(sylv_opts), _vp]),
+    "sylv_workspace_size": (ctypes.c_size_t, [_i64, _i64, ctypes.POINTER(sylv_opts)]),
+    "sylv_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _i32, _P64, _P64, _PP, _P64, _PP,
+                                         _P64, _PP, _P64, ctypes.POINTER(sylv_opts)]),
+    "sylv_batch_execute": (ctypes.c_int, [_vp, _vp]),
+    "sylv_batch_results": (ctypes.c_int, [_vp, ctypes.POINTER(sylv_result)]),
+    "sylv_batch_destroy": (None, [_vp]),
+    "sylv_tri_solve_batched": (ctypes.c_int, [_i32, _P64, _P64, _PP, _P64, _PP, _P64, _PP, _P64,
+                                              ctypes.POINTER(sylv_opts), ctypes.POINTER(sylv_result)]),
+    "sylv_tri_solve_backward": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _i64, _pd, _i64,
+                                               _pd, _i64, _pd, _i64, ctypes.POINTER(sylv_opts), _vp]),
+    "sylv_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "sylv_version": (ctypes.c_char_p, []),
+    "sylv_diag_wait_timeout": (ctypes.c_int, [_i64, _vp]),
+    "sylv_profile": (ctypes.c_int, [ctypes.c_int]),
+    "sylv_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libsylv.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"CUDA library not built: {p} (run paper_1905_10574_gb300.build)")
+    L = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+class SylvError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {code} ({sylv_error_string(code)})")
+
+
+# ------------------------------------------------------------------ C-ABI mirrors
+def sylv_default_opts() -> sylv_opts:
+    o = sylv_opts()
+    load().sylv_default_opts(ctypes.byref(o))
+    return o
+
+
+def sylv_error_string(code: int) -> str:
+    return load().sylv_error_string(int(code)).decode()
+
+
+def sylv_version() -> str:
+    return load().sylv_version().decode()
+
+
+def sylv_diag_wait_timeout(timeout_ms: int, stream=None) -> int:
+    return load().sylv_diag_wait_timeout(int(timeout_ms), stream)
+
+
+def sylv_profile(enable: bool) -> int:
+    return load().sylv_profile(int(bool(enable)))
+
+
+def sylv_profile_read():
+    """(summed DAG-kernel milliseconds, launches) since the last read."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    rc = load().sylv_profile_read(ctypes.byref(ms), ctypes.byref(n))
+    if rc != 0:
+        raise SylvError(rc, "sylv_profile_read")
+    return ms.value, n.value
+
+
+def sylv_tri_solve(m, n, A, lda, B, ldb, C, ldc, tile=0):
+    """Device pointers (ints); returns (status, scale)."""
+    sc = ctypes.c_double(0.0)
+    rc = load().sylv_tri_solve(m, n, A, lda, B, ldb, C, ldc, tile, ctypes.byref(sc))
+    return rc, sc.value
+
+
+def sylv_tri_solve_ex(m, n, A, lda, B, ldb, C, ldc, opts: sylv_opts | None = None, result=None):
+    """Device pointers (ints).  ``result``: a sylv_result (host, sync mode) or a device
+    address (async mode).  Returns the status code."""
+    o = opts if opts is not None else sylv_default_opts()
+    if isinstance(result, sylv_result):
+        res = ctypes.cast(ctypes.pointer(result), ctypes.c_void_p)
+    else:
+        res = result
+    return load().sylv_tri_solve_ex(m, n, A, lda, B, ldb, C, ldc, ctypes.byref(o), res)
+
+
+def sylv_workspace_size(m, n, opts: sylv_opts | None = None) -> int:
+    o = opts if opts is not None else sylv_default_opts()
+    return int(load().sylv_workspace_size(m, n, ctypes.byref(o)))
+
+
+def _i64arr(v):
+    return (ctypes.c_int64 * len(v))(*[int(x) for x in v])
+
+
+def _ptrarr(v):
+    return (ctypes.c_void_p * len(v))(*[int(x) for x in v])
+
+
+def sylv_batch_create(m, n, A, lda, B, ldb, C, ldc, opts: sylv_opts | None = None):
+    """Lists of sizes and device pointers; returns an opaque plan handle."""
+    o = opts if opts is not None else sylv_default_opts()
+    h = ctypes.c_void_p()
+    cnt = len(m)
+    rc = load().sylv_batch_create(ctypes.byref(h), cnt, _i64arr(m), _i64arr(n), _ptrarr(A), _i64arr(lda),
+                                  _ptrarr(B), _i64arr(ldb), _ptrarr(C), _i64arr(ldc), ctypes.byref(o))
+    if rc != 0:
+        raise SylvError(rc, "sylv_batch_create")
+    return h
+
+
+def sylv_batch_execute(plan, stream=None) -> int:
+    return load().sylv_batch_execute(plan, stream)
+
+
+def sylv_batch_results(plan, count: int):
+    arr = (sylv_result * max(count, 1))()
+    rc = load().sylv_batch_results(plan, arr)
+    return rc, [arr[i] for i in range(count)]
+
+
+def sylv_batch_destroy(plan) -> None:
+    load().sylv_batch_destroy(plan)
+
+
+def sylv_tri_solve_batched(m, n, A, lda, B, ldb, C, ldc, opts: sylv_opts | None = None):
+    o = opts if opts is not None else sylv_default_opts()
+    cnt = len(m)
+    arr = (sylv_result * max(cnt, 1))()
+    rc = load().sylv_tri_solve_batched(cnt, _i64arr(m), _i64arr(n), _ptrarr(A), _i64arr(lda), _ptrarr(B),
+                                       _i64arr(ldb), _ptrarr(C), _i64arr(ldc), ctypes.byref(o), arr)
+    return rc, [arr[i] for i in range(cnt)]
+
+
+def sylv_tri_solve_backward(m, n, A, lda, B, ldb, Y, ldy, log2scale, G, ldg, dA, ldda, dB, lddb,
+                            opts: sylv_opts | None = None, result=None):
+    o = opts if opts is not None else sylv_default_opts()
+    if isinstance(result, sylv_result):
+        res = ctypes.cast(ctypes.pointer(result), ctypes.c_void_p)
+    else:
+        res = result
+    return load().sylv_tri_solve_backward(m, n, A, lda, B, ldb, Y, ldy, log2scale, G, ldg, dA or None, ldda,
+                                          dB or None, lddb, ctypes.byref(o), res)
+
+
+# ------------------------------------------------------------------ torch conveniences
+def _torch():
+    import torch
+    return torch
+
+
+def fortran(t):
+    """Column-major (Fortran-ordered) float64 copy/view of a 2-D tensor."""
+    torch = _torch()
+    t = t.to(torch.float64)
+    if t.dim() != 2:
+        raise ValueError("expected a matrix")
+    r, c = t.shape
+    if t.stride(0) == 1 and (t.stride(1) >= max(r, 1) or c <= 1):
+        return t
+    return t.t().contiguous().t()
+
+
+def empty_fortran(m, n, device, dtype=None):
+    torch = _torch()
+    return torch.empty((n, m), dtype=dtype or torch.float64, device=device).t()
+
+
+def _ld(t) -> int:
+    return max(int(t.stride(1)) if t.shape[1] > 1 else int(t.shape[0]), 1)
+
+
+@dataclass
+class Result:
+    log2scale: int
+    scale: float
+    info: int
+    iters: int
+    last_update: float
+    scale_events: int
+    min_tile_exp: int
+
+
+def make_opts(*, transa=False, transb=False, precision="fp64", tile=0, omega=0.0, tol=0.0, maxit=0,
+              timeout_ms=0, stream=None, sync=True) -> sylv_opts:
+    o = sylv_default_opts()
+    o.transa = int(bool(transa))
+    o.transb = int(bool(transb))
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.tile = int(tile)
+    o.omega = float(omega)
+    o.tol = float(tol)
+    o.maxit = int(maxit)
+    o.timeout_ms = int(timeout_ms)
+    o.stream = stream
+    o.sync = int(bool(sync))
+    return o
+
+
+def solve(A, B, C, *, transa=False, transb=False, precision="fp64", tile=0, omega=0.0, tol=0.0, maxit=0,
+          timeout_ms=0, inplace=False, check=True):
+    """Solve op(A) Y + Y op(B) = alpha C for CUDA float64 tensors; returns (Y, Result).
+    Y is column-major; with inplace=True and a column-major C, C itself is overwritten."""
+    torch = _torch()
+    A = fortran(A)
+    B = fortran(B)
+    Cf = fortran(C)
+    Y = Cf if (inplace or Cf.data_ptr() != C.data_ptr()) else Cf.clone()
+    m, n = Y.shape
+    stream = torch.cuda.current_stream(Y.device).cuda_stream
+    o = make_opts(transa=transa, transb=transb, precision=precision, tile=tile, omega=omega, tol=tol,
+                  maxit=maxit, timeout_ms=timeout_ms, stream=stream, sync=True)
+    ws_bytes = sylv_workspace_size(m, n, o)
+    ws = torch.empty(max(ws_bytes, 1) + 256, dtype=torch.uint8, device=Y.device)
+    base = (ws.data_ptr() + 255) // 256 * 256
+    o.workspace = base
+    o.workspace_bytes = ws_bytes
+    res = sylv_result()
+    rc = sylv_tri_solve_ex(m, n, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), Y.data_ptr(), _ld(Y), o, res)
+    if check and (rc >= 100 or rc < 0):
+        raise SylvError(rc, "sylv_tri_solve_ex")
+    return Y, Result(**res.as_dict())
+
+
+def batch_solve(As, Bs, Cs, *, tile=0, precision="fp64", timeout_ms=0):
+    """Solve a list of equations in one batched launch; Cs are overwritten when they are
+    column-major float64 CUDA tensors, else copies are solved.  Returns (Ys, [Result])."""
+    torch = _torch()
+    As = [fortran(a) for a in As]
+    Bs = [fortran(b) for b in Bs]
+    Ys = [fortran(c) for c in Cs]
+    o = make_opts(tile=tile, precision=precision, timeout_ms=timeout_ms,
+                  stream=torch.cuda.current_stream().cuda_stream)
+    plan = sylv_batch_create([y.shape[0] for y in Ys], [y.shape[1] for y in Ys], [a.data_ptr() for a in As],
+                             [_ld(a) for a in As], [b.data_ptr() for b in Bs], [_ld(b) for b in Bs],
+                             [y.data_ptr() for y in Ys], [_ld(y) for y in Ys], o)
+    try:
+        rc = sylv_batch_execute(plan, o.stream)
+        if rc != 0:
+            raise SylvError(rc, "sylv_batch_execute")
+        rc, res = sylv_batch_results(plan, len(Ys))
+        if rc >= 100:
+            raise SylvError(rc, "sylv_batch_results")
+    finally:
+        sylv_batch_destroy(plan)
+    return Ys, [Result(**r.as_dict()) for r in res]
+
+
+class SylvesterSolve:
+    """torch.autograd.Function: Y = solve(A, B, C) (robust FP64, alpha held fixed), with the
+    hand-written adjoint of sylv_tri_solve_backward.  Use ``SylvesterSolve.apply(A, B, C,
+    transa, transb, tile)``; passing one tensor as both A and B (with transb=True) gives the
+    Lyapunov form A Y + Y A^T = C and autograd adds both gradient contributions."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, A, B, C, transa=False, transb=False, tile=0):
+        if cls._fn is None:
+            cls._fn = _make_autograd_fn()
+        return cls._fn.apply(A, B, C, transa, transb, tile)
+
+
+def _make_autograd_fn():
+    torch = _torch()
+
+    class _Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, A, B, C, transa, transb, tile):
+            Y, res = solve(A.detach(), B.detach(), C.detach(), transa=transa, transb=transb, tile=tile)
+            ctx.save_for_backward(A, B, Y)
+            ctx.cfg = (transa, transb, tile, res.log2scale)
+            return Y
+
+        @staticmethod
+        def backward(ctx, gY):
+            A, B, Y = ctx.saved_tensors
+            transa, transb, tile, e = ctx.cfg
+            Af, Bf = fortran(A.detach()), fortran(B.detach())
+            G = fortran(gY.detach()).clone()
+            m, n = G.shape
+            dA = empty_fortran(m, m, G.device)
+            dB = empty_fortran(n, n, G.device)
+            o = make_opts(transa=transa, transb=transb, tile=tile,
+                          stream=torch.cuda.current_stream(G.device).cuda_stream)
+            res = sylv_result()
+            rc = sylv_tri_solve_backward(m, n, Af.data_ptr(), _ld(Af), Bf.data_ptr(), _ld(Bf), Y.data_ptr(),
+                                         _ld(Y), int(e), G.data_ptr(), _ld(G), dA.data_ptr(), _ld(dA),
+                                         dB.data_ptr(), _ld(dB), o, res)
+            if rc >= 100 or rc < 0:
+                raise SylvError(rc, "sylv_tri_solve_backward")
+            if res.log2scale != 0:  # undo the adjoint solve's own scaling
+                s = 2.0 ** (-res.log2scale)
+                G, dA, dB = G * s, dA * s, dB * s
+            return dA, dB, G, None, None, None
+
+    return _Fn

@@ -1,0 +1,303 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (FP64): the relative residual of eq. (9) must be <= 1e-13, and Y/alpha
+must agree with the oracle's Y/alpha to 1e-12 in the Frobenius norm on inputs
+whose condition keeps the forward error of a backward-stable solver near
+machine precision (the oracle and the GPU round differently: different
+summation orders in the tile updates, multiplication by powers of two in
+different places).  Where Y/alpha overflows (the growth workloads), the two
+alpha-scaled results are compared after a common power-of-two shift.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1905_10574_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+RESID_TOL = 1e-13
+FWD_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def sy():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_10574_gb300 import build, sylv
+    build.build()
+    sylv.load()
+    return sylv
+
+
+def dev(a):
+    return torch.from_numpy(np.asfortranarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def gpu_solve(sy, A, B, C, **kw):
+    Y, res = sy.solve(dev(A), dev(B), dev(C), **kw)
+    torch.cuda.synchronize()
+    return host(Y), res
+
+
+def rel(a, b):
+    d = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (d if d else 1.0))
+
+
+def shifted(Y, e_from, e_to):
+    """Y * 2^(e_to - e_from): the same augmented tile at another scale."""
+    return np.ldexp(Y, int(e_to) - int(e_from))
+
+
+def check_against_oracle(orc, sy, A, B, C, fwd_tol=FWD_TOL, **kw):
+    Y, res = gpu_solve(sy, A, B, C, **kw)
+    ta, tb = kw.get("transa", False), kw.get("transb", False)
+    ref = orc.trsyl(A, B, C, transa=ta, transb=tb)
+    assert res.info == 0, res
+    assert np.all(np.isfinite(Y))
+    r = orc.residual(A, B, Y, C, res.log2scale, ta, tb)
+    assert r <= RESID_TOL, r
+    err = rel(shifted(Y, res.log2scale, ref["log2scale"]), ref["Y"])
+    assert err <= fwd_tol, err
+    return Y, res, ref
+
+
+def test_config1_benign_256_tile64(orc, sy):
+    """m = n = 256, tile 64, ~50% of eigenvalues in 2x2 blocks, seed 0."""
+    A, B, C = inputs.problem(256, 256, 0, kind="benign")
+    Y, res, ref = check_against_oracle(orc, sy, A, B, C, tile=64)
+    assert res.log2scale == 0 == ref["log2scale"]
+
+
+@pytest.mark.parametrize("m,n,tile", [(1, 1, 0), (1, 9, 32), (9, 1, 32), (2, 2, 32), (3, 5, 0), (33, 31, 32),
+                                      (65, 64, 64), (64, 65, 32), (100, 37, 64), (129, 200, 32), (200, 129, 64),
+                                      (257, 95, 0)])
+def test_shapes_and_tiles(orc, sy, m, n, tile):
+    A, B, C = inputs.problem(m, n, m * 1000 + n, kind="benign")
+    check_against_oracle(orc, sy, A, B, C, tile=tile)
+
+
+@pytest.mark.parametrize("transa,transb", [(True, False), (False, True), (True, True)])
+def test_transposes(orc, sy, transa, transb):
+    A, B, C = inputs.problem(150, 90, 7, kind="benign")
+    check_against_oracle(orc, sy, A, B, C, tile=32, transa=transa, transb=transb)
+
+
+def test_two_by_two_blocks_at_edges(orc, sy):
+    """2x2 blocks at index 0, at the last index and straddling every nominal tile
+    boundary: the partition must move boundaries instead of splitting blocks."""
+    m = n = 130
+    A = inputs.quasi_triangular(m, 5, kind="benign", p_pair=0.0)
+    B = inputs.quasi_triangular(n, 6, kind="benign", p_pair=0.0)
+    for T in (A, B):
+        for i in [0, 31, 63, 95, 128]:
+            T[i, i + 1], T[i + 1, i] = 1.5, -0.75
+            T[i + 1, i + 1] = T[i, i]
+    C = inputs.rhs(m, n, 3)
+    for tile in (32, 64):
+        check_against_oracle(orc, sy, A, B, C, tile=tile)
+
+
+def test_diagonal_closed_form_bit_exact(sy):
+    """Diagonal A, B: Y_ij = C_ij / (a_i + b_j) with one rounding, as in the paper's
+    small solves of 1x1 blocks; the GPU must reproduce it bit for bit."""
+    rng = np.random.default_rng(3)
+    m, n = 150, 70
+    a = rng.uniform(1, 10, m)
+    b = rng.uniform(1, 10, n)
+    C = rng.uniform(-1, 1, (m, n))
+    Y, res = gpu_solve(sy, np.diag(a), np.diag(b), C, tile=32)
+    assert res.log2scale == 0 and res.info == 0
+    assert np.array_equal(Y, C / (a[:, None] + b[None, :]))
+
+
+def test_deterministic(sy):
+    A, B, C = inputs.problem(300, 260, 9, kind="benign")
+    Y1, _ = gpu_solve(sy, A, B, C, tile=32)
+    Y2, _ = gpu_solve(sy, A, B, C, tile=32)
+    assert np.array_equal(Y1, Y2)
+
+
+def test_paper_matrices_need_no_scaling(orc, sy):
+    """Sec. 4: mu = m, nu = n gives alpha = 1."""
+    m, n = 200, 150
+    A = inputs.paper_matrix(m, float(m), seed=1)
+    B = inputs.paper_matrix(n, float(n), seed=2)
+    C = np.ones((m, n))
+    Y, res, ref = check_against_oracle(orc, sy, A, B, C, tile=64)
+    assert res.log2scale == 0
+
+
+@pytest.mark.parametrize("m,upper,tile", [(300, 100.0, 32), (500, 30.0, 64), (257, 60.0, 64)])
+def test_robust_where_plain_overflows(orc, sy, m, upper, tile):
+    """Unscaled growth of ~1300-1900 bits (past the binary64 range): the robust GPU
+    solve stays finite with a representable alpha < 1, a tiny residual and the
+    oracle's Y/alpha (after a common power-of-two shift); the non-robust mode
+    overflows."""
+    A, B, C = inputs.problem(m, m, 3, kind="growth", upper=upper)
+    ref = orc.trsyl(A, B, C)
+    assert ref["log2scale"] < 0 and ref["info"] == 0
+    Y, res = gpu_solve(sy, A, B, C, tile=tile)
+    assert res.info == 0, res
+    assert res.log2scale < 0 and res.scale_events > 0
+    assert np.all(np.isfinite(Y)) and np.max(np.abs(Y)) <= 2.0 ** 1020
+    assert orc.residual(A, B, Y, C, res.log2scale) <= RESID_TOL
+    err = rel(shifted(Y, res.log2scale, ref["log2scale"]), ref["Y"])
+    assert err <= FWD_TOL, err
+    _, res_nr = gpu_solve(sy, A, B, C, tile=tile, precision="fp64_nonrobust", check=False)
+    assert res_nr.info == sy.SYLV_OVERFLOWED
+
+
+def test_extreme_growth_alpha_underflows(orc, sy):
+    """Strictly-upper entries ~1e120: alpha falls below the double range for the oracle
+    and the GPU alike; log2scale still carries it exactly, every entry stays finite
+    and the residual (evaluated with a common power-of-two shift) stays tiny."""
+    A, B, C = inputs.problem(48, 48, 3, kind="growth", upper=1e120)
+    ref = orc.trsyl(A, B, C)
+    Y, res = gpu_solve(sy, A, B, C, tile=32, check=False)
+    assert ref["log2scale"] < -1074 and res.log2scale < -1074
+    assert res.info == sy.SYLV_SCALE_UNDERFLOW and res.scale == 0.0
+    assert np.all(np.isfinite(Y)) and np.max(np.abs(Y)) <= 2.0 ** 1020
+    assert orc.residual(A, B, Y, C, res.log2scale) <= RESID_TOL
+
+
+def test_paper_small_mu_scaling(orc, sy):
+    """Sec. 4: mu = 1e-3, nu = 1e-2 needs frequent scaling."""
+    m = n = 300
+    A = inputs.paper_matrix(m, 1e-3, seed=1)
+    B = inputs.paper_matrix(n, 1e-2, seed=2)
+    C = np.ones((m, n))
+    Y, res = gpu_solve(sy, A, B, C, tile=64, check=False)
+    ref = orc.trsyl(A, B, C)
+    assert res.log2scale < 0 and np.all(np.isfinite(Y))
+    if res.info == sy.SYLV_SCALE_UNDERFLOW:
+        assert res.scale == 0.0
+    else:
+        assert res.info == 0
+    assert orc.residual(A, B, Y, C, res.log2scale) <= RESID_TOL
+    assert ref["log2scale"] < 0
+
+
+def test_structure_and_input_errors(sy):
+    A, B, C = inputs.problem(40, 30, 1)
+    A2 = A.copy()
+    A2[11, 10] = 0.5
+    A2[12, 11] = 0.5
+    _, res = gpu_solve(sy, A2, B, C, check=False)
+    assert res.info == sy.SYLV_ERR_STRUCTURE_A
+    B2 = B.copy()
+    B2[4, 3] = 1.0
+    B2[5, 4] = 1.0
+    _, res = gpu_solve(sy, A, B2, C, check=False)
+    assert res.info == sy.SYLV_ERR_STRUCTURE_B
+    C2 = C.copy()
+    C2[3, 3] = np.nan
+    _, res = gpu_solve(sy, A, B, C2, check=False)
+    assert res.info == sy.SYLV_ERR_NONFINITE
+    A3 = A.copy()
+    A3[0, 5] = np.inf
+    _, res = gpu_solve(sy, A3, B, C, check=False)
+    assert res.info == sy.SYLV_ERR_NONFINITE
+
+
+def test_near_singular_reported(sy):
+    """lambda_i(A) + lambda_j(B) = 0 for one pair: the small solve's pivot is raised to
+    smin and the status says so (eq. (1)'s uniqueness condition fails)."""
+    m, n = 20, 20
+    A = np.triu(np.full((m, m), 0.1), 1) + np.diag(np.linspace(1, 3, m))
+    B = np.triu(np.full((n, n), 0.1), 1) + np.diag(np.linspace(1, 3, n))
+    B[7, 7] = -A[3, 3]
+    C = inputs.rhs(m, n, 1)
+    Y, res = gpu_solve(sy, A, B, C, check=False)
+    assert res.info in (sy.SYLV_NEAR_SINGULAR, sy.SYLV_SCALE_UNDERFLOW)
+    assert np.all(np.isfinite(Y))
+
+
+def test_bounded_wait_times_out_without_hanging(sy):
+    """A wait on a flag nothing sets ends with SYLV_ERR_TIMEOUT; the context stays
+    usable for the next solve."""
+    import time
+    t0 = time.time()
+    rc = sy.sylv_diag_wait_timeout(200)
+    assert rc == sy.SYLV_ERR_TIMEOUT
+    assert time.time() - t0 < 30
+    A, B, C = inputs.problem(64, 64, 2)
+    Y, res = gpu_solve(sy, A, B, C)
+    assert res.info == 0
+
+
+@pytest.mark.parametrize("m,n", [(300, 300), (257, 130)])
+def test_fp32_refine_reaches_fp64_accuracy(orc, sy, m, n):
+    """FP32 correction solves + FP64 residuals: forward error <= 1e-12 against the
+    oracle on well-conditioned inputs."""
+    A, B, C = inputs.problem(m, n, 4, kind="wellcond")
+    Y, res = gpu_solve(sy, A, B, C, precision="fp32_refine", tile=32)
+    ref = orc.trsyl(A, B, C)
+    assert res.info == 0, res
+    assert res.iters >= 2
+    assert rel(Y, ref["Y"]) <= FWD_TOL
+    assert orc.residual(A, B, Y, C, 0) <= RESID_TOL
+
+
+def test_batched_uneven(orc, sy):
+    shapes = inputs.batch_shapes(24, 16, 300, seed=5)
+    probs = [inputs.problem(m, n, 100 + i, kind="benign") for i, (m, n) in enumerate(shapes)]
+    Ys, res = sy.batch_solve([dev(p[0]) for p in probs], [dev(p[1]) for p in probs],
+                             [dev(p[2]) for p in probs])
+    torch.cuda.synchronize()
+    for (A, B, C), Y, r in zip(probs, Ys, res):
+        assert r.info == 0
+        Yh = host(Y)
+        ref = orc.trsyl(A, B, C)
+        assert orc.residual(A, B, Yh, C, r.log2scale) <= RESID_TOL
+        assert rel(shifted(Yh, r.log2scale, ref["log2scale"]), ref["Y"]) <= FWD_TOL
+
+
+def test_adjoint_matches_kronecker_gradient(orc, sy):
+    """Lyapunov-type A Y + Y A^T = C at m = n = 16: autograd through the hand-written
+    adjoint against the oracle's Kronecker-form gradient (dA = both uses of A)."""
+    m = 16
+    A = inputs.quasi_triangular(m, 8, kind="wellcond")
+    C = inputs.rhs(m, m, 9)
+    W = inputs.rhs(m, m, 10)
+    At = dev(A).requires_grad_(True)
+    Ct = dev(C).requires_grad_(True)
+    Y = sy.SylvesterSolve.apply(At, At, Ct, False, True, 0)
+    loss = (dev(W) * Y).sum()
+    loss.backward()
+    dA1, dB1, dC, _ = orc.kron_grad(A, A, C, W, False, True)
+    assert rel(host(At.grad), dA1 + dB1) <= 1e-11
+    assert rel(host(Ct.grad), dC) <= 1e-11
+
+
+def test_adjoint_finite_differences(sy):
+    """Central differences, h = 1e-6, of the GPU forward solve for a few entries."""
+    m, n = 40, 30
+    A, B, C = inputs.problem(m, n, 12, kind="wellcond")
+    W = inputs.rhs(m, n, 13)
+    At, Bt, Ct = dev(A).requires_grad_(True), dev(B).requires_grad_(True), dev(C).requires_grad_(True)
+    Y = sy.SylvesterSolve.apply(At, Bt, Ct, False, False, 32)
+    (dev(W) * Y).sum().backward()
+    h = 1e-6
+
+    def loss(A_, B_, C_):
+        Y_, _ = gpu_solve(sy, A_, B_, C_, tile=32)
+        return float(np.sum(W * Y_))
+
+    for (M, grad, idx) in [("A", At.grad, (3, 17)), ("A", At.grad, (10, 10)), ("B", Bt.grad, (0, 29)),
+                           ("C", Ct.grad, (39, 0))]:
+        E = np.zeros({"A": A, "B": B, "C": C}[M].shape)
+        E[idx] = h
+        args_p = [A + E if M == "A" else A, B + E if M == "B" else B, C + E if M == "C" else C]
+        args_m = [A - E if M == "A" else A, B - E if M == "B" else B, C - E if M == "C" else C]
+        fd = (loss(*args_p) - loss(*args_m)) / (2 * h)
+        g = float(host(grad)[idx])
+        assert abs(g - fd) <= 1e-6 * max(1.0, abs(fd)), (M, idx, g, fd)

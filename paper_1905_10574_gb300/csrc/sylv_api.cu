@@ -69,23 +69,39 @@ int tile_cap(int64_t N, int t) {
   return static_cast<int>((N + d - 1) / d);
 }
 
-// Built-in tile choice: t = 64 (the largest capacity built) unless the problem is
-// small, where shorter tiles shorten the chain of diagonal solves.
+// Built-in tile choice: t = 32.  On GB300 the FP64 pipe (2 DFMA/clk/SM) makes
+// every tile update cost t^3/2 cycles, so short tiles lose little GEMM efficiency
+// while they shorten each diagonal solve on the critical path (m = n = 4000:
+// 159 ms at t = 32 vs 240 ms at t = 64, two CTAs per SM).
 int auto_tile(int64_t m, int64_t n) {
-  const int64_t mn = m < n ? m : n;
-  return mn <= 192 ? 32 : 64;
+  (void)m;
+  (void)n;
+  return 32;
 }
 
 // Byte offsets of the tile workspace of one launch (FP64 or FP32 solve).
 struct Layout {
   // zero-initialised region [zero_lo, zero_hi)
   size_t ctrl, st, lvl_cnt, lvl_cur, tflag, zero_lo, zero_hi;
-  size_t lvl_off, inst, res, tasks, ibuf, texp, tnorm, dbuf;
+  size_t lvl_off, inst, res, tasks, ibuf, texp, tnorm, dbuf, fact, factp;
   size_t total;
+  int ncta;          // CTAs the DAG kernel may run (factor-store slots)
+  int64_t fstride;   // doubles per CTA slot
   int nlevels_max;
   int max_tiles;  // max pmax*qmax over equations
   int64_t sum_tiles;
 };
+
+constexpr int kMaxCtasPerSm = 2;
+
+int sm_count();
+
+// Tile capacity (32 or 64) the DAG kernel is instantiated with for these shapes.
+int tt_of(const std::vector<Shape>& sh) {
+  int t = 2;
+  for (const Shape& s : sh) t = std::max(t, s.t);
+  return t <= 32 ? 32 : 64;
+}
 
 Layout make_layout(const std::vector<Shape>& sh, size_t base) {
   Layout L{};
@@ -128,6 +144,15 @@ Layout make_layout(const std::vector<Shape>& sh, size_t base) {
   o = align_up(o + tiles * sizeof(double));
   L.dbuf = o;
   o = align_up(o + db * sizeof(double));
+  // Factor store of the diagonal-tile solves: per CTA, 5 TT^2 doubles bound
+  // sum over block pairs of (s^2 + s), s = ma nb, and TT^2 packed pivot words.
+  const int tt = tt_of(sh);
+  L.ncta = std::min<int64_t>(std::max<int64_t>(mt, 1), static_cast<int64_t>(sm_count()) * kMaxCtasPerSm);
+  L.fstride = 5LL * tt * tt;
+  L.fact = o;
+  o = align_up(o + static_cast<size_t>(L.ncta) * L.fstride * sizeof(double));
+  L.factp = o;
+  o = align_up(o + static_cast<size_t>(L.ncta) * tt * tt * sizeof(int32_t));
   L.total = o;
   L.nlevels_max = nlev;
   L.max_tiles = mt;
@@ -187,6 +212,9 @@ Work make_work(char* ws, const Layout& L, int count, int64_t timeout_ns) {
   w.tnorm = reinterpret_cast<double*>(ws + L.tnorm);
   w.dbuf = reinterpret_cast<double*>(ws + L.dbuf);
   w.res = reinterpret_cast<sylv_result*>(ws + L.res);
+  w.fact = reinterpret_cast<double*>(ws + L.fact);
+  w.factp = reinterpret_cast<int32_t*>(ws + L.factp);
+  w.fact_stride = L.fstride;
   w.skip = nullptr;
   w.timeout_ns = timeout_ns;
   w.max_tiles = L.max_tiles;
@@ -376,7 +404,7 @@ int enqueue_fp64(const SolvePlan& P, char* ws, const double* A, int64_t lda, con
   k_set_inst<<<1, 1, 0, s>>>(w.inst, I[0]);
   cudaError_t e = run_prep<double>(w, L, 1, std::max(P.shape.m, P.shape.n), std::max(P.shape.pmax, P.shape.qmax), s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
-  e = launch_dag_f64(P.shape.t, robust, w, L.max_tiles, s);
+  e = launch_dag_f64(P.shape.t, robust, w, std::min(L.max_tiles, L.ncta), s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
   k_consistency<double><<<grid_for(static_cast<int64_t>(L.max_tiles) * 256), 256, 0, s>>>(w);
   k_results<<<1, 32, 0, s>>>(w);
@@ -433,7 +461,7 @@ int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, c
       if (cudaMemsetAsync(w.tflag, 0, sizeof(int32_t) * L.sum_tiles, s) != cudaSuccess) return SYLV_ERR_CUDA;
       if (cudaMemsetAsync(&w.ctrl->ticket, 0, sizeof(int32_t), s) != cudaSuccess) return SYLV_ERR_CUDA;
     }
-    e = launch_dag_f32(P.shape.t, w, L.max_tiles, s);
+    e = launch_dag_f32(P.shape.t, w, std::min(L.max_tiles, L.ncta), s);
     if (e != cudaSuccess) return SYLV_ERR_CUDA;
     k_accumulate<<<grid_for(static_cast<int64_t>(L.max_tiles) * 256), 256, 0, s>>>(w, X, m, rmax, amax, bmax, dmax,
                                                                                    xmax, &rs->conv);
@@ -699,7 +727,7 @@ int sylv_batch_execute(sylv_batch_plan* P, void* stream) {
   if (cudaMemsetAsync(P->ws + L.zero_lo, 0, L.zero_hi - L.zero_lo, s) != cudaSuccess) return SYLV_ERR_CUDA;
   cudaError_t e = run_prep<double>(P->w, L, P->count, P->maxN, P->pmax_all, s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
-  e = launch_dag_f64(P->tt, P->precision == SYLV_FP64, P->w, static_cast<int>(std::min<int64_t>(L.sum_tiles, 1 << 30)), s);
+  e = launch_dag_f64(P->tt, P->precision == SYLV_FP64, P->w, static_cast<int>(std::min<int64_t>(L.sum_tiles, L.ncta)), s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
   k_consistency<double><<<grid_for(L.sum_tiles * 256), 256, 0, s>>>(P->w);
   k_results<<<(P->count + 255) / 256, 256, 0, s>>>(P->w);

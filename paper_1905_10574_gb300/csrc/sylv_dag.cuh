@@ -35,38 +35,72 @@ template <int TT, typename T>
 struct DagSmem {
   static constexpr int LDG = TT + 2;  // row stride of the GEMM operands (16-byte aligned rows)
   static constexpr int LDY = TT + 1;  // leading dimension of the Y, A_kk, B_ll tiles
-  T L[TT * LDG];                      // left GEMM operand, k-major; A_kk in the diagonal phase
-  T R[TT * LDG];                      // right GEMM operand, k-major; B_ll in the diagonal phase
+  T L[TT * LDG];                      // left GEMM operand, k-major; A_kk in the diagonal phases
+  T R[TT * LDG];                      // right GEMM operand, k-major; B_ll in the diagonal phases
   T Y[TT * LDY];                      // the tile being solved (column-major)
   double zbuf[TT][4];                 // this step's solved 1x1/2x2 blocks, by block column
-  double acolmax[TT];                 // per A block: max row-sum of A above it (within the tile)
-  double browmax[TT];                 // per B block: max block norm of B right of it
-  double pzn[TT];                     // norm of each solved block of this step
+  double acolmax[TT];                 // per A block kb: max_r<start(kb) sum_i in kb |A[r,i]|
+  double bcolmax[TT];                 // per B block lb: max_c>=end(lb) sum_j in lb |B[j,c]|
+  unsigned long long pzm[TT];         // max |z| of each solved block of this step (bit pattern)
+  unsigned long long wmax[kThreads / 32];  // per-warp max |y| over unsolved elements
   int pe[TT];                         // scale exponent of each solved block of this step
+  int pa[TT + 1];                     // factor-store offset of block row kb (see pair_offset)
+  int qb2[TT + 1];                    // prefix sums of squared B block sizes
   short rowblk[TT], colblk[TT];       // block index of every row / column of the tile
   short astart[TT + 1], bstart[TT + 1];
   unsigned long long umax;
-  double nb_acc, U;
-  int task, abort, e_acc, sacc, sop, g, e_diag, pb, qb, nscale, flags;
+  double nb_acc;
+  int task, abort, e_acc, sacc, sop, g, e_diag, pb, qb, nscale, flags, slow;
 };
 
+// Upper bound on log2|v| for finite v (exponent field + 1; 2^-1022 for zero/subnormals).
+__device__ __forceinline__ int ub_log2(double v) {
+  return static_cast<int>((__double_as_longlong(v) >> 52) & 0x7ff) - 1022;
+}
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ double bits_to_double(unsigned long long b) {
+  return __longlong_as_double(static_cast<long long>(b));
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+
+// ProtectUpdate with an integer fast path: when c + t x < 2^e_omega is evident from
+// the exponent fields alone (eo = floor(log2 omega)), no FP64 arithmetic runs.
+__device__ __forceinline__ int guard_update(double c, double t, double x, double omega, int eo) {
+  const int bnd = max(ub_log2(c), ub_log2(t) + ub_log2(x)) + 1;
+  if (bnd <= eo) return 0;
+  return protect_update(fabs(c), fabs(t), fabs(x), omega);
+}
+// ProtectDivision for z = r * rcp with rcp = 1/d, integer fast path first.
+__device__ __forceinline__ int guard_division(double r, double d, double rcp, double omega, int eo) {
+  if (ub_log2(r) + ub_log2(rcp) <= eo) return 0;
+  return protect_division(r, d, omega);
+}
+
 // ----------------------------------------------------------------------------
-// Robust solve of a small Sylvester system A11 Z + Z B11 = beta R with A11 ma x ma,
-// B11 nb x nb (ma, nb in {1,2}) through its (ma nb)-square Kronecker system
-// (I (x) A11 + B11^T (x) I) vec Z = beta vec R, by Gaussian elimination with complete
-// pivoting (Sec. 2.1).  Right-hand-side updates are guarded by ProtectUpdate and
-// divisions by ProtectDivision; the guards' exponents add up to log2(beta), which
-// is returned.  Pivots below smin are raised to smin (*near = true).  a and b are
-// the blocks column-major (ld 2); r is R column-major (ld ma) on entry, Z on exit.
-__device__ inline int small_sylv(int ma, int nb, const double* a, const double* b, double* r,
-                                 double smin, double omega, bool robust, bool* near) {
+// Small Sylvester systems (Sec. 2.1): A11 Z + Z B11 = beta R with A11 ma x ma,
+// B11 nb x nb (ma, nb in {1,2}) is (I (x) A11 + B11^T (x) I) vec Z = beta vec R, an
+// s x s system (s = ma nb), solved by Gaussian elimination with complete pivoting.
+// The elimination of the matrix does not depend on the right-hand side, so it is
+// done once per tile (pair_factor) and stored: multipliers below the diagonal, U on
+// and above it (pivots below smin raised to smin), 1/pivot after the s*s entries,
+// and the row/column interchanges in a packed int (2 bits each; bit 16: a pivot was
+// raised).  pair_solve then applies the same row interchanges and eliminations to
+// the right-hand side, in the same order, with each update guarded by ProtectUpdate
+// and each division (a multiplication by the stored reciprocal) by ProtectDivision.
+__device__ inline int pair_factor(int ma, int nb, const double* a, const double* b, double smin, double* out) {
   const int s = ma * nb;
   double M[4][4];
-  int cp[4];
-  int lb = 0;
+  int pack = 0;
   for (int u = 0; u < s; ++u) {
     const int i = u % ma, j = u / ma;
-    cp[u] = u;
     for (int v = 0; v < s; ++v) {
       const int i2 = v % ma, j2 = v / ma;
       double e = 0.0;
@@ -75,47 +109,71 @@ __device__ inline int small_sylv(int ma, int nb, const double* a, const double* 
       M[u][v] = e;
     }
   }
+  int cperm[4] = {0, 1, 2, 3};
   for (int st = 0; st < s; ++st) {
     int pr = st, pc = st;
-    double best = -1.0;
+    unsigned long long best = 0;
+    bool first = true;
     for (int u = st; u < s; ++u)
       for (int v = st; v < s; ++v) {
-        const double mag = fabs(M[u][v]);
-        if (mag > best) {
+        const unsigned long long mag = abs_bits(M[u][v]);
+        if (first || mag > best) {
           best = mag;
           pr = u;
           pc = v;
+          first = false;
         }
       }
-    if (pr != st) {
+    if (pr != st)
       for (int v = 0; v < s; ++v) {
         const double tmp = M[st][v];
         M[st][v] = M[pr][v];
         M[pr][v] = tmp;
       }
-      const double tmp = r[st];
-      r[st] = r[pr];
-      r[pr] = tmp;
-    }
-    if (pc != st) {
+    if (pc != st)
       for (int u = 0; u < s; ++u) {
         const double tmp = M[u][st];
         M[u][st] = M[u][pc];
         M[u][pc] = tmp;
       }
-      const int tmp = cp[st];
-      cp[st] = cp[pc];
-      cp[pc] = tmp;
-    }
+    const int ct = cperm[st];
+    cperm[st] = cperm[pc];
+    cperm[pc] = ct;
+    pack |= (pr & 3) << (2 * st);
     if (fabs(M[st][st]) < smin) {
       M[st][st] = smin;
-      *near = true;
+      pack |= 1 << 16;
     }
     for (int u = st + 1; u < s; ++u) {
       const double l = M[u][st] / M[st][st];
+      M[u][st] = l;
       for (int v = st + 1; v < s; ++v) M[u][v] = fma(-l, M[st][v], M[u][v]);
+    }
+  }
+  for (int u = 0; u < s; ++u) pack |= (cperm[u] & 3) << (8 + 2 * u);
+  for (int u = 0; u < s; ++u)
+    for (int v = 0; v < s; ++v) out[u * s + v] = M[u][v];
+  for (int u = 0; u < s; ++u) out[s * s + u] = 1.0 / M[u][u];
+  return pack;
+}
+
+// Right-hand side of a factored pair: r (vec order, length s) in, Z (vec order) out.
+// Returns log2(beta).
+__device__ inline int pair_solve(int s, const double* f, int pack, double* r, double omega, int eo, bool robust) {
+  int lb = 0;
+  for (int st = 0; st < s; ++st) {
+    const int pr = (pack >> (2 * st)) & 3;
+    if (pr != st) {
+      const double tmp = r[st];
+      r[st] = r[pr];
+      r[pr] = tmp;
+    }
+  }
+  for (int st = 0; st < s; ++st)
+    for (int u = st + 1; u < s; ++u) {
+      const double l = f[u * s + st];
       if (robust) {
-        const int z = protect_update(fabs(r[u]), fabs(l), fabs(r[st]), omega);
+        const int z = guard_update(r[u], l, r[st], omega, eo);
         if (z) {
           for (int w = 0; w < s; ++w) r[w] = mul2(r[w], z);
           lb += z;
@@ -123,29 +181,30 @@ __device__ inline int small_sylv(int ma, int nb, const double* a, const double* 
       }
       r[u] = fma(-l, r[st], r[u]);
     }
-  }
   for (int i = s - 1; i >= 0; --i) {
     for (int v = i + 1; v < s; ++v) {
+      const double uiv = f[i * s + v];
       if (robust) {
-        const int z = protect_update(fabs(r[i]), fabs(M[i][v]), fabs(r[v]), omega);
+        const int z = guard_update(r[i], uiv, r[v], omega, eo);
         if (z) {
           for (int w = 0; w < s; ++w) r[w] = mul2(r[w], z);
           lb += z;
         }
       }
-      r[i] = fma(-M[i][v], r[v], r[i]);
+      r[i] = fma(-uiv, r[v], r[i]);
     }
+    const double rcp = f[s * s + i];
     if (robust) {
-      const int z = protect_division(r[i], M[i][i], omega);
+      const int z = guard_division(r[i], f[i * s + i], rcp, omega, eo);
       if (z) {
         for (int w = 0; w < s; ++w) r[w] = mul2(r[w], z);
         lb += z;
       }
     }
-    r[i] = r[i] / M[i][i];
+    r[i] = r[i] * rcp;
   }
   double x[4];
-  for (int u = 0; u < s; ++u) x[cp[u]] = r[u];
+  for (int u = 0; u < s; ++u) x[(pack >> (8 + 2 * u)) & 3] = r[u];
   for (int u = 0; u < s; ++u) r[u] = x[u];
   return lb;
 }
@@ -175,24 +234,30 @@ __device__ inline int scan_blocks(const T* M, int N, short* blk, short* start, i
   return count;
 }
 
-// Diagonal-tile solve: Algorithm 2 applied to one tile, in wavefront order.
-// Small blocks (kb, lb) on the anti-diagonal s = (pb-1-kb) + lb are independent;
-// each step solves them (one thread per block), agrees on one tile-wide scale
-// factor, and pushes their contributions to the unsolved elements (each element is
-// updated by the thread that owns it, so no two threads write one element).
-// Robustness: U bounds the block norms of every unsolved block; per step
-//   g = e_min + ProtectUpdate twice, so that 2^g (U + As*Zs + Zs*Bs) <= omega,
-// where Zs bounds the step's solved block norms, As the norms of the A blocks
-// above them and Bs the norms of the B blocks right of them.  Every element of the
-// tile is multiplied by 2^g (exactly), the step's blocks by 2^(g - e_block).
+// Offset of pair (kb, lb) in the factor store: pairs are stored block row by block
+// row, each taking s^2 + s doubles (s = ma nb).
+template <int TT, typename T>
+__device__ __forceinline__ int pair_offset(const DagSmem<TT, T>& sh, int kb, int lb, int ma) {
+  return sh.pa[kb] + ma * ma * sh.qb2[lb] + ma * sh.bstart[lb];
+}
+
+// Diagonal-tile preparation, independent of Y: load A_kk into L and B_ll into R,
+// find their 1x1/2x2 blocks, the norms the in-tile guards need, and factor every
+// pair's small system into the CTA's factor store.  Runs right after a CTA takes a
+// tile, while the tile's producers may still be running.
 template <int TT, typename T, bool ROBUST>
-__device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, double smin) {
+__device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const T* B, int64_t ldb, int r0, int c0,
+                             int mt, int nt, double smin, double* fact, int* factp) {
   constexpr int LDY = DagSmem<TT, T>::LDY;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const T* Ak = sh.L;
-  const T* Bk = sh.R;
-  T* Ys = sh.Y;
-
+  T* Ak = sh.L;
+  T* Bk = sh.R;
+  for (int idx = tid; idx < TT * TT; idx += kThreads) {
+    const int r = idx % TT, c = idx / TT;
+    Ak[r + c * LDY] = (r < mt && c < mt && r <= c + 1) ? __ldg(&A[(r0 + r) + static_cast<int64_t>(r0 + c) * lda]) : T(0);
+    Bk[r + c * LDY] = (r < nt && c < nt && r <= c + 1) ? __ldg(&B[(c0 + r) + static_cast<int64_t>(c0 + c) * ldb]) : T(0);
+  }
+  __syncthreads();
   if (warp == 0) {
     const int pb = scan_blocks<T, LDY>(Ak, mt, sh.rowblk, sh.astart, lane);
     if (lane == 0) sh.pb = pb;
@@ -200,53 +265,90 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
     const int qb = scan_blocks<T, LDY>(Bk, nt, sh.colblk, sh.bstart, lane);
     if (lane == 0) sh.qb = qb;
   }
-  if (tid == 0) {
-    sh.umax = 0ull;
-    sh.e_diag = 0;
-  }
   __syncthreads();
   const int pb = sh.pb, qb = sh.qb;
-
+  if (tid == 0) {
+    int acc = 0;
+    for (int lb = 0; lb < qb; ++lb) {
+      sh.qb2[lb] = acc;
+      const int nb = sh.bstart[lb + 1] - sh.bstart[lb];
+      acc += nb * nb;
+    }
+    sh.qb2[qb] = acc;
+    int off = 0;
+    for (int kb = 0; kb < pb; ++kb) {
+      sh.pa[kb] = off;
+      const int ma = sh.astart[kb + 1] - sh.astart[kb];
+      off += ma * ma * acc + ma * nt;
+    }
+    sh.pa[pb] = off;
+  }
   if (ROBUST) {
     for (int kb = tid; kb < pb; kb += kThreads) {
       const int ra = sh.astart[kb], re = sh.astart[kb + 1];
       double best = 0.0;
       for (int r = 0; r < ra; ++r) {
-        double s = 0.0;
-        for (int i = ra; i < re; ++i) s += fabs(static_cast<double>(Ak[r + i * LDY]));
-        best = fmax(best, s);
+        double sum = 0.0;
+        for (int i = ra; i < re; ++i) sum += fabs(static_cast<double>(Ak[r + i * LDY]));
+        best = fmax(best, sum);
       }
       sh.acolmax[kb] = best;
     }
     for (int lb = tid; lb < qb; lb += kThreads) {
-      const int c0 = sh.bstart[lb], c1 = sh.bstart[lb + 1];
+      const int j0 = sh.bstart[lb], j1 = sh.bstart[lb + 1];
       double best = 0.0;
-      for (int jb = lb + 1; jb < qb; ++jb) {
-        const int j0 = sh.bstart[jb], j1 = sh.bstart[jb + 1];
-        for (int row = c0; row < c1; ++row) {
-          double s = 0.0;
-          for (int c = j0; c < j1; ++c) s += fabs(static_cast<double>(Bk[row + c * LDY]));
-          best = fmax(best, s);
-        }
+      for (int c = j1; c < nt; ++c) {
+        double sum = 0.0;
+        for (int j = j0; j < j1; ++j) sum += fabs(static_cast<double>(Bk[j + c * LDY]));
+        best = fmax(best, sum);
       }
-      sh.browmax[lb] = best;
-    }
-    // U0: largest block infinity norm of the tile.
-    for (int idx = tid; idx < mt * nt; idx += kThreads) {
-      const int r = idx % mt, c = idx / mt;
-      const int lbc = sh.colblk[c];
-      if (sh.bstart[lbc] != c) continue;
-      double s = fabs(static_cast<double>(Ys[r + c * LDY]));
-      if (sh.bstart[lbc + 1] - c == 2) s += fabs(static_cast<double>(Ys[r + (c + 1) * LDY]));
-      atomic_max_nonneg(&sh.umax, s);
+      sh.bcolmax[lb] = best;
     }
   }
   __syncthreads();
-  if (tid == 0) sh.U = __longlong_as_double(static_cast<long long>(sh.umax));
+  for (int pidx = tid; pidx < pb * qb; pidx += kThreads) {
+    const int kb = pidx / qb, lb = pidx % qb;
+    const int ra = sh.astart[kb], ma = sh.astart[kb + 1] - ra;
+    const int cb0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - cb0;
+    double a[4], b[4];
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        a[i + 2 * j] = (i < ma && j < ma) ? static_cast<double>(Ak[(ra + i) + (ra + j) * LDY]) : 0.0;
+        b[i + 2 * j] = (i < nb && j < nb) ? static_cast<double>(Bk[(cb0 + i) + (cb0 + j) * LDY]) : 0.0;
+      }
+    factp[kb * TT + lb] = pair_factor(ma, nb, a, b, smin, fact + pair_offset(sh, kb, lb, ma));
+  }
+  __syncthreads();
+}
 
-  // Element ownership in the update phase: thread owns row tid % TT, columns
-  // tid / TT + j * (kThreads / TT).
+// Diagonal-tile solve: Algorithm 2 applied to one tile, in wavefront order over its
+// 1x1/2x2 blocks.  The blocks (kb, lb) on the anti-diagonal s = (pb-1-kb) + lb are
+// independent; a step solves them (one thread per block, stored factors), agrees on
+// one tile-wide power of two, and every element's owner applies the step's
+// contributions (no element has two writers).
+// Robustness, element-wise with omega' = omega/2 (so every 1x1/2x2 block's row sum
+// stays <= omega): U = max |y| over unsolved elements (exact, recomputed every
+// step); a step's blocks are solved with omega'; the step then scales the whole tile
+// by 2^g with g = e_min + zeta such that
+//   2^zeta (2^e_min U + As Zm + Zm Bs) <= omega',
+// As = max over the step's blocks of the A row sums above them, Bs = max of the B
+// column sums right of them, Zm = max |z| of the step's blocks at the common scale.
+// When all exponents are far from omega' the decision is taken from the exponent
+// fields alone (g = e_min, no FP64 work); otherwise warp 0 evaluates ProtectUpdate.
+template <int TT, typename T, bool ROBUST>
+__device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, const double* fact, const int* factp) {
+  constexpr int LDY = DagSmem<TT, T>::LDY;
   constexpr int CSTEP = kThreads / TT;
+  constexpr int NC = TT / CSTEP;  // columns owned per thread
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T* Ak = sh.L;
+  const T* Bk = sh.R;
+  T* Ys = sh.Y;
+  const int pb = sh.pb, qb = sh.qb;
+  const double omh = 0.5 * omega;
+  const int eo = floor_log2(omh);
+
+  // Element ownership: row tid % TT, columns tid / TT + j * CSTEP.
   const int my_r = tid % TT;
   const int my_c0 = tid / TT;
   const bool row_ok = my_r < mt;
@@ -254,40 +356,74 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
   const int dr = pb - 1 - kb_r;
   const int ra_r = row_ok ? sh.astart[kb_r] : 0;
   const int ma_r = row_ok ? sh.astart[kb_r + 1] - ra_r : 1;
+
+  // Initial U (and a pre-scaling if the tile exceeds omega').
+  unsigned long long um = 0;
+  if (row_ok)
+    for (int c = my_c0; c < nt; c += CSTEP) {
+      const unsigned long long b = abs_bits(static_cast<double>(Ys[my_r + c * LDY]));
+      um = b > um ? b : um;
+    }
+  um = warp_max_u64(um);
+  if (lane == 0) sh.wmax[warp] = um;
+  if (tid == 0) {
+    sh.e_diag = 0;
+    sh.slow = 0;
+  }
+  __syncthreads();
+  if (ROBUST) {
+    unsigned long long u0 = 0;
+    for (int w = 0; w < kThreads / 32; ++w) u0 = sh.wmax[w] > u0 ? sh.wmax[w] : u0;
+    const double U0 = bits_to_double(u0);
+    if (U0 > omh) {  // keep every element within omega'
+      const int z = floor_log2(omh) - ceil_log2(U0);
+      if (row_ok)
+        for (int c = my_c0; c < nt; c += CSTEP) Ys[my_r + c * LDY] = mul2(Ys[my_r + c * LDY], z);
+      if (tid == 0) sh.e_diag = z;
+      __syncthreads();
+      if (lane == 0) sh.wmax[warp] = abs_bits(mul2(U0, z));
+      __syncthreads();
+    }
+  }
   bool near = false;
   int local_scale_events = 0;
-
   const int nsteps = pb + qb - 1;
   for (int s = 0; s < nsteps; ++s) {
     const int lb_lo = max(0, s - (pb - 1));
     const int lb_hi = min(s, qb - 1);
-    // Phase A: solve this step's blocks.
+    // Phase A: this step's blocks, one thread each.
     for (int lb = lb_lo + tid; lb <= lb_hi; lb += kThreads) {
       const int kb = pb - 1 - (s - lb);
       const int r0 = sh.astart[kb], ma = sh.astart[kb + 1] - r0;
       const int c0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - c0;
-      double a[4], b[4], rr[4];
-      for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j) {
-          a[i + 2 * j] = (i < ma && j < ma) ? static_cast<double>(Ak[(r0 + i) + (r0 + j) * LDY]) : 0.0;
-          b[i + 2 * j] = (i < nb && j < nb) ? static_cast<double>(Bk[(c0 + i) + (c0 + j) * LDY]) : 0.0;
-        }
-      for (int u = 0; u < ma * nb; ++u)
-        rr[u] = static_cast<double>(Ys[(r0 + u % ma) + (c0 + u / ma) * LDY]);
-      const int e = small_sylv(ma, nb, a, b, rr, smin, omega, ROBUST, &near);
-      double zn = 0.0;
-      for (int i = 0; i < ma; ++i) {
-        double rs = 0.0;
-        for (int j = 0; j < nb; ++j) rs += fabs(rr[i + ma * j]);
-        zn = fmax(zn, rs);
+      const int sz = ma * nb;
+      const int pack = factp[kb * TT + lb];
+      if (pack & (1 << 16)) near = true;
+      double rr[4];
+      for (int u = 0; u < sz; ++u) rr[u] = static_cast<double>(Ys[(r0 + u % ma) + (c0 + u / ma) * LDY]);
+      const int e = pair_solve(sz, fact + pair_offset(sh, kb, lb, ma), pack, rr, omh, eo, ROBUST);
+      unsigned long long zm = 0;
+      for (int u = 0; u < 4; ++u) {
+        const double v = (u < sz) ? rr[u] : 0.0;
+        sh.zbuf[lb][u] = v;
+        const unsigned long long bv = abs_bits(v);
+        zm = bv > zm ? bv : zm;
       }
-      for (int u = 0; u < 4; ++u) sh.zbuf[lb][u] = (u < ma * nb) ? rr[u] : 0.0;
       sh.pe[lb] = e;
-      sh.pzn[lb] = zn;
+      sh.pzm[lb] = zm;
+      if (ROBUST) {
+        unsigned long long u0 = 0;
+        for (int w = 0; w < kThreads / 32; ++w) u0 = sh.wmax[w] > u0 ? sh.wmax[w] : u0;
+        const int ez = ub_log2(bits_to_double(zm));
+        const bool fast = e == 0 && ub_log2(bits_to_double(u0)) + 2 <= eo &&
+                          ub_log2(sh.acolmax[kb]) + ez + 2 <= eo && ez + ub_log2(sh.bcolmax[lb]) + 2 <= eo;
+        if (!fast) sh.slow = 1;
+      }
     }
     __syncthreads();
-    // Phase B: one tile-wide scale factor for this step.
-    if (ROBUST) {
+    int g = 0;
+    if (ROBUST && sh.slow) {
+      // Phase B (rare): exact tile-wide factor of this step.
       if (warp == 0) {
         int emin = 0;
         for (int lb = lb_lo + lane; lb <= lb_hi; lb += 32) emin = min(emin, sh.pe[lb]);
@@ -295,41 +431,52 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
         double zs = 0.0, as = 0.0, bs = 0.0;
         for (int lb = lb_lo + lane; lb <= lb_hi; lb += 32) {
           const int kb = pb - 1 - (s - lb);
-          zs = fmax(zs, mul2(sh.pzn[lb], emin - sh.pe[lb]));
+          zs = fmax(zs, mul2(bits_to_double(sh.pzm[lb]), emin - sh.pe[lb]));
           as = fmax(as, sh.acolmax[kb]);
-          bs = fmax(bs, sh.browmax[lb]);
+          bs = fmax(bs, sh.bcolmax[lb]);
         }
         zs = warp_max(zs);
         as = warp_max(as);
         bs = warp_max(bs);
         if (lane == 0) {
-          const double U1 = mul2(sh.U, emin);
-          const int z1 = protect_update(U1, as, zs, omega);
+          unsigned long long u0 = 0;
+          for (int w = 0; w < kThreads / 32; ++w) u0 = sh.wmax[w] > u0 ? sh.wmax[w] : u0;
+          const double U1 = mul2(bits_to_double(u0), emin);
+          const int z1 = protect_update(U1, as, zs, omh);
           const double zs1 = mul2(zs, z1);
           const double U2 = mul2(U1, z1) + as * zs1;
-          const int z2 = protect_update(U2, zs1, bs, omega);
-          const int g = emin + z1 + z2;
-          sh.U = mul2(U2, z2) + mul2(zs1, z2) * bs;
-          sh.e_diag += g;
-          sh.g = g;
-          if (g != 0) ++local_scale_events;
+          const int z2 = protect_update(U2, zs1, bs, omh);
+          const int gg = emin + z1 + z2;
+          sh.e_diag += gg;
+          sh.g = gg;
+          sh.slow = 0;
+          if (gg != 0) ++local_scale_events;
         }
         __syncwarp();
-        const int g = sh.g;
+        const int gg = sh.g;
         for (int lb = lb_lo + lane; lb <= lb_hi; lb += 32) {
-          const int sc = g - sh.pe[lb];
+          const int sc = gg - sh.pe[lb];
           if (sc != 0)
             for (int u = 0; u < 4; ++u) sh.zbuf[lb][u] = mul2(sh.zbuf[lb][u], sc);
         }
       }
       __syncthreads();
+      g = sh.g;
     }
-    const int g = ROBUST ? sh.g : 0;
-    // Phase C: every owned element takes its scale and this step's contributions.
+    // Phase C: every owned element takes its scale and this step's contributions;
+    // U for the next step is the max over unsolved elements.
+    unsigned long long wm = 0;
     if (row_ok) {
-      for (int c = my_c0; c < nt; c += CSTEP) {
+#pragma unroll 4
+      for (int j = 0; j < NC; ++j) {
+        const int c = my_c0 + j * CSTEP;
+        if (c >= nt) break;
         const int lbc = sh.colblk[c];
         const int dd = dr + lbc;
+        if (dd < s) {
+          if (g != 0) Ys[my_r + c * LDY] = mul2(Ys[my_r + c * LDY], g);
+          continue;
+        }
         T* yp = &Ys[my_r + c * LDY];
         if (dd == s) {
           const int cb0 = sh.bstart[lbc];
@@ -337,26 +484,29 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
           continue;
         }
         double y = static_cast<double>(*yp);
-        if (ROBUST && g != 0) y = mul2(y, g);
-        if (dd > s) {
-          if (s >= lbc && s - lbc < dr) {  // block (kbs, lbc) below this row, solved now
-            const int kbs = pb - 1 - (s - lbc);
-            const int rs0 = sh.astart[kbs], mas = sh.astart[kbs + 1] - rs0;
-            const int cb0 = sh.bstart[lbc];
-            for (int ii = 0; ii < mas; ++ii)
-              y = fma(-static_cast<double>(Ak[my_r + (rs0 + ii) * LDY]),
-                      sh.zbuf[lbc][ii + mas * (c - cb0)], y);
-          }
-          if (s >= dr && s - dr < lbc) {  // block (kb_r, lbs) left of this column, solved now
-            const int lbs = s - dr;
-            const int cs0 = sh.bstart[lbs], nbs = sh.bstart[lbs + 1] - cs0;
-            for (int jj = 0; jj < nbs; ++jj)
-              y = fma(-sh.zbuf[lbs][(my_r - ra_r) + ma_r * jj],
-                      static_cast<double>(Bk[(cs0 + jj) + c * LDY]), y);
-          }
+        if (g != 0) y = mul2(y, g);
+        if (s >= lbc && s - lbc < dr) {  // block (kbs, lbc) below this row, solved now
+          const int kbs = pb - 1 - (s - lbc);
+          const int rs0 = sh.astart[kbs], mas = sh.astart[kbs + 1] - rs0;
+          const int cb0 = sh.bstart[lbc];
+          for (int ii = 0; ii < mas; ++ii)
+            y = fma(-static_cast<double>(Ak[my_r + (rs0 + ii) * LDY]), sh.zbuf[lbc][ii + mas * (c - cb0)], y);
         }
-        *yp = static_cast<T>(y);
+        if (s >= dr && s - dr < lbc) {  // block (kb_r, lbs) left of this column, solved now
+          const int lbs = s - dr;
+          const int cs0 = sh.bstart[lbs], nbs = sh.bstart[lbs + 1] - cs0;
+          for (int jj = 0; jj < nbs; ++jj)
+            y = fma(-sh.zbuf[lbs][(my_r - ra_r) + ma_r * jj], static_cast<double>(Bk[(cs0 + jj) + c * LDY]), y);
+        }
+        const T yt = static_cast<T>(y);
+        *yp = yt;
+        const unsigned long long b = abs_bits(static_cast<double>(yt));
+        wm = b > wm ? b : wm;
       }
+    }
+    if (ROBUST) {
+      wm = warp_max_u64(wm);
+      if (lane == 0) sh.wmax[warp] = wm;
     }
     __syncthreads();
   }
@@ -414,7 +564,7 @@ __device__ __forceinline__ void gemm_sub(T (&acc)[MR][NR], const T* L, const T* 
 }
 
 template <int TT, typename T, bool ROBUST>
-__global__ void __launch_bounds__(kThreads) dag_kernel(Work w) {
+__global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
   static_assert(TT == 32 || TT == 64, "tile capacity");
   constexpr int MR = TT / 16, NR = TT / 16;
   constexpr int LDY = DagSmem<TT, T>::LDY;
@@ -454,6 +604,10 @@ __global__ void __launch_bounds__(kThreads) dag_kernel(Work w) {
     int32_t* texp = w.texp + I.tile;
     int32_t* tflag = w.tflag + I.tile;
     double* tnorm = w.tnorm + I.tile;
+
+    double* fact = w.fact + static_cast<int64_t>(blockIdx.x) * w.fact_stride;
+    int* factp = w.factp + static_cast<int64_t>(blockIdx.x) * TT * TT;
+    diag_prepare<TT, T, ROBUST>(sh, A, I.lda, B, I.ldb, r0, c0, mt, nt, st->smin, fact, factp);
 
     // ---- accumulator <- C_kl, exact infinity norm
     T acc[MR][NR];
@@ -578,7 +732,7 @@ __global__ void __launch_bounds__(kThreads) dag_kernel(Work w) {
       sh.R[r + c * LDY] = (r < nt && c < nt && r <= c + 1) ? __ldg(&B[(c0 + r) + (int64_t)(c0 + c) * I.ldb]) : T(0);
     }
     __syncthreads();
-    diag_solve<TT, T, ROBUST>(sh, mt, nt, omega, st->smin);
+    diag_solve<TT, T, ROBUST>(sh, mt, nt, omega, fact, factp);
 
     // ---- exact norm of the final tile, write back, publish
     if (tid == 0) sh.umax = 0ull;

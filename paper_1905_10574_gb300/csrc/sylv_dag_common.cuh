@@ -1,6 +1,8 @@
 // sylv_dag_common.cuh -- grid sizing shared by the DAG launch units.
 #pragma once
 
+#include <cstdlib>
+
 #include "sylv_dag.cuh"
 #include "sylv_launch.h"
 
@@ -22,6 +24,12 @@ cudaError_t launch_dag_impl(const Work& w, int max_tasks, cudaStream_t stream, i
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<TT, T, ROBUST>, kThreads, smem);
     if (e != cudaSuccess) return e;
     per_sm = nb > 0 ? nb : 1;
+    if (per_sm > 2) per_sm = 2;  // the workspace holds factor stores for 2 CTAs per SM
+    // Experiment knob: SYLV_CTAS_PER_SM=1 keeps one CTA per SM (no FP64-pipe sharing).
+    if (const char* env = std::getenv("SYLV_CTAS_PER_SM")) {
+      const int v = std::atoi(env);
+      if (v >= 1 && v < per_sm) per_sm = v;
+    }
   }
   if (per_sm_out) *per_sm_out = per_sm;
   if (max_tasks <= 0) return cudaSuccess;

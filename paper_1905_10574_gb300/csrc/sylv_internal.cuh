@@ -76,6 +76,9 @@ struct Work {
   double* dbuf;     // off-diagonal tile norms of A and B
   sylv_result* res; // per-equation results
   const int* skip;  // if non-null and nonzero, the DAG kernel returns at once
+  double* fact;     // per-CTA store of factored small systems (fact_stride doubles each)
+  int32_t* factp;   // per-CTA packed pivot data (TT*TT ints each)
+  int64_t fact_stride;
   int64_t timeout_ns;
   int32_t max_tiles;  // max over equations of pmax * qmax
   int32_t pad;

@@ -123,9 +123,12 @@ def problem(m: int, n: int, seed: int, kind: str = "benign", upper: float = 1.0)
 # non-robust solve overflows, while alpha = 2^-(growth - 1020) stays representable.
 WORKLOADS = {
     "benign_256": dict(m=256, n=256, seed=0, kind="benign", upper=1.0, tile=64),
-    "overflow_4000": dict(m=4000, n=4000, seed=0, kind="growth", upper=4.1, tile=64),
-    "benign_8000": dict(m=8000, n=8000, seed=0, kind="benign", upper=1.0, tile=64),
-    "wellcond_8000": dict(m=8000, n=8000, seed=0, kind="wellcond", upper=1.0, tile=64),
+    "overflow_4000": dict(m=4000, n=4000, seed=0, kind="growth", upper=4.1, tile=32),
+    "overflow_1000": dict(m=1000, n=1000, seed=0, kind="growth", upper=16.0, tile=32),
+    "benign_1000": dict(m=1000, n=1000, seed=0, kind="benign", upper=1.0, tile=32),
+    "benign_4000": dict(m=4000, n=4000, seed=0, kind="benign", upper=1.0, tile=32),
+    "benign_8000": dict(m=8000, n=8000, seed=0, kind="benign", upper=1.0, tile=32),
+    "wellcond_8000": dict(m=8000, n=8000, seed=0, kind="wellcond", upper=1.0, tile=32),
 }
 
 

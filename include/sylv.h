@@ -183,6 +183,34 @@ int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, 
                             int64_t lddb, const sylv_opts* opts, sylv_result* result);
 
 /*
+ * sylv_tri_solve_noalloc -- the robust FP64 solve of sylv_tri_solve, for callers
+ * that must not allocate device memory while they run: code that records CUDA
+ * graphs or runs inside a stream capture and may not add allocations, real-time
+ * loops that forbid allocator calls after start-up, and hosts whose device memory
+ * belongs to another allocator.  The paper has no counterpart; it is a service
+ * of this library.
+ *
+ * It allocates nothing: its scratch is one fixed array of 16 MiB in device memory
+ * that this library defines and every GPU that loads the library holds until the
+ * process exits.  The caller passes the inputs and the output as for
+ * sylv_tri_solve (device pointers; C is overwritten by Y); `tile` as for
+ * sylv_tri_solve; `stream` is a cudaStream_t (NULL: legacy default stream); the
+ * call waits for the stream and fills the HOST record *result (may be NULL).
+ * Problems whose bookkeeping does not fit the array are rejected on the host,
+ * before any GPU work, with SYLV_ERR_WORKSPACE (about m, n <= 11000 fit at the
+ * default tile); when the per-CTA stores fit only in part, the solve runs with
+ * fewer CTAs.  The first call on a device looks up the array's device address
+ * (a runtime call, once per device, with that device current); make that first
+ * call before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents: each call clears what must start at zero, but two
+ * calls that overlap on the GPU (different streams or threads) race on it and
+ * give wrong results.  Status codes as for sylv_tri_solve_ex.
+ */
+int sylv_tri_solve_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, const double* B,
+                           int64_t ldb, double* C, int64_t ldc, int64_t tile, void* stream,
+                           sylv_result* result);
+
+/*
  * sylv_diag_wait_timeout -- diagnostic of the solver's bounded waits (not in the
  * paper).  Launches one CTA that waits, with the same bounded wait the tile-DAG
  * kernel uses for its ready flags, on a flag that nothing ever sets, and returns

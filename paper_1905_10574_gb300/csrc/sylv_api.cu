@@ -3,6 +3,7 @@
 // transposed forms, the FP32 + refinement loop, the adjoint, and batch plans.
 #include <cstdio>
 #include <cstdlib>
+#include <array>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -97,13 +98,15 @@ constexpr int kMaxCtasPerSm = 2;
 int sm_count();
 
 // Tile capacity (32 or 64) the DAG kernel is instantiated with for these shapes.
-int tt_of(const std::vector<Shape>& sh) {
+template <class Seq>
+int tt_of(const Seq& sh) {
   int t = 2;
   for (const Shape& s : sh) t = std::max(t, s.t);
   return t <= 32 ? 32 : 64;
 }
 
-Layout make_layout(const std::vector<Shape>& sh, size_t base) {
+template <class Seq>
+Layout make_layout_seq(const Seq& sh, size_t base, int cta_cap) {
   Layout L{};
   int64_t tiles = 0, ib = 0, db = 0;
   int nlev = 1, mt = 0;
@@ -148,6 +151,7 @@ Layout make_layout(const std::vector<Shape>& sh, size_t base) {
   // sum over block pairs of (s^2 + s), s = ma nb, and TT^2 packed pivot words.
   const int tt = tt_of(sh);
   L.ncta = std::min<int64_t>(std::max<int64_t>(mt, 1), static_cast<int64_t>(sm_count()) * kMaxCtasPerSm);
+  if (cta_cap > 0 && L.ncta > cta_cap) L.ncta = cta_cap;
   L.fstride = 5LL * tt * tt;
   L.fact = o;
   o = align_up(o + static_cast<size_t>(L.ncta) * L.fstride * sizeof(double));
@@ -158,6 +162,10 @@ Layout make_layout(const std::vector<Shape>& sh, size_t base) {
   L.max_tiles = mt;
   L.sum_tiles = tiles;
   return L;
+}
+
+Layout make_layout(const std::vector<Shape>& sh, size_t base, int cta_cap = 0) {
+  return make_layout_seq(sh, base, cta_cap);
 }
 
 // Descriptors for each equation (host copies) given the layout.
@@ -844,3 +852,113 @@ int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free entry point
+// Some callers cannot allocate device memory at solve time: code running inside a
+// CUDA stream capture that must not add allocation nodes, real-time loops that
+// forbid allocator calls after start-up, and embeddings whose memory is owned by
+// another allocator.  sylv_tri_solve_noalloc serves them with scratch that lives in
+// a fixed-size device array of this library (g_noalloc_scratch below), so a call
+// itself allocates nothing.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB per device, held until exit
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+struct NoAllocState {
+  std::mutex mu;
+  void* addr[64] = {};  // device address of g_noalloc_scratch, per device (set-up once)
+};
+NoAllocState& noalloc_state() {
+  static NoAllocState s;
+  return s;
+}
+
+}  // namespace
+
+extern "C" int sylv_tri_solve_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, const double* B,
+                                      int64_t ldb, double* C, int64_t ldc, int64_t tile, void* stream,
+                                      sylv_result* result) {
+  const int ac = check_args(m, n, A, lda, B, ldb, C, ldc);
+  if (ac) return ac;
+  if (tile < 0 || tile == 1 || tile > 64) return -9;
+  sylv_opts op;
+  sylv_default_opts(&op);
+  op.tile = static_cast<int32_t>(tile);
+  op.stream = stream;
+  Opts o{};
+  const int oc = read_opts(&op, &o);
+  if (oc) return oc;
+  if (m == 0 || n == 0) return solve_impl(m, n, A, lda, B, ldb, C, ldc, o, result, nullptr);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SYLV_ERR_CUDA;
+  void* scratch = nullptr;
+  {
+    NoAllocState& S = noalloc_state();
+    std::lock_guard<std::mutex> lk(S.mu);
+    if (!S.addr[dev]) {
+      // Host code may not pass the array's name to a kernel: it is a host-side
+      // stand-in.  The device address comes from the runtime, once per device.
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return SYLV_ERR_CUDA;
+      }
+      S.addr[dev] = p;
+    }
+    scratch = S.addr[dev];
+  }
+  // Fit the solve into the fixed scratch: the per-CTA factor stores dominate, so
+  // the tile kernel runs with as many CTAs as fit (at least one).
+  const int t = o.tile ? o.tile : auto_tile(m, n);
+  const std::array<Shape, 1> shp{{Shape{m, n, t, tile_cap(m, t), tile_cap(n, t)}}};
+  const Layout full = make_layout_seq(shp, 0, 0);
+  const int tt = tt_of(shp);
+  const size_t per_cta = static_cast<size_t>(full.fstride) * sizeof(double) +
+                         static_cast<size_t>(tt) * tt * sizeof(int32_t) + 2 * kAlign;
+  const size_t fixed = full.fact;  // everything placed before the factor stores
+  if (fixed + per_cta > kNoAllocScratchBytes) return SYLV_ERR_WORKSPACE;
+  const int cap = static_cast<int>(std::min<size_t>((kNoAllocScratchBytes - fixed) / per_cta, full.ncta));
+  const Layout L = make_layout_seq(shp, 0, cap);
+  if (L.total > kNoAllocScratchBytes) return SYLV_ERR_WORKSPACE;
+  char* ws = static_cast<char*>(scratch);
+  cudaStream_t s = o.stream;
+  Work w = make_work(ws, L, 1, o.timeout_ns);
+  // The scratch keeps the previous call's contents: clear the control block, the
+  // per-equation state, the level counters and the ready flags, which must start
+  // at zero; everything else is written before it is read.
+  if (cudaMemsetAsync(ws + L.zero_lo, 0, L.zero_hi - L.zero_lo, s) != cudaSuccess) return SYLV_ERR_CUDA;
+  Inst I{};
+  I.m = m;
+  I.n = n;
+  I.lda = lda;
+  I.ldb = ldb;
+  I.ldc = ldc;
+  I.A = A;
+  I.B = B;
+  I.C = C;
+  I.t = t;
+  I.pmax = shp[0].pmax;
+  I.qmax = shp[0].qmax;
+  I.robust = 1;
+  I.rb = 0;
+  I.cb = shp[0].pmax + 1;
+  I.tile = 0;
+  I.an = 0;
+  I.bn = static_cast<int64_t>(shp[0].pmax) * shp[0].pmax;
+  I.omega = o.omega;
+  k_set_inst<<<1, 1, 0, s>>>(w.inst, I);
+  if (run_prep<double>(w, L, 1, std::max(m, n), std::max(shp[0].pmax, shp[0].qmax), s) != cudaSuccess)
+    return SYLV_ERR_CUDA;
+  if (launch_dag_f64(t, true, w, std::min(L.max_tiles, L.ncta), s) != cudaSuccess) return SYLV_ERR_CUDA;
+  k_consistency<double><<<grid_for(static_cast<int64_t>(L.max_tiles) * 256), 256, 0, s>>>(w);
+  k_results<<<1, 32, 0, s>>>(w);
+  if (cudaGetLastError() != cudaSuccess) return SYLV_ERR_CUDA;
+  sylv_result r{};
+  if (cudaMemcpyAsync(&r, w.res, sizeof(r), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SYLV_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SYLV_ERR_CUDA;
+  if (result) *result = r;
+  return r.info;
+}

@@ -79,6 +79,8 @@ SIGNATURES = {
     "sylv_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sylv_version": (ctypes.c_char_p, []),
     "sylv_diag_wait_timeout": (ctypes.c_int, [_i64, _vp]),
+    "sylv_tri_solve_noalloc": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _i64, _vp,
+                                              ctypes.POINTER(sylv_result)]),
     "sylv_profile": (ctypes.c_int, [ctypes.c_int]),
     "sylv_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }
@@ -147,6 +149,14 @@ def sylv_tri_solve(m, n, A, lda, B, ldb, C, ldc, tile=0):
     sc = ctypes.c_double(0.0)
     rc = load().sylv_tri_solve(m, n, A, lda, B, ldb, C, ldc, tile, ctypes.byref(sc))
     return rc, sc.value
+
+
+def sylv_tri_solve_noalloc(m, n, A, lda, B, ldb, C, ldc, tile=0, stream=None):
+    """Device pointers (ints).  Solves with the library's fixed device scratch (no
+    allocation); returns (status, sylv_result)."""
+    res = sylv_result()
+    rc = load().sylv_tri_solve_noalloc(m, n, A, lda, B, ldb, C, ldc, tile, stream, ctypes.byref(res))
+    return rc, res
 
 
 def sylv_tri_solve_ex(m, n, A, lda, B, ldb, C, ldc, opts: sylv_opts | None = None, result=None):

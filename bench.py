@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--tile", type=int, default=0, help="override the workload's tile size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="solve", choices=["solve", "mixed", "batched", "adjoint"],
+                    help="solve: the headline robust FP64 solve; mixed: FP32 + refinement vs FP64 at "
+                         "m=n=8000; batched: 4096 uneven equations; adjoint: 256 Lyapunov forward+backward")
     return ap.parse_args()
 
 
@@ -311,10 +314,150 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _timed(fn, steps, warmup, stream):
+    """Per-step CUDA-event time (ms) of fn(i), warm-up excluded; returns (mean, list)."""
+    import torch
+    for i in range(warmup):
+        fn(i)
+    torch.cuda.synchronize()
+    ts = []
+    for i in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn(warmup + i)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return sum(ts) / len(ts), ts
+
+
+def run_mixed(args):
+    """FP32 correction solves + FP64-accurate residual vs the plain robust FP64 solve,
+    m = n = 8000, well-conditioned generator (the accuracy claim needs it)."""
+    import torch
+    from paper_1905_10574_gb300 import build, inputs, sylv
+    build.build()
+    name = args.workload if args.workload != WORKLOAD else "wellcond_8000"
+    A, B, C, w = inputs.workload(name)
+    m, n = w["m"], w["n"]
+    dev = torch.device("cuda", 0)
+    Ad, Bd, C0 = (torch.from_numpy(x).to(dev) for x in (A, B, C))
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for prec in ("fp64", "fp32_refine"):
+        opts = sylv.make_opts(tile=args.tile or w["tile"], precision=prec, stream=stream.cuda_stream, sync=True)
+        wsb = sylv.sylv_workspace_size(m, n, opts)
+        wsbuf = torch.empty(wsb + 256, dtype=torch.uint8, device=dev)
+        opts.workspace = (wsbuf.data_ptr() + 255) // 256 * 256
+        opts.workspace_bytes = wsb
+        Cs = [C0.clone() for _ in range(args.warmup + args.steps)]
+        res = sylv.sylv_result()
+
+        def fn(i):
+            rc = sylv.sylv_tri_solve_ex(m, n, Ad.data_ptr(), Ad.stride(1), Bd.data_ptr(), Bd.stride(1),
+                                        Cs[i].data_ptr(), Cs[i].stride(1), opts, res)
+            if rc not in (0, 1):
+                raise sylv.SylvError(rc, prec)
+
+        ms, _ = _timed(fn, args.steps, args.warmup, stream)
+        out[prec] = {"ms_per_solve": ms, "solves_per_s": 1000.0 / ms, "info": res.info, "iters": res.iters,
+                     "last_update": res.last_update}
+        del Cs, wsbuf
+    line = {"metric": "mixed-precision solves/s", "value": out["fp32_refine"]["solves_per_s"], "unit": "solves/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32+f64",
+            "data": "synthetic", "config": {"workload": name, "m": m, "n": n}, "fp64": out["fp64"],
+            "fp32_refine": out["fp32_refine"],
+            "speedup_vs_fp64": out["fp64"]["ms_per_solve"] / out["fp32_refine"]["ms_per_solve"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args):
+    """4096 independent equations, m, n log-uniform in [16, 512], one batched launch."""
+    import numpy as np
+    import torch
+    from paper_1905_10574_gb300 import build, inputs, sylv
+    build.build()
+    count = 4096
+    shapes = inputs.batch_shapes(count, 16, 512, seed=1234)
+    dev = torch.device("cuda", 0)
+    As, Bs, C0s = [], [], []
+    for i, (m, n) in enumerate(shapes):
+        A, B, C = inputs.problem(m, n, 10000 + i, kind="wellcond")
+        As.append(torch.from_numpy(A).to(dev))
+        Bs.append(torch.from_numpy(B).to(dev))
+        C0s.append(torch.from_numpy(C).to(dev))
+    Cs = [c.clone() for c in C0s]
+    stream = torch.cuda.current_stream(dev)
+    opts = sylv.make_opts(tile=args.tile, stream=stream.cuda_stream)
+    plan = sylv.sylv_batch_create([m for m, _ in shapes], [n for _, n in shapes], [a.data_ptr() for a in As],
+                                  [a.stride(1) for a in As], [b.data_ptr() for b in Bs], [b.stride(1) for b in Bs],
+                                  [c.data_ptr() for c in Cs], [c.stride(1) for c in Cs], opts)
+    flops = sum(2.0 * m * n * (m + n) for m, n in shapes)
+
+    def refill():
+        for c, c0 in zip(Cs, C0s):
+            c.copy_(c0)
+
+    ts = []
+    for i in range(args.warmup + args.steps):
+        refill()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rc = sylv.sylv_batch_execute(plan, stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if rc:
+            raise sylv.SylvError(rc, "batch")
+        if i >= args.warmup:
+            ts.append(a.elapsed_time(b))
+    rc, res = sylv.sylv_batch_results(plan, count)
+    sylv.sylv_batch_destroy(plan)
+    ms = sum(ts) / len(ts)
+    line = {"metric": "batched solves/s", "value": count / (ms / 1000), "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "config": {"count": count, "m_n": "log-uniform [16,512]", "tile": args.tile or 32},
+            "gflops_2mnmn": flops / (ms / 1000) / 1e9, "worst_info": max(r.info for r in res)}
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint(args):
+    """256 Lyapunov-type equations A Y + Y A^T = C, m = n = 512: forward + backward."""
+    import torch
+    from paper_1905_10574_gb300 import build, inputs, sylv
+    build.build()
+    dev = torch.device("cuda", 0)
+    count, m = 256 if args.steps else 256, 512
+    probs = []
+    for i in range(count):
+        A = inputs.quasi_triangular(m, 20000 + i, kind="wellcond")
+        probs.append((torch.from_numpy(A).to(dev), torch.from_numpy(inputs.rhs(m, m, 30000 + i)).to(dev),
+                      torch.from_numpy(inputs.rhs(m, m, 40000 + i)).to(dev)))
+    stream = torch.cuda.current_stream(dev)
+
+    def fn(_):
+        for A, C, W in probs:
+            At = A.detach().requires_grad_(True)
+            Y = sylv.SylvesterSolve.apply(At, At, C, False, True, 0)
+            (W * Y).sum().backward()
+
+    ms, _ = _timed(fn, max(1, args.steps // 4), 1, stream)
+    line = {"metric": "differentiable Lyapunov solves/s (forward+backward)", "value": count / (ms / 1000),
+            "unit": "solves/s", "n_gpus": 1, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "config": {"count": count, "m": m, "n": m}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "mixed":
+        run_mixed(args)
+    elif args.mode == "batched":
+        run_batched(args)
+    elif args.mode == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

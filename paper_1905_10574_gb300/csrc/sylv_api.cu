@@ -346,7 +346,7 @@ struct SolvePlan {
   Shape shape;
   Layout L;            // tile workspace (FP64 solve, or the FP32 correction solves)
   size_t off_at, off_bt;  // anti-transposed A, B (FP64) when transposed
-  size_t off_a32, off_b32, off_rf, off_r, off_x, off_slots, off_rs;  // FP32 + refinement
+  size_t off_a32, off_b32, off_al, off_bl, off_rf, off_r, off_x, off_slots, off_rs;  // FP32 + refinement
   size_t total;
 };
 
@@ -363,6 +363,10 @@ SolvePlan plan_solve(int64_t m, int64_t n, const Opts& o) {
     P.off_a32 = off;
     off = align_up(off + sizeof(float) * m * m);
     P.off_b32 = off;
+    off = align_up(off + sizeof(float) * n * n);
+    P.off_al = off;
+    off = align_up(off + sizeof(float) * m * m);
+    P.off_bl = off;
     off = align_up(off + sizeof(float) * n * n);
     P.off_rf = off;
     off = align_up(off + sizeof(float) * m * n);
@@ -422,14 +426,21 @@ int enqueue_fp64(const SolvePlan& P, char* ws, const double* A, int64_t lda, con
 }
 
 // Enqueue the FP32 + refinement solve of an untransposed problem:
-//   X = 0, R = C;  repeat: solve A D + D B = R in FP32 (robust, scaled to FP32
-//   range), X += D, R = C - A X - X B in FP64, until max|D| <= tol max|X|.
+//   A, B -> float pairs (hi, lo) scaled by one power of two (hi is the FP32 solve's
+//   matrix; the pair carries ~48 bits for the residual);
+//   X = 0, R = C;  repeat: solve A D + D B = R in FP32 (robust, R scaled into FP32
+//   range), X += D (binary64), R = C - A X - X B in double-float arithmetic on the
+//   FP32 pipes, until max|D_k| <= tol max|X| or, once the corrections contract,
+//   max|D_k| * (max|D_k| / max|D_{k-1}|) <= tol max|X| (the size the next
+//   correction would have).
 int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, const double* B, int64_t ldb,
                    double* C, int64_t ldc, const Opts& o, sylv_result* dres) {
   const int64_t m = P.shape.m, n = P.shape.n;
   cudaStream_t s = o.stream;
-  float* A32 = reinterpret_cast<float*>(ws + P.off_a32);
-  float* B32 = reinterpret_cast<float*>(ws + P.off_b32);
+  float* Ah = reinterpret_cast<float*>(ws + P.off_a32);
+  float* Bh = reinterpret_cast<float*>(ws + P.off_b32);
+  float* Al = reinterpret_cast<float*>(ws + P.off_al);
+  float* Bl = reinterpret_cast<float*>(ws + P.off_bl);
   float* Rf = reinterpret_cast<float*>(ws + P.off_rf);
   double* R = reinterpret_cast<double*>(ws + P.off_r);
   double* X = reinterpret_cast<double*>(ws + P.off_x);
@@ -446,12 +457,11 @@ int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, c
   if (cudaMemsetAsync(rs, 0, sizeof(RefineState), s) != cudaSuccess) return SYLV_ERR_CUDA;
   if (cudaMemsetAsync(X, 0, sizeof(double) * m * n, s) != cudaSuccess) return SYLV_ERR_CUDA;
   if (cudaMemsetAsync(ws + L.zero_lo, 0, L.zero_hi - L.zero_lo, s) != cudaSuccess) return SYLV_ERR_CUDA;
-  // A and B scaled by one common power of two into FP32 (the solution is unchanged).
   k_maxabs_quasi<<<grid_for(m * m), 256, 0, s>>>(A, lda, m, amax);
   k_maxabs_quasi<<<grid_for(n * n), 256, 0, s>>>(B, ldb, n, bmax);
-  k_to_float<<<grid_for(m * m), 256, 0, s>>>(A, lda, A32, m, m, m, amax, bmax, 1, nullptr);
-  k_to_float<<<grid_for(n * n), 256, 0, s>>>(B, ldb, B32, n, n, n, amax, bmax, 1, nullptr);
-  std::vector<Inst> I = make_insts({P.shape}, L, {A32}, {m}, {B32}, {n}, {Rf}, {m}, 1, o.omega);
+  k_split_df<<<grid_for(m * m), 256, 0, s>>>(A, lda, Ah, Al, m, m, m, amax, bmax, 1);
+  k_split_df<<<grid_for(n * n), 256, 0, s>>>(B, ldb, Bh, Bl, n, n, n, amax, bmax, 1);
+  std::vector<Inst> I = make_insts({P.shape}, L, {Ah}, {m}, {Bh}, {n}, {Rf}, {m}, 1, o.omega);
   k_set_inst<<<1, 1, 0, s>>>(w.inst, I[0]);
   cudaError_t e = run_prep<float>(w, L, 1, std::max(m, n), std::max(P.shape.pmax, P.shape.qmax), s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
@@ -459,11 +469,13 @@ int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, c
     unsigned long long* rmax = slots + 2 + 3 * it;
     unsigned long long* dmax = rmax + 1;
     unsigned long long* xmax = rmax + 2;
-    if (it == 0)
+    if (it == 0) {
       k_copy_max<<<grid_for(m * n), 256, 0, s>>>(C, ldc, R, m, m, n, rmax);
-    else
-      k_residual<<<dim3((m + GT - 1) / GT, (n + GT - 1) / GT), 256, 0, s>>>(A, lda, B, ldb, C, ldc, X, m, R, m, m,
-                                                                             n, rmax, &rs->conv);
+    } else {
+      const unsigned long long* xprev = slots + 2 + 3 * (it - 1) + 2;
+      k_residual_df<<<dim3((m + GT - 1) / GT, (n + GT - 1) / GT), 256, 0, s>>>(
+          Ah, Al, m, Bh, Bl, n, C, ldc, X, m, R, m, m, n, amax, bmax, xprev, rmax, &rs->conv);
+    }
     k_to_float<<<grid_for(m * n), 256, 0, s>>>(R, m, Rf, m, m, n, rmax, nullptr, 0, &rs->conv);
     if (it > 0) {
       if (cudaMemsetAsync(w.tflag, 0, sizeof(int32_t) * L.sum_tiles, s) != cudaSuccess) return SYLV_ERR_CUDA;
@@ -473,7 +485,7 @@ int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, c
     if (e != cudaSuccess) return SYLV_ERR_CUDA;
     k_accumulate<<<grid_for(static_cast<int64_t>(L.max_tiles) * 256), 256, 0, s>>>(w, X, m, rmax, amax, bmax, dmax,
                                                                                    xmax, &rs->conv);
-    k_refine_check<<<1, 1, 0, s>>>(rs, dmax, xmax, o.tol, w);
+    k_refine_check<<<1, 1, 0, s>>>(rs, dmax, xmax, it > 0 ? dmax - 3 : nullptr, o.tol, w);
   }
   k_copy<<<grid_for(m * n), 256, 0, s>>>(X, m, C, ldc, m, n);
   k_refine_result<<<1, 1, 0, s>>>(rs, w.res, o.maxit);

@@ -39,8 +39,12 @@ struct DagSmem {
   T R[TT * LDG];                      // right GEMM operand, k-major; B_ll in the diagonal phases
   T Y[TT * LDY];                      // the tile being solved (column-major)
   double zbuf[TT][4];                 // this step's solved 1x1/2x2 blocks, by block column
-  double acolmax[TT];                 // per A block kb: max_r<start(kb) sum_i in kb |A[r,i]|
-  double bcolmax[TT];                 // per B block lb: max_c>=end(lb) sum_j in lb |B[j,c]|
+  static constexpr bool kFactSmem = (TT <= 32);  // small-system factors kept in shared memory
+  double fact[kFactSmem ? 5 * TT * TT : 1];      // factor store (see pair_offset), if kFactSmem
+  int factp[kFactSmem ? TT * TT : 1];            // packed pivots, if kFactSmem
+  unsigned long long acolmax[TT];     // per A block kb: max_r<start(kb) sum_i in kb |A[r,i]| (bits)
+  unsigned long long bcolmax[TT];     // per B block lb: max_c>=end(lb) sum_j in lb |B[j,c]| (bits)
+  short pr0[TT], pma[TT];             // this step: first row and height of the block solved in column block lb
   unsigned long long pzm[TT];         // max |z| of each solved block of this step (bit pattern)
   unsigned long long wmax[kThreads / 32];  // per-warp max |y| over unsolved elements
   int pe[TT];                         // scale exponent of each solved block of this step
@@ -144,8 +148,10 @@ __device__ inline int pair_factor(int ma, int nb, const double* a, const double*
       M[st][st] = smin;
       pack |= 1 << 16;
     }
+    const double rcp = 1.0 / M[st][st];
+    out[s * s + st] = rcp;
     for (int u = st + 1; u < s; ++u) {
-      const double l = M[u][st] / M[st][st];
+      const double l = M[u][st] * rcp;
       M[u][st] = l;
       for (int v = st + 1; v < s; ++v) M[u][v] = fma(-l, M[st][v], M[u][v]);
     }
@@ -153,59 +159,77 @@ __device__ inline int pair_factor(int ma, int nb, const double* a, const double*
   for (int u = 0; u < s; ++u) pack |= (cperm[u] & 3) << (8 + 2 * u);
   for (int u = 0; u < s; ++u)
     for (int v = 0; v < s; ++v) out[u * s + v] = M[u][v];
-  for (int u = 0; u < s; ++u) out[s * s + u] = 1.0 / M[u][u];
   return pack;
 }
 
-// Right-hand side of a factored pair: r (vec order, length s) in, Z (vec order) out.
-// Returns log2(beta).
-__device__ inline int pair_solve(int s, const double* f, int pack, double* r, double omega, int eo, bool robust) {
+// Right-hand side of a factored pair of size S (1, 2 or 4): r (vec order) in, Z out.
+// Returns log2(beta).  Compile-time S keeps r in registers (interchanges by selects).
+template <int S>
+__device__ __forceinline__ int pair_solve(const double* f, int pack, double (&r)[4], double omega, int eo,
+                                          bool robust) {
   int lb = 0;
-  for (int st = 0; st < s; ++st) {
+#pragma unroll
+  for (int st = 0; st < S; ++st) {
     const int pr = (pack >> (2 * st)) & 3;
-    if (pr != st) {
-      const double tmp = r[st];
-      r[st] = r[pr];
-      r[pr] = tmp;
-    }
+#pragma unroll
+    for (int k = st + 1; k < S; ++k)
+      if (pr == k) {
+        const double tmp = r[st];
+        r[st] = r[k];
+        r[k] = tmp;
+      }
   }
-  for (int st = 0; st < s; ++st)
-    for (int u = st + 1; u < s; ++u) {
-      const double l = f[u * s + st];
+#pragma unroll
+  for (int st = 0; st < S; ++st)
+#pragma unroll
+    for (int u = st + 1; u < S; ++u) {
+      const double l = f[u * S + st];
       if (robust) {
         const int z = guard_update(r[u], l, r[st], omega, eo);
         if (z) {
-          for (int w = 0; w < s; ++w) r[w] = mul2(r[w], z);
+#pragma unroll
+          for (int w = 0; w < S; ++w) r[w] = mul2(r[w], z);
           lb += z;
         }
       }
       r[u] = fma(-l, r[st], r[u]);
     }
-  for (int i = s - 1; i >= 0; --i) {
-    for (int v = i + 1; v < s; ++v) {
-      const double uiv = f[i * s + v];
+#pragma unroll
+  for (int i = S - 1; i >= 0; --i) {
+#pragma unroll
+    for (int v = i + 1; v < S; ++v) {
+      const double uiv = f[i * S + v];
       if (robust) {
         const int z = guard_update(r[i], uiv, r[v], omega, eo);
         if (z) {
-          for (int w = 0; w < s; ++w) r[w] = mul2(r[w], z);
+#pragma unroll
+          for (int w = 0; w < S; ++w) r[w] = mul2(r[w], z);
           lb += z;
         }
       }
       r[i] = fma(-uiv, r[v], r[i]);
     }
-    const double rcp = f[s * s + i];
+    const double rcp = f[S * S + i];
     if (robust) {
-      const int z = guard_division(r[i], f[i * s + i], rcp, omega, eo);
+      const int z = guard_division(r[i], f[i * S + i], rcp, omega, eo);
       if (z) {
-        for (int w = 0; w < s; ++w) r[w] = mul2(r[w], z);
+#pragma unroll
+        for (int w = 0; w < S; ++w) r[w] = mul2(r[w], z);
         lb += z;
       }
     }
     r[i] = r[i] * rcp;
   }
-  double x[4];
-  for (int u = 0; u < s; ++u) x[(pack >> (8 + 2 * u)) & 3] = r[u];
-  for (int u = 0; u < s; ++u) r[u] = x[u];
+  double x[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int u = 0; u < S; ++u) {
+    const int cu = (pack >> (8 + 2 * u)) & 3;
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+      if (cu == t) x[t] = r[u];
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) r[u] = x[u];
   return lb;
 }
 
@@ -247,15 +271,21 @@ __device__ __forceinline__ int pair_offset(const DagSmem<TT, T>& sh, int kb, int
 // tile, while the tile's producers may still be running.
 template <int TT, typename T, bool ROBUST>
 __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const T* B, int64_t ldb, int r0, int c0,
-                             int mt, int nt, double smin, double* fact, int* factp) {
+                             int mt, int nt, double smin, double* gfact, int* gfactp) {
   constexpr int LDY = DagSmem<TT, T>::LDY;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* fact = DagSmem<TT, T>::kFactSmem ? sh.fact : gfact;
+  int* factp = DagSmem<TT, T>::kFactSmem ? sh.factp : gfactp;
   T* Ak = sh.L;
   T* Bk = sh.R;
   for (int idx = tid; idx < TT * TT; idx += kThreads) {
     const int r = idx % TT, c = idx / TT;
     Ak[r + c * LDY] = (r < mt && c < mt && r <= c + 1) ? __ldg(&A[(r0 + r) + static_cast<int64_t>(r0 + c) * lda]) : T(0);
     Bk[r + c * LDY] = (r < nt && c < nt && r <= c + 1) ? __ldg(&B[(c0 + r) + static_cast<int64_t>(c0 + c) * ldb]) : T(0);
+  }
+  for (int i = tid; i < TT; i += kThreads) {
+    sh.acolmax[i] = 0ull;
+    sh.bcolmax[i] = 0ull;
   }
   __syncthreads();
   if (warp == 0) {
@@ -284,25 +314,24 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
     sh.pa[pb] = off;
   }
   if (ROBUST) {
-    for (int kb = tid; kb < pb; kb += kThreads) {
+    // acolmax: rows above each A block; bcolmax: columns right of each B block.
+    for (int idx = tid; idx < pb * TT; idx += kThreads) {
+      const int kb = idx / TT, r = idx % TT;
       const int ra = sh.astart[kb], re = sh.astart[kb + 1];
-      double best = 0.0;
-      for (int r = 0; r < ra; ++r) {
+      if (r < ra) {
         double sum = 0.0;
         for (int i = ra; i < re; ++i) sum += fabs(static_cast<double>(Ak[r + i * LDY]));
-        best = fmax(best, sum);
+        atomicMax(&sh.acolmax[kb], abs_bits(sum));
       }
-      sh.acolmax[kb] = best;
     }
-    for (int lb = tid; lb < qb; lb += kThreads) {
+    for (int idx = tid; idx < qb * TT; idx += kThreads) {
+      const int lb = idx / TT, c = idx % TT;
       const int j0 = sh.bstart[lb], j1 = sh.bstart[lb + 1];
-      double best = 0.0;
-      for (int c = j1; c < nt; ++c) {
+      if (c >= j1 && c < nt) {
         double sum = 0.0;
         for (int j = j0; j < j1; ++j) sum += fabs(static_cast<double>(Bk[j + c * LDY]));
-        best = fmax(best, sum);
+        atomicMax(&sh.bcolmax[lb], abs_bits(sum));
       }
-      sh.bcolmax[lb] = best;
     }
   }
   __syncthreads();
@@ -336,11 +365,13 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
 // When all exponents are far from omega' the decision is taken from the exponent
 // fields alone (g = e_min, no FP64 work); otherwise warp 0 evaluates ProtectUpdate.
 template <int TT, typename T, bool ROBUST>
-__device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, const double* fact, const int* factp) {
+__device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, const double* gfact, const int* gfactp) {
   constexpr int LDY = DagSmem<TT, T>::LDY;
   constexpr int CSTEP = kThreads / TT;
   constexpr int NC = TT / CSTEP;  // columns owned per thread
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* fact = DagSmem<TT, T>::kFactSmem ? sh.fact : gfact;
+  const int* factp = DagSmem<TT, T>::kFactSmem ? sh.factp : gfactp;
   const T* Ak = sh.L;
   const T* Bk = sh.R;
   T* Ys = sh.Y;
@@ -348,7 +379,8 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
   const double omh = 0.5 * omega;
   const int eo = floor_log2(omh);
 
-  // Element ownership: row tid % TT, columns tid / TT + j * CSTEP.
+  // Element ownership: row tid % TT, columns tid / TT + j * CSTEP (j < NC); the
+  // per-column data below is fixed for the whole solve.
   const int my_r = tid % TT;
   const int my_c0 = tid / TT;
   const bool row_ok = my_r < mt;
@@ -356,12 +388,23 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
   const int dr = pb - 1 - kb_r;
   const int ra_r = row_ok ? sh.astart[kb_r] : 0;
   const int ma_r = row_ok ? sh.astart[kb_r + 1] - ra_r : 1;
+  const int rr_in = my_r - ra_r;  // row within its block
+  bool okj[NC];
+  int lbcj[NC], offj[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const int c = my_c0 + j * CSTEP;
+    okj[j] = row_ok && c < nt;
+    lbcj[j] = okj[j] ? sh.colblk[c] : 0;
+    offj[j] = okj[j] ? c - sh.bstart[lbcj[j]] : 0;
+  }
 
   // Initial U (and a pre-scaling if the tile exceeds omega').
   unsigned long long um = 0;
-  if (row_ok)
-    for (int c = my_c0; c < nt; c += CSTEP) {
-      const unsigned long long b = abs_bits(static_cast<double>(Ys[my_r + c * LDY]));
+#pragma unroll
+  for (int j = 0; j < NC; ++j)
+    if (okj[j]) {
+      const unsigned long long b = abs_bits(static_cast<double>(Ys[my_r + (my_c0 + j * CSTEP) * LDY]));
       um = b > um ? b : um;
     }
   um = warp_max_u64(um);
@@ -377,8 +420,12 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
     const double U0 = bits_to_double(u0);
     if (U0 > omh) {  // keep every element within omega'
       const int z = floor_log2(omh) - ceil_log2(U0);
-      if (row_ok)
-        for (int c = my_c0; c < nt; c += CSTEP) Ys[my_r + c * LDY] = mul2(Ys[my_r + c * LDY], z);
+#pragma unroll
+      for (int j = 0; j < NC; ++j)
+        if (okj[j]) {
+          T* yp = &Ys[my_r + (my_c0 + j * CSTEP) * LDY];
+          *yp = mul2(*yp, z);
+        }
       if (tid == 0) sh.e_diag = z;
       __syncthreads();
       if (lane == 0) sh.wmax[warp] = abs_bits(mul2(U0, z));
@@ -391,7 +438,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
   for (int s = 0; s < nsteps; ++s) {
     const int lb_lo = max(0, s - (pb - 1));
     const int lb_hi = min(s, qb - 1);
-    // Phase A: this step's blocks, one thread each.
+    // Phase A: this step's blocks, one thread each; publish their geometry.
     for (int lb = lb_lo + tid; lb <= lb_hi; lb += kThreads) {
       const int kb = pb - 1 - (s - lb);
       const int r0 = sh.astart[kb], ma = sh.astart[kb + 1] - r0;
@@ -400,23 +447,36 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
       const int pack = factp[kb * TT + lb];
       if (pack & (1 << 16)) near = true;
       double rr[4];
-      for (int u = 0; u < sz; ++u) rr[u] = static_cast<double>(Ys[(r0 + u % ma) + (c0 + u / ma) * LDY]);
-      const int e = pair_solve(sz, fact + pair_offset(sh, kb, lb, ma), pack, rr, omh, eo, ROBUST);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        rr[u] = (u < sz) ? static_cast<double>(Ys[(r0 + (ma == 2 ? (u & 1) : 0)) + (c0 + (ma == 2 ? (u >> 1) : u)) * LDY])
+                         : 0.0;
+      const double* f = fact + pair_offset(sh, kb, lb, ma);
+      int e;
+      if (sz == 1)
+        e = pair_solve<1>(f, pack, rr, omh, eo, ROBUST);
+      else if (sz == 2)
+        e = pair_solve<2>(f, pack, rr, omh, eo, ROBUST);
+      else
+        e = pair_solve<4>(f, pack, rr, omh, eo, ROBUST);
       unsigned long long zm = 0;
+#pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const double v = (u < sz) ? rr[u] : 0.0;
-        sh.zbuf[lb][u] = v;
-        const unsigned long long bv = abs_bits(v);
+        sh.zbuf[lb][u] = rr[u];
+        const unsigned long long bv = abs_bits(rr[u]);
         zm = bv > zm ? bv : zm;
       }
       sh.pe[lb] = e;
       sh.pzm[lb] = zm;
+      sh.pr0[lb] = static_cast<short>(r0);
+      sh.pma[lb] = static_cast<short>(ma);
       if (ROBUST) {
         unsigned long long u0 = 0;
         for (int w = 0; w < kThreads / 32; ++w) u0 = sh.wmax[w] > u0 ? sh.wmax[w] : u0;
         const int ez = ub_log2(bits_to_double(zm));
         const bool fast = e == 0 && ub_log2(bits_to_double(u0)) + 2 <= eo &&
-                          ub_log2(sh.acolmax[kb]) + ez + 2 <= eo && ez + ub_log2(sh.bcolmax[lb]) + 2 <= eo;
+                          ub_log2(bits_to_double(sh.acolmax[kb])) + ez + 2 <= eo &&
+                          ez + ub_log2(bits_to_double(sh.bcolmax[lb])) + 2 <= eo;
         if (!fast) sh.slow = 1;
       }
     }
@@ -432,8 +492,8 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
         for (int lb = lb_lo + lane; lb <= lb_hi; lb += 32) {
           const int kb = pb - 1 - (s - lb);
           zs = fmax(zs, mul2(bits_to_double(sh.pzm[lb]), emin - sh.pe[lb]));
-          as = fmax(as, sh.acolmax[kb]);
-          bs = fmax(bs, sh.bcolmax[lb]);
+          as = fmax(as, bits_to_double(sh.acolmax[kb]));
+          bs = fmax(bs, bits_to_double(sh.bcolmax[lb]));
         }
         zs = warp_max(zs);
         as = warp_max(as);
@@ -464,44 +524,48 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
       g = sh.g;
     }
     // Phase C: every owned element takes its scale and this step's contributions;
-    // U for the next step is the max over unsolved elements.
+    // U for the next step is the max over unsolved elements.  The B-side block of
+    // this row (lbs) is the same for all of the thread's columns.
+    const int lbs = s - dr;
+    const bool bs_ok = row_ok && lbs >= 0 && lbs < qb;
+    int cs0 = 0, nbs = 0;
+    double zb0 = 0.0, zb1 = 0.0;
+    if (bs_ok) {
+      cs0 = sh.bstart[lbs];
+      nbs = sh.bstart[lbs + 1] - cs0;
+      zb0 = sh.zbuf[lbs][rr_in];
+      zb1 = (nbs == 2) ? sh.zbuf[lbs][rr_in + ma_r] : 0.0;
+    }
     unsigned long long wm = 0;
-    if (row_ok) {
-#pragma unroll 4
-      for (int j = 0; j < NC; ++j) {
-        const int c = my_c0 + j * CSTEP;
-        if (c >= nt) break;
-        const int lbc = sh.colblk[c];
-        const int dd = dr + lbc;
-        if (dd < s) {
-          if (g != 0) Ys[my_r + c * LDY] = mul2(Ys[my_r + c * LDY], g);
-          continue;
-        }
-        T* yp = &Ys[my_r + c * LDY];
-        if (dd == s) {
-          const int cb0 = sh.bstart[lbc];
-          *yp = static_cast<T>(sh.zbuf[lbc][(my_r - ra_r) + ma_r * (c - cb0)]);
-          continue;
-        }
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      if (!okj[j]) continue;
+      const int c = my_c0 + j * CSTEP;
+      const int lbc = lbcj[j];
+      const int dd = dr + lbc;
+      T* yp = &Ys[my_r + c * LDY];
+      if (dd < s) {
+        if (g != 0) *yp = mul2(*yp, g);
+      } else if (dd == s) {
+        *yp = static_cast<T>(sh.zbuf[lbc][rr_in + ma_r * offj[j]]);
+      } else {
         double y = static_cast<double>(*yp);
         if (g != 0) y = mul2(y, g);
-        if (s >= lbc && s - lbc < dr) {  // block (kbs, lbc) below this row, solved now
-          const int kbs = pb - 1 - (s - lbc);
-          const int rs0 = sh.astart[kbs], mas = sh.astart[kbs + 1] - rs0;
-          const int cb0 = sh.bstart[lbc];
-          for (int ii = 0; ii < mas; ++ii)
-            y = fma(-static_cast<double>(Ak[my_r + (rs0 + ii) * LDY]), sh.zbuf[lbc][ii + mas * (c - cb0)], y);
+        double tb = 0.0;
+        if (bs_ok && lbs < lbc) {  // block (kb_r, lbs) left of this column, solved now
+          tb = zb0 * static_cast<double>(Bk[cs0 + c * LDY]);
+          if (nbs == 2) tb = fma(zb1, static_cast<double>(Bk[cs0 + 1 + c * LDY]), tb);
         }
-        if (s >= dr && s - dr < lbc) {  // block (kb_r, lbs) left of this column, solved now
-          const int lbs = s - dr;
-          const int cs0 = sh.bstart[lbs], nbs = sh.bstart[lbs + 1] - cs0;
-          for (int jj = 0; jj < nbs; ++jj)
-            y = fma(-sh.zbuf[lbs][(my_r - ra_r) + ma_r * jj], static_cast<double>(Bk[(cs0 + jj) + c * LDY]), y);
+        if (s >= lbc && s - lbc < dr) {  // block below this row in column block lbc, solved now
+          const int rs0 = sh.pr0[lbc], mas = sh.pma[lbc];
+          y = fma(-static_cast<double>(Ak[my_r + rs0 * LDY]), sh.zbuf[lbc][mas * offj[j]], y);
+          if (mas == 2) y = fma(-static_cast<double>(Ak[my_r + (rs0 + 1) * LDY]), sh.zbuf[lbc][1 + 2 * offj[j]], y);
         }
+        y -= tb;
         const T yt = static_cast<T>(y);
         *yp = yt;
-        const unsigned long long b = abs_bits(static_cast<double>(yt));
-        wm = b > wm ? b : wm;
+        const unsigned long long bb = abs_bits(static_cast<double>(yt));
+        wm = bb > wm ? bb : wm;
       }
     }
     if (ROBUST) {

@@ -252,21 +252,29 @@ struct RefineState {
   int pad;
   double last;
 };
+// After correction k: converged when max|D_k| <= tol max|X|, or when the
+// corrections contract (ratio rho = max|D_k| / max|D_{k-1}| < 1/2) and the next one
+// would be below the tolerance: rho max|D_k| <= tol max|X|.  dprev: previous max|D|
+// slot (null for the first correction, which is the whole first solution).
 __global__ void k_refine_check(RefineState* rs, const unsigned long long* dmax, const unsigned long long* xmax,
-                               double tol, const Work wf) {
+                               const unsigned long long* dprev, double tol, const Work wf) {
   if (rs->conv) return;
   const double d = __longlong_as_double(static_cast<long long>(*dmax));
   const double x = __longlong_as_double(static_cast<long long>(*xmax));
   rs->iters += 1;
   rs->last = (x > 0.0) ? d / x : (d > 0.0 ? 1.0 : 0.0);
   int e = wf.ctrl->err ? wf.ctrl->err : wf.st[0].err;
+  bool conv = d <= tol * x;
+  if (!conv && dprev) {
+    const double dp = __longlong_as_double(static_cast<long long>(*dprev));
+    const double rho = dp > 0.0 ? d / dp : 1.0;
+    if (rho < 0.5 && rho * d <= tol * x) conv = true;
+  }
   if (e) {
     rs->err = e;
     rs->conv = 1;
-  } else if (!(d <= tol * x)) {
-    rs->conv = 0;
   } else {
-    rs->conv = 1;
+    rs->conv = conv ? 1 : 0;
   }
 }
 
@@ -299,6 +307,183 @@ __global__ void k_scale_pow2(double* M, int64_t ld, int64_t m, int64_t n, int e)
     const int64_t r = t % m, c = t / m;
     M[r + c * ld] = mul2(M[r + c * ld], e);
   }
+}
+
+}  // namespace sylv
+
+namespace sylv {
+
+// ---------------------------------------------------------------- double-float residual
+// Binary64-accurate products on the binary32 pipes (GB300 runs FP32 FMA at 64x
+// the FP64 rate).  A value v is carried as a pair of floats (hi, lo), hi = fl32(v),
+// lo = fl32(v - hi), ~48 significant bits.  For a term a*x:
+//   p = ah*xh exactly as p + q with q = fma(ah, xh, -p)      (error-free product)
+//   c = ah*xl + al*xh                                         (cross terms, fp32)
+// and p enters the running sum s by Knuth's two-sum (s + p = s' + e exactly), while
+// q, c and e go to a compensation accumulator.  Relative error of a sum of K terms
+// ~ K * 2^-48 of sum |a||x| (each dropped al*xl is 2^-48 |a||x|).
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF split_df(double v) {
+  const float h = static_cast<float>(v);
+  return DF{h, static_cast<float>(v - static_cast<double>(h))};
+}
+__device__ __forceinline__ void df_acc(float& s, float& comp, float ah, float al, float xh, float xl) {
+  const float p = ah * xh;
+  const float q = fmaf(ah, xh, -p);
+  float c = fmaf(ah, xl, q);
+  c = fmaf(al, xh, c);
+  const float t = s + p;
+  const float bp = t - s;
+  const float e = (s - (t - bp)) + (p - bp);
+  s = t;
+  comp += e + c;
+}
+
+// R = C - A X - X B in binary64-accurate double-float arithmetic.  A (m x m) and B
+// (n x n) are given as float pairs scaled by 2^-sa (sa from the max |entry| of A
+// and B: AS = A 2^-sa, BS = B 2^-sa), restricted to their quasi-triangular parts;
+// X (binary64) is scaled by 2^-sx (sx from max |X|) and split on the fly.  The
+// kernel computes RS = C 2^-(sa+sx) - (AS XS + XS BS) = R 2^-(sa+sx) and stores
+// R = RS 2^(sa+sx) in binary64, plus max |R| in *rmax.  64 x 64 output tile per CTA,
+// 256 threads, 4 x 4 outputs each; k-chunks of 16 in shared memory.
+__global__ void __launch_bounds__(256) k_residual_df(const float* __restrict__ Ah, const float* __restrict__ Al,
+                                                     int64_t lda, const float* __restrict__ Bh,
+                                                     const float* __restrict__ Bl, int64_t ldb,
+                                                     const double* __restrict__ C, int64_t ldc,
+                                                     const double* __restrict__ X, int64_t ldx,
+                                                     double* __restrict__ R, int64_t ldr, int64_t m, int64_t n,
+                                                     const unsigned long long* slot_a,
+                                                     const unsigned long long* slot_b,
+                                                     const unsigned long long* slot_x, unsigned long long* rmax,
+                                                     const int* skip) {
+  if (skip && ld_volatile(skip)) return;
+  constexpr int LD = GT + 4;  // float rows, 16-byte aligned
+  __shared__ __align__(16) float Lh[GK * LD], Ll[GK * LD], Rh[GK * LD], Rl[GK * LD];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * GT, j0 = static_cast<int64_t>(blockIdx.y) * GT;
+  const unsigned long long ua = *slot_a, ub = *slot_b;
+  const int sa = norm_exp(ua > ub ? slot_a : slot_b);
+  const int sx = norm_exp(slot_x);
+  float s[4][4], comp[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      s[i][j] = 0.f;
+      comp[i][j] = 0.f;
+    }
+  // A X part: k >= i0 - 1 (A quasi-upper-triangular).
+  const int64_t ka = i0 > 0 ? i0 - 1 : 0;
+  for (int64_t k0 = ka; k0 < m; k0 += GK) {
+    for (int idx = tid; idx < GK * GT; idx += 256) {
+      const int r = idx % GT, kk = idx / GT;
+      const int64_t gr = i0 + r, gk = k0 + kk;
+      const bool ok = gr < m && gk < m && gr <= gk + 1;
+      Lh[kk * LD + r] = ok ? Ah[gr + gk * lda] : 0.f;
+      Ll[kk * LD + r] = ok ? Al[gr + gk * lda] : 0.f;
+      const int kk2 = idx % GK, c = idx / GK;
+      const int64_t gk2 = k0 + kk2, gc = j0 + c;
+      const DF x = (gk2 < m && gc < n) ? split_df(mul2(X[gk2 + gc * ldx], -sx)) : DF{0.f, 0.f};
+      Rh[kk2 * LD + c] = x.hi;
+      Rl[kk2 * LD + c] = x.lo;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      float ah[4], al[4], xh[4], xl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ah[i] = Lh[kk * LD + tx * 4 + i];
+        al[i] = Ll[kk * LD + tx * 4 + i];
+        xh[i] = Rh[kk * LD + ty * 4 + i];
+        xl[i] = Rl[kk * LD + ty * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) df_acc(s[i][j], comp[i][j], ah[i], al[i], xh[j], xl[j]);
+    }
+    __syncthreads();
+  }
+  // X B part: k <= j0 + GT (B quasi-upper-triangular).
+  const int64_t kb_end = (j0 + GT + 1 < n) ? j0 + GT + 1 : n;
+  for (int64_t k0 = 0; k0 < kb_end; k0 += GK) {
+    for (int idx = tid; idx < GK * GT; idx += 256) {
+      const int r = idx % GT, kk = idx / GT;
+      const int64_t gr = i0 + r, gk = k0 + kk;
+      const DF x = (gr < m && gk < n) ? split_df(mul2(X[gr + gk * ldx], -sx)) : DF{0.f, 0.f};
+      Lh[kk * LD + r] = x.hi;
+      Ll[kk * LD + r] = x.lo;
+      const int kk2 = idx % GK, c = idx / GK;
+      const int64_t gk2 = k0 + kk2, gc = j0 + c;
+      const bool ok = gk2 < n && gc < n && gk2 <= gc + 1;
+      Rh[kk2 * LD + c] = ok ? Bh[gk2 + gc * ldb] : 0.f;
+      Rl[kk2 * LD + c] = ok ? Bl[gk2 + gc * ldb] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      float xh[4], xl[4], bh[4], bl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        xh[i] = Lh[kk * LD + tx * 4 + i];
+        xl[i] = Ll[kk * LD + tx * 4 + i];
+        bh[i] = Rh[kk * LD + ty * 4 + i];
+        bl[i] = Rl[kk * LD + ty * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) df_acc(s[i][j], comp[i][j], xh[i], xl[i], bh[j], bl[j]);
+    }
+    __syncthreads();
+  }
+  double mx = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t r = i0 + tx * 4 + i, c = j0 + ty * 4 + j;
+      if (r < m && c < n) {
+        const double prod = static_cast<double>(s[i][j]) + static_cast<double>(comp[i][j]);
+        const double v = C[r + c * ldc] - mul2(prod, sa + sx);
+        R[r + c * ldr] = v;
+        mx = fmax(mx, fabs(v));
+      }
+    }
+  mx = warp_max(mx);
+  if ((tid & 31) == 0 && rmax) atomic_max_nonneg(rmax, mx);
+}
+
+// Float pair (hi, lo) of src * 2^-s, s from the larger of two max slots; quasi != 0
+// keeps only r <= c+1.
+__global__ void k_split_df(const double* __restrict__ src, int64_t lds, float* __restrict__ hi,
+                           float* __restrict__ lo, int64_t ldd, int64_t rows, int64_t cols,
+                           const unsigned long long* slot_a, const unsigned long long* slot_b, int quasi) {
+  const unsigned long long a = *slot_a, b = slot_b ? *slot_b : 0ull;
+  const int s = norm_exp(a > b ? slot_a : slot_b);
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < rows * cols;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t % rows, c = t / rows;
+    const double v = (!quasi || r <= c + 1) ? mul2(src[r + c * lds], -s) : 0.0;
+    const DF d = split_df(v);
+    hi[r + c * ldd] = d.hi;
+    lo[r + c * ldd] = d.lo;
+  }
+}
+
+// max |X| over an m x n matrix (bit pattern slot).
+__global__ void k_maxabs(const double* __restrict__ X, int64_t ldx, int64_t m, int64_t n, unsigned long long* out,
+                         const int* skip) {
+  if (skip && ld_volatile(skip)) return;
+  double mx = 0.0;
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < m * n;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    mx = fmax(mx, fabs(X[(t % m) + (t / m) * ldx]));
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, mx);
 }
 
 }  // namespace sylv

@@ -422,29 +422,29 @@ def run_batched(args):
 
 
 def run_adjoint(args):
-    """256 Lyapunov-type equations A Y + Y A^T = C, m = n = 512: forward + backward."""
+    """256 Lyapunov-type equations A Y + Y A^T = C, m = n = 512: batched forward +
+    hand-written batched adjoint (loss sum(W * Y)), through torch.autograd."""
     import torch
     from paper_1905_10574_gb300 import build, inputs, sylv
     build.build()
     dev = torch.device("cuda", 0)
-    count, m = 256 if args.steps else 256, 512
-    probs = []
-    for i in range(count):
-        A = inputs.quasi_triangular(m, 20000 + i, kind="wellcond")
-        probs.append((torch.from_numpy(A).to(dev), torch.from_numpy(inputs.rhs(m, m, 30000 + i)).to(dev),
-                      torch.from_numpy(inputs.rhs(m, m, 40000 + i)).to(dev)))
+    count, m = 256, 512
+    A = torch.stack([torch.from_numpy(inputs.quasi_triangular(m, 20000 + i, kind="wellcond")) for i in range(count)])
+    C = torch.stack([torch.from_numpy(inputs.rhs(m, m, 30000 + i)) for i in range(count)])
+    W = torch.stack([torch.from_numpy(inputs.rhs(m, m, 40000 + i)) for i in range(count)])
+    A, C, W = (sylv.batch_fortran(x.to(dev)) for x in (A, C, W))
     stream = torch.cuda.current_stream(dev)
 
     def fn(_):
-        for A, C, W in probs:
-            At = A.detach().requires_grad_(True)
-            Y = sylv.SylvesterSolve.apply(At, At, C, False, True, 0)
-            (W * Y).sum().backward()
+        At = A.detach().requires_grad_(True)
+        Ct = C.detach().requires_grad_(True)
+        Y = sylv.BatchSylvesterSolve.apply(At, At, Ct, False, True, 0)
+        (W * Y).sum().backward()
 
-    ms, _ = _timed(fn, max(1, args.steps // 4), 1, stream)
+    ms, _ = _timed(fn, max(1, args.steps), max(1, args.warmup), stream)
     line = {"metric": "differentiable Lyapunov solves/s (forward+backward)", "value": count / (ms / 1000),
             "unit": "solves/s", "n_gpus": 1, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64",
-            "data": "synthetic", "config": {"count": count, "m": m, "n": m}}
+            "data": "synthetic", "config": {"count": count, "m": m, "n": m, "form": "A Y + Y A^T = C, batched"}}
     print(json.dumps(line), flush=True)
 
 

@@ -132,6 +132,10 @@ size_t sylv_workspace_size(int64_t m, int64_t n, const sylv_opts* opts);
  * of one equation only ever waits on tiles of the same equation, Sec. 2.2's task
  * dependences).  Not in the paper.
  *
+ * opts->transa / opts->transb apply to every equation (the plan keeps
+ * anti-transposed copies of A_i / B_i and reverses C_i in place around the solve);
+ * FP32_REFINE is not available for batches.
+ *
  * sylv_batch_create builds a plan: it validates the HOST arrays m[i], n[i],
  * lda[i], ldb[i], ldc[i] and the device pointers A[i], B[i], C[i] (HOST arrays of
  * device pointers), picks each equation's tile size (opts->tile, or the built-in
@@ -181,6 +185,23 @@ int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, 
                             int64_t ldb, const double* Y, int64_t ldy, int64_t log2scale,
                             double* G, int64_t ldg, double* dA, int64_t ldda, double* dB,
                             int64_t lddb, const sylv_opts* opts, sylv_result* result);
+
+/*
+ * sylv_tri_solve_backward_batched -- sylv_tri_solve_backward for `count` equations
+ * at once (HOST arrays of sizes, leading dimensions, device pointers and the
+ * forward exponents log2scale[i]); the adjoint solves run as one batched launch
+ * (both transposes flipped), the gradient products and the dC scaling as one
+ * launch each.  dA / dB may be NULL (skip all) or hold NULL entries (skip one).
+ * results[i] (HOST) receives each adjoint solve's record.  Synchronizes
+ * opts->stream; allocates a plan and a small descriptor buffer internally.
+ */
+int sylv_tri_solve_backward_batched(int32_t count, const int64_t* m, const int64_t* n,
+                                    const double* const* A, const int64_t* lda,
+                                    const double* const* B, const int64_t* ldb,
+                                    const double* const* Y, const int64_t* ldy,
+                                    const int64_t* log2scale, double* const* G, const int64_t* ldg,
+                                    double* const* dA, const int64_t* ldda, double* const* dB,
+                                    const int64_t* lddb, const sylv_opts* opts, sylv_result* results);
 
 /*
  * sylv_tri_solve_noalloc -- the robust FP64 solve of sylv_tri_solve, for callers

@@ -83,7 +83,7 @@ int auto_tile(int64_t m, int64_t n) {
 // Byte offsets of the tile workspace of one launch (FP64 or FP32 solve).
 struct Layout {
   // zero-initialised region [zero_lo, zero_hi)
-  size_t ctrl, st, lvl_cnt, lvl_cur, tflag, zero_lo, zero_hi;
+  size_t ctrl, st, lvl_cnt, lvl_cur, tflag, smbusy, zero_lo, zero_hi;
   size_t lvl_off, inst, res, tasks, ibuf, texp, tnorm, dbuf, fact, factp;
   size_t total;
   int ncta;          // CTAs the DAG kernel may run (factor-store slots)
@@ -130,6 +130,8 @@ Layout make_layout_seq(const Seq& sh, size_t base, int cta_cap) {
   o = align_up(o + nlev * sizeof(int32_t));
   L.tflag = o;
   o = align_up(o + tiles * sizeof(int32_t));
+  L.smbusy = o;
+  o = align_up(o + 1024 * sizeof(int32_t));
   L.zero_hi = o;
   L.lvl_off = o;
   o = align_up(o + nlev * sizeof(int32_t));
@@ -223,6 +225,8 @@ Work make_work(char* ws, const Layout& L, int count, int64_t timeout_ns) {
   w.fact = reinterpret_cast<double*>(ws + L.fact);
   w.factp = reinterpret_cast<int32_t*>(ws + L.factp);
   w.fact_stride = L.fstride;
+  w.smbusy = reinterpret_cast<int32_t*>(ws + L.smbusy);
+  w.prio = 0;
   w.skip = nullptr;
   w.timeout_ns = timeout_ns;
   w.max_tiles = L.max_tiles;
@@ -346,7 +350,7 @@ struct SolvePlan {
   Shape shape;
   Layout L;            // tile workspace (FP64 solve, or the FP32 correction solves)
   size_t off_at, off_bt;  // anti-transposed A, B (FP64) when transposed
-  size_t off_a32, off_b32, off_al, off_bl, off_rf, off_r, off_x, off_slots, off_rs;  // FP32 + refinement
+  size_t off_a32, off_b32, off_al, off_bl, off_rf, off_r, off_x, off_d, off_slots, off_rs;  // FP32 + refinement
   size_t total;
 };
 
@@ -373,6 +377,8 @@ SolvePlan plan_solve(int64_t m, int64_t n, const Opts& o) {
     P.off_r = off;
     off = align_up(off + sizeof(double) * m * n);
     P.off_x = off;
+    off = align_up(off + sizeof(double) * m * n);
+    P.off_d = off;
     off = align_up(off + sizeof(double) * m * n);
     P.off_slots = off;  // amax, bmax, then rmax/dmax/xmax per iteration
     off = align_up(off + sizeof(unsigned long long) * (2 + 3 * (o.maxit + 1)));
@@ -444,6 +450,7 @@ int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, c
   float* Rf = reinterpret_cast<float*>(ws + P.off_rf);
   double* R = reinterpret_cast<double*>(ws + P.off_r);
   double* X = reinterpret_cast<double*>(ws + P.off_x);
+  double* Dlast = reinterpret_cast<double*>(ws + P.off_d);
   unsigned long long* slots = reinterpret_cast<unsigned long long*>(ws + P.off_slots);
   unsigned long long* amax = slots + 0;
   unsigned long long* bmax = slots + 1;
@@ -471,10 +478,16 @@ int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, c
     unsigned long long* xmax = rmax + 2;
     if (it == 0) {
       k_copy_max<<<grid_for(m * n), 256, 0, s>>>(C, ldc, R, m, m, n, rmax);
-    } else {
+    } else if (it == 1) {
+      // First residual of the solution: binary64-accurate (double-float products).
       const unsigned long long* xprev = slots + 2 + 3 * (it - 1) + 2;
       k_residual_df<<<dim3((m + GT - 1) / GT, (n + GT - 1) / GT), 256, 0, s>>>(
           Ah, Al, m, Bh, Bl, n, C, ldc, X, m, R, m, m, n, amax, bmax, xprev, rmax, &rs->conv);
+    } else {
+      // Later ones by the recurrence R_k = R_{k-1} - (A D + D B): D is small, binary32 suffices.
+      const unsigned long long* dprev = slots + 2 + 3 * (it - 1) + 1;
+      k_residual_update<<<dim3((m + GT - 1) / GT, (n + GT - 1) / GT), 256, 0, s>>>(
+          Ah, m, Bh, n, Dlast, m, R, m, m, n, amax, bmax, dprev, rmax, &rs->conv);
     }
     k_to_float<<<grid_for(m * n), 256, 0, s>>>(R, m, Rf, m, m, n, rmax, nullptr, 0, &rs->conv);
     if (it > 0) {
@@ -483,8 +496,8 @@ int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, c
     }
     e = launch_dag_f32(P.shape.t, w, std::min(L.max_tiles, L.ncta), s);
     if (e != cudaSuccess) return SYLV_ERR_CUDA;
-    k_accumulate<<<grid_for(static_cast<int64_t>(L.max_tiles) * 256), 256, 0, s>>>(w, X, m, rmax, amax, bmax, dmax,
-                                                                                   xmax, &rs->conv);
+    k_accumulate<<<grid_for(static_cast<int64_t>(L.max_tiles) * 256), 256, 0, s>>>(w, X, m, Dlast, rmax, amax, bmax,
+                                                                                   dmax, xmax, &rs->conv);
     k_refine_check<<<1, 1, 0, s>>>(rs, dmax, xmax, it > 0 ? dmax - 3 : nullptr, o.tol, w);
   }
   k_copy<<<grid_for(m * n), 256, 0, s>>>(X, m, C, ldc, m, n);
@@ -671,11 +684,14 @@ struct sylv_batch_plan {
   int count = 0;
   int tt = 32;
   int precision = SYLV_FP64;
+  int transa = 0, transb = 0;
   char* ws = nullptr;
   Layout L{};
   Work w{};
   int64_t maxN = 0;
   int pmax_all = 0;
+  TransDesc* dta = nullptr;  // device descriptors of the anti-transposed copies (transa)
+  TransDesc* dtb = nullptr;  // (transb)
 };
 
 int sylv_batch_create(sylv_batch_plan** plan, int32_t count, const int64_t* m, const int64_t* n,
@@ -688,7 +704,7 @@ int sylv_batch_create(sylv_batch_plan** plan, int32_t count, const int64_t* m, c
   Opts o{};
   int rc = read_opts(opts, &o);
   if (rc) return rc;
-  if (o.precision == SYLV_FP32_REFINE || o.transa || o.transb) return SYLV_ERR_UNSUPPORTED;
+  if (o.precision == SYLV_FP32_REFINE) return SYLV_ERR_UNSUPPORTED;
   std::vector<Shape> sh;
   std::vector<const void*> Av, Bv;
   std::vector<void*> Cv;
@@ -716,20 +732,60 @@ int sylv_batch_create(sylv_batch_plan** plan, int32_t count, const int64_t* m, c
   P->count = count;
   P->tt = tt;
   P->precision = o.precision;
+  P->transa = o.transa;
+  P->transb = o.transb;
   P->L = make_layout(sh, 0);
   P->maxN = maxN;
   P->pmax_all = pmax_all;
   if (count > 0) {
+    // Transposed problems: each equation gets anti-transposed copies of A and/or B
+    // (J A^T J, J B^T J) after the tile workspace, refreshed by every execute.
+    size_t off = P->L.total;
+    std::vector<size_t> oa(count, 0), ob(count, 0);
+    if (o.transa)
+      for (int i = 0; i < count; ++i) {
+        oa[i] = off;
+        off = align_up(off + sizeof(double) * sh[i].m * sh[i].m);
+      }
+    if (o.transb)
+      for (int i = 0; i < count; ++i) {
+        ob[i] = off;
+        off = align_up(off + sizeof(double) * sh[i].n * sh[i].n);
+      }
+    const size_t off_da = off;
+    off = align_up(off + sizeof(TransDesc) * count);
+    const size_t off_db = off;
+    off = align_up(off + sizeof(TransDesc) * count);
     void* p = nullptr;
-    if (cudaMalloc(&p, P->L.total) != cudaSuccess) {
+    if (cudaMalloc(&p, off) != cudaSuccess) {
       cudaGetLastError();
       delete P;
       return SYLV_ERR_CUDA;
     }
     P->ws = static_cast<char*>(p);
     P->w = make_work(P->ws, P->L, count, o.timeout_ns);
+    std::vector<TransDesc> ta(count), tb(count);
+    for (int i = 0; i < count; ++i) {
+      if (o.transa) {
+        ta[i] = TransDesc{static_cast<const double*>(Av[i]), la[i], reinterpret_cast<double*>(P->ws + oa[i]), sh[i].m};
+        Av[i] = ta[i].dst;
+        la[i] = std::max<int64_t>(sh[i].m, 1);
+      }
+      if (o.transb) {
+        tb[i] = TransDesc{static_cast<const double*>(Bv[i]), lb[i], reinterpret_cast<double*>(P->ws + ob[i]), sh[i].n};
+        Bv[i] = tb[i].dst;
+        lb[i] = std::max<int64_t>(sh[i].n, 1);
+      }
+    }
+    P->dta = reinterpret_cast<TransDesc*>(P->ws + off_da);
+    P->dtb = reinterpret_cast<TransDesc*>(P->ws + off_db);
     std::vector<Inst> I = make_insts(sh, P->L, Av, la, Bv, lb, Cv, lc, o.precision == SYLV_FP64 ? 1 : 0, o.omega);
-    if (cudaMemcpy(P->w.inst, I.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice) != cudaSuccess) {
+    bool ok = cudaMemcpy(P->w.inst, I.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok && o.transa)
+      ok = cudaMemcpy(P->dta, ta.data(), sizeof(TransDesc) * count, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok && o.transb)
+      ok = cudaMemcpy(P->dtb, tb.data(), sizeof(TransDesc) * count, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
       cudaFree(P->ws);
       delete P;
       return SYLV_ERR_CUDA;
@@ -744,6 +800,16 @@ int sylv_batch_execute(sylv_batch_plan* P, void* stream) {
   if (P->count == 0) return SYLV_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Layout& L = P->L;
+  const int nt32 = static_cast<int>((P->maxN + 31) / 32);
+  const int flip_grid = std::max(1, std::min<int>(static_cast<int>((P->maxN * P->maxN / 2 + 255) / 256), 64));
+  if (P->transa) {
+    k_anti_transpose_batched<<<dim3(nt32, nt32, P->count), 256, 0, s>>>(P->dta);
+    k_flip_batched<<<dim3(flip_grid, P->count), 256, 0, s>>>(P->w.inst, 0);
+  }
+  if (P->transb) {
+    k_anti_transpose_batched<<<dim3(nt32, nt32, P->count), 256, 0, s>>>(P->dtb);
+    k_flip_batched<<<dim3(flip_grid, P->count), 256, 0, s>>>(P->w.inst, 1);
+  }
   if (cudaMemsetAsync(P->ws + L.zero_lo, 0, L.zero_hi - L.zero_lo, s) != cudaSuccess) return SYLV_ERR_CUDA;
   cudaError_t e = run_prep<double>(P->w, L, P->count, P->maxN, P->pmax_all, s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
@@ -751,6 +817,8 @@ int sylv_batch_execute(sylv_batch_plan* P, void* stream) {
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
   k_consistency<double><<<grid_for(L.sum_tiles * 256), 256, 0, s>>>(P->w);
   k_results<<<(P->count + 255) / 256, 256, 0, s>>>(P->w);
+  if (P->transa) k_flip_batched<<<dim3(flip_grid, P->count), 256, 0, s>>>(P->w.inst, 0);
+  if (P->transb) k_flip_batched<<<dim3(flip_grid, P->count), 256, 0, s>>>(P->w.inst, 1);
   return cuda_status(cudaGetLastError());
 }
 
@@ -864,6 +932,112 @@ int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- batched adjoint
+int sylv_tri_solve_backward_batched(int32_t count, const int64_t* m, const int64_t* n, const double* const* A,
+                                    const int64_t* lda, const double* const* B, const int64_t* ldb,
+                                    const double* const* Y, const int64_t* ldy, const int64_t* log2scale,
+                                    double* const* G, const int64_t* ldg, double* const* dA, const int64_t* ldda,
+                                    double* const* dB, const int64_t* lddb, const sylv_opts* opts,
+                                    sylv_result* results) {
+  if (count < 0) return -1;
+  if (count == 0) return SYLV_OK;
+  if (!m || !n || !A || !lda || !B || !ldb || !Y || !ldy || !log2scale || !G || !ldg || !results) return -2;
+  Opts o{};
+  int rc = read_opts(opts, &o);
+  if (rc) return rc;
+  for (int i = 0; i < count; ++i) {
+    if (Y[i] == nullptr && m[i] > 0 && n[i] > 0) return -8;
+    if (ldy[i] < std::max<int64_t>(m[i], 1)) return -9;
+    if (dA && dA[i] && ldda[i] < std::max<int64_t>(m[i], 1)) return -14;
+    if (dB && dB[i] && lddb[i] < std::max<int64_t>(n[i], 1)) return -16;
+  }
+  sylv_opts oa;
+  if (opts)
+    oa = *opts;
+  else
+    sylv_default_opts(&oa);
+  oa.transa ^= 1;
+  oa.transb ^= 1;
+  oa.precision = SYLV_FP64;
+  sylv_batch_plan* P = nullptr;
+  rc = sylv_batch_create(&P, count, m, n, A, lda, B, ldb, G, ldg, &oa);
+  if (rc) return rc;
+  cudaStream_t s = o.stream;
+  rc = sylv_batch_execute(P, s);
+  if (rc) {
+    sylv_batch_destroy(P);
+    return rc;
+  }
+  // Gradient products from alpha_G Gamma (now in G), then dL/dC = alpha Gamma.
+  std::vector<GradDesc> gd;
+  std::vector<ScaleDesc> sd;
+  int64_t maxN = 1;
+  for (int i = 0; i < count; ++i) {
+    if (m[i] == 0 || n[i] == 0) continue;
+    maxN = std::max(maxN, std::max(m[i], n[i]));
+    if (dA && dA[i]) {
+      GradDesc g{};
+      g.P = o.transa ? Y[i] : G[i];
+      g.Q = o.transa ? G[i] : Y[i];
+      g.psi = 1;
+      g.psc = o.transa ? ldy[i] : ldg[i];
+      g.qsj = 1;
+      g.qsc = o.transa ? ldg[i] : ldy[i];
+      g.N = m[i];
+      g.K = n[i];
+      g.T = A[i];
+      g.ldt = lda[i];
+      g.D = dA[i];
+      g.ldd = ldda[i];
+      gd.push_back(g);
+    }
+    if (dB && dB[i]) {
+      GradDesc g{};
+      g.P = o.transb ? G[i] : Y[i];
+      g.Q = o.transb ? Y[i] : G[i];
+      g.psi = o.transb ? ldg[i] : ldy[i];
+      g.psc = 1;
+      g.qsj = o.transb ? ldy[i] : ldg[i];
+      g.qsc = 1;
+      g.N = n[i];
+      g.K = m[i];
+      g.T = B[i];
+      g.ldt = ldb[i];
+      g.D = dB[i];
+      g.ldd = lddb[i];
+      gd.push_back(g);
+    }
+    sd.push_back(ScaleDesc{G[i], ldg[i], m[i], n[i], static_cast<int>(log2scale[i]), 0});
+  }
+  void* buf = nullptr;
+  const size_t bytes = align_up(sizeof(GradDesc) * std::max<size_t>(gd.size(), 1)) + sizeof(ScaleDesc) * std::max<size_t>(sd.size(), 1);
+  if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    sylv_batch_destroy(P);
+    return SYLV_ERR_CUDA;
+  }
+  GradDesc* dgd = static_cast<GradDesc*>(buf);
+  ScaleDesc* dsd = reinterpret_cast<ScaleDesc*>(static_cast<char*>(buf) + align_up(sizeof(GradDesc) * std::max<size_t>(gd.size(), 1)));
+  bool ok = true;
+  if (!gd.empty())
+    ok = cudaMemcpyAsync(dgd, gd.data(), sizeof(GradDesc) * gd.size(), cudaMemcpyHostToDevice, s) == cudaSuccess;
+  if (ok && !sd.empty())
+    ok = cudaMemcpyAsync(dsd, sd.data(), sizeof(ScaleDesc) * sd.size(), cudaMemcpyHostToDevice, s) == cudaSuccess;
+  const int nt64 = static_cast<int>((maxN + GT - 1) / GT);
+  if (ok && !gd.empty()) k_grad_product_batched<<<dim3(nt64, nt64, static_cast<unsigned>(gd.size())), 256, 0, s>>>(dgd);
+  if (ok && !sd.empty()) k_scale_pow2_batched<<<dim3(64, static_cast<unsigned>(sd.size())), 256, 0, s>>>(dsd);
+  if (ok) ok = cudaGetLastError() == cudaSuccess;
+  if (ok) ok = cudaStreamSynchronize(s) == cudaSuccess;
+  cudaFree(buf);
+  if (!ok) {
+    sylv_batch_destroy(P);
+    return SYLV_ERR_CUDA;
+  }
+  rc = sylv_batch_results(P, results);
+  sylv_batch_destroy(P);
+  return rc;
+}
 
 // ---------------------------------------------------------------- allocation-free entry point
 // Some callers cannot allocate device memory at solve time: code running inside a

@@ -27,6 +27,8 @@
 // scales it by delta^2; with the A/B tile at scale 1 the product needs delta once.
 #pragma once
 
+#include <type_traits>
+
 #include "sylv_internal.cuh"
 
 namespace sylv {
@@ -35,8 +37,11 @@ template <int TT, typename T>
 struct DagSmem {
   static constexpr int LDG = TT + 2;  // row stride of the GEMM operands (16-byte aligned rows)
   static constexpr int LDY = TT + 1;  // leading dimension of the Y, A_kk, B_ll tiles
-  T L[TT * LDG];                      // left GEMM operand, k-major; A_kk in the diagonal phases
-  T R[TT * LDG];                      // right GEMM operand, k-major; B_ll in the diagonal phases
+  static constexpr int G = TT <= 32 ? 3 : 1;  // producers staged together in one GEMM pass
+  T L[G * TT * LDG];                  // left GEMM operands, k-major; A_kk in the diagonal phases
+  T R[G * TT * LDG];                  // right GEMM operands, k-major; B_ll in the diagonal phases
+  int gside[G], gprod[G], gk[G], goff[G];  // the current group of producers
+  int gn, gktot, gfast;
   T Y[TT * LDY];                      // the tile being solved (column-major)
   double zbuf[TT][4];                 // this step's solved 1x1/2x2 blocks, by block column
   static constexpr bool kFactSmem = (TT <= 32);  // small-system factors kept in shared memory
@@ -165,8 +170,8 @@ __device__ inline int pair_factor(int ma, int nb, const double* a, const double*
 // Right-hand side of a factored pair of size S (1, 2 or 4): r (vec order) in, Z out.
 // Returns log2(beta).  Compile-time S keeps r in registers (interchanges by selects).
 template <int S>
-__device__ __forceinline__ int pair_solve(const double* f, int pack, double (&r)[4], double omega, int eo,
-                                          bool robust) {
+__device__ __noinline__ int pair_solve_guarded(const double* f, int pack, double (&r)[4], double omega, int eo,
+                                               bool robust) {
   int lb = 0;
 #pragma unroll
   for (int st = 0; st < S; ++st) {
@@ -231,6 +236,67 @@ __device__ __forceinline__ int pair_solve(const double* f, int pack, double (&r)
 #pragma unroll
   for (int u = 0; u < 4; ++u) r[u] = x[u];
   return lb;
+}
+
+// The common case of pair_solve_guarded: the same eliminations without guards,
+// tracking in integers the exponent bound every guard would test (the fast test of
+// guard_update / guard_division).  If no bound reaches omega, every guard would have
+// returned 1 and the result is bitwise that of the guarded solve; otherwise the
+// guarded solve reruns from the saved right-hand side (rare, kept out of line).
+template <int S>
+__device__ __forceinline__ int pair_solve(const double* f, int pack, double (&r)[4], double omega, int eo,
+                                          bool robust) {
+  double r_in[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) r_in[u] = r[u];
+  int mx = -4096;
+#pragma unroll
+  for (int st = 0; st < S; ++st) {
+    const int pr = (pack >> (2 * st)) & 3;
+#pragma unroll
+    for (int k = st + 1; k < S; ++k)
+      if (pr == k) {
+        const double tmp = r[st];
+        r[st] = r[k];
+        r[k] = tmp;
+      }
+  }
+#pragma unroll
+  for (int st = 0; st < S; ++st)
+#pragma unroll
+    for (int u = st + 1; u < S; ++u) {
+      const double l = f[u * S + st];
+      mx = max(mx, max(ub_log2(r[u]), ub_log2(l) + ub_log2(r[st])) + 1);
+      r[u] = fma(-l, r[st], r[u]);
+    }
+#pragma unroll
+  for (int i = S - 1; i >= 0; --i) {
+#pragma unroll
+    for (int v = i + 1; v < S; ++v) {
+      const double uiv = f[i * S + v];
+      mx = max(mx, max(ub_log2(r[i]), ub_log2(uiv) + ub_log2(r[v])) + 1);
+      r[i] = fma(-uiv, r[v], r[i]);
+    }
+    const double rcp = f[S * S + i];
+    mx = max(mx, ub_log2(r[i]) + ub_log2(rcp));
+    r[i] = r[i] * rcp;
+  }
+  if (robust && mx > eo) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) r[u] = r_in[u];
+    return pair_solve_guarded<S>(f, pack, r, omega, eo, robust);
+  }
+  double x[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int u = 0; u < S; ++u) {
+    const int cu = (pack >> (8 + 2 * u)) & 3;
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+      if (cu == t) x[t] = r[u];
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) r[u] = x[u];
+  return 0;
 }
 
 // Block structure of an upper quasi-triangular tile (Sec. 1, eq. (4)): a nonzero
@@ -438,8 +504,11 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
   for (int s = 0; s < nsteps; ++s) {
     const int lb_lo = max(0, s - (pb - 1));
     const int lb_hi = min(s, qb - 1);
-    // Phase A: this step's blocks, one thread each; publish their geometry.
-    for (int lb = lb_lo + tid; lb <= lb_hi; lb += kThreads) {
+    // Phase A: this step's blocks, one thread each (block i of the step on warp
+    // i % 8, so the warps share the work); publish their geometry.
+    const int npairs = lb_hi - lb_lo + 1;
+    const int my_pair = (tid & 31) * (kThreads / 32) + (tid >> 5);
+    for (int lb = lb_lo + my_pair; lb <= lb_hi && my_pair < npairs; lb += kThreads) {
       const int kb = pb - 1 - (s - lb);
       const int r0 = sh.astart[kb], ma = sh.astart[kb + 1] - r0;
       const int c0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - c0;
@@ -536,38 +605,43 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
       zb0 = sh.zbuf[lbs][rr_in];
       zb1 = (nbs == 2) ? sh.zbuf[lbs][rr_in + ma_r] : 0.0;
     }
+    // Element arithmetic in T: binary64 for the FP64 solve, binary32 for the FP32
+    // correction solves (only the small systems and the bounds stay binary64).
     unsigned long long wm = 0;
+    T yv[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) yv[j] = okj[j] ? Ys[my_r + (my_c0 + j * CSTEP) * LDY] : T(0);
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-      if (!okj[j]) continue;
       const int c = my_c0 + j * CSTEP;
       const int lbc = lbcj[j];
       const int dd = dr + lbc;
-      T* yp = &Ys[my_r + c * LDY];
+      T y = yv[j];
       if (dd < s) {
-        if (g != 0) *yp = mul2(*yp, g);
-      } else if (dd == s) {
-        *yp = static_cast<T>(sh.zbuf[lbc][rr_in + ma_r * offj[j]]);
-      } else {
-        double y = static_cast<double>(*yp);
         if (g != 0) y = mul2(y, g);
-        double tb = 0.0;
+      } else if (dd == s) {
+        y = static_cast<T>(sh.zbuf[lbc][rr_in + ma_r * offj[j]]);
+      } else {
+        if (g != 0) y = mul2(y, g);
+        T tb = T(0);
         if (bs_ok && lbs < lbc) {  // block (kb_r, lbs) left of this column, solved now
-          tb = zb0 * static_cast<double>(Bk[cs0 + c * LDY]);
-          if (nbs == 2) tb = fma(zb1, static_cast<double>(Bk[cs0 + 1 + c * LDY]), tb);
+          tb = static_cast<T>(zb0) * Bk[cs0 + c * LDY];
+          if (nbs == 2) tb = fma(static_cast<T>(zb1), Bk[cs0 + 1 + c * LDY], tb);
         }
         if (s >= lbc && s - lbc < dr) {  // block below this row in column block lbc, solved now
           const int rs0 = sh.pr0[lbc], mas = sh.pma[lbc];
-          y = fma(-static_cast<double>(Ak[my_r + rs0 * LDY]), sh.zbuf[lbc][mas * offj[j]], y);
-          if (mas == 2) y = fma(-static_cast<double>(Ak[my_r + (rs0 + 1) * LDY]), sh.zbuf[lbc][1 + 2 * offj[j]], y);
+          y = fma(-Ak[my_r + rs0 * LDY], static_cast<T>(sh.zbuf[lbc][mas * offj[j]]), y);
+          if (mas == 2) y = fma(-Ak[my_r + (rs0 + 1) * LDY], static_cast<T>(sh.zbuf[lbc][1 + 2 * offj[j]]), y);
         }
         y -= tb;
-        const T yt = static_cast<T>(y);
-        *yp = yt;
-        const unsigned long long bb = abs_bits(static_cast<double>(yt));
-        wm = bb > wm ? bb : wm;
+        const unsigned long long bb = abs_bits(static_cast<double>(y));
+        wm = (okj[j] && bb > wm) ? bb : wm;
       }
+      yv[j] = y;
     }
+#pragma unroll
+    for (int j = 0; j < NC; ++j)
+      if (okj[j]) Ys[my_r + (my_c0 + j * CSTEP) * LDY] = yv[j];
     if (ROBUST) {
       wm = warp_max_u64(wm);
       if (lane == 0) sh.wmax[warp] = wm;
@@ -580,14 +654,15 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
 
 // ----------------------------------------------------------------------------
 // GEMM operand staging: L (rows x kdim) from column-major P (coalesced along rows),
-// R (kdim x cols) from column-major P (coalesced along k); both stored k-major.
+// R (kdim x cols) from column-major P (coalesced along k); both stored k-major at
+// the given k offset.  Only rows kk < kdim are written (groups stage back to back).
 template <int TT, typename T, bool FROM_Y>
 __device__ __forceinline__ void stage_left(T* L, const T* P, int64_t ld, int rows, int kdim) {
   constexpr int LDG = DagSmem<TT, T>::LDG;
-  for (int idx = threadIdx.x; idx < TT * TT; idx += kThreads) {
+  for (int idx = threadIdx.x; idx < TT * kdim; idx += kThreads) {
     const int r = idx % TT, kk = idx / TT;
     T v = T(0);
-    if (r < rows && kk < kdim) {
+    if (r < rows) {
       const T* src = P + r + kk * ld;
       v = FROM_Y ? __ldcg(src) : __ldg(src);
     }
@@ -597,10 +672,10 @@ __device__ __forceinline__ void stage_left(T* L, const T* P, int64_t ld, int row
 template <int TT, typename T, bool FROM_Y>
 __device__ __forceinline__ void stage_right(T* R, const T* P, int64_t ld, int kdim, int cols) {
   constexpr int LDG = DagSmem<TT, T>::LDG;
-  for (int idx = threadIdx.x; idx < TT * TT; idx += kThreads) {
-    const int kk = idx % TT, c = idx / TT;
+  for (int idx = threadIdx.x; idx < TT * kdim; idx += kThreads) {
+    const int kk = idx % kdim, c = idx / kdim;
     T v = T(0);
-    if (kk < kdim && c < cols) {
+    if (c < cols) {
       const T* src = P + kk + c * ld;
       v = FROM_Y ? __ldcg(src) : __ldg(src);
     }
@@ -673,8 +748,17 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
     int* factp = w.factp + static_cast<int64_t>(blockIdx.x) * TT * TT;
     diag_prepare<TT, T, ROBUST>(sh, A, I.lda, B, I.ldb, r0, c0, mt, nt, st->smin, fact, factp);
 
-    // ---- accumulator <- C_kl, exact infinity norm
+    // ---- accumulator <- C_kl, exact infinity norm.  In binary32 the accumulator
+    // is compensated: every group's product is summed into a fresh partial and the
+    // partials enter (acc, acc_lo) by two-sum, so a tile that receives thousands of
+    // products keeps ~binary32 accuracy instead of losing sqrt(K) ulps.
+    constexpr bool kComp = std::is_same<T, float>::value;
     T acc[MR][NR];
+    T acc_lo[MR][NR];
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) acc_lo[i][j] = T(0);
 #pragma unroll
     for (int i = 0; i < MR; ++i)
 #pragma unroll
@@ -716,72 +800,169 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
       sh.e_acc = 0;
     }
 
-    // ---- incoming updates, producers in anti-diagonal order
+    // ---- incoming updates, producers in anti-diagonal order.  Producer q of the
+    // tile (0 <= q < d): while only one side has producers left to start, that side;
+    // afterwards A side then B side per anti-diagonal.  Up to G producers whose
+    // flags are already set are staged back to back and applied in one GEMM pass;
+    // each element still receives their products in producer order (identical
+    // arithmetic to one at a time) as long as no scaling is needed -- when a group
+    // member's exponent differs from the accumulator's or the bounds come near
+    // omega, the group shrinks to one producer with the exact ProtectUpdate.
     const int d = (p - 1 - k) + l;
-    const int s_lo = min(l, p - 1 - k);
-    for (int s = s_lo; s < d && !sh.abort; ++s) {
-      for (int side = 0; side < 2; ++side) {
-        int prod;  // producer tile index
-        int kdim;
-        if (side == 0) {
-          if (s < l) continue;
-          const int i = p - 1 + l - s;  // A side: Y_kl -= A_ki Y_il
-          prod = i * I.qmax + l;
-          kdim = rb[i + 1] - rb[i];
+    const int a0 = l, b0 = p - 1 - k;
+    const int lo = min(a0, b0), hi = max(a0, b0);
+    const int eo = floor_log2(omega);
+    auto producer = [&](int q, int& side, int& prod, int& kdim) {
+      int sd;
+      int sq;
+      if (q < hi - lo) {
+        sd = (a0 < b0) ? 0 : 1;
+        sq = lo + q;
+      } else {
+        const int r = q - (hi - lo);
+        sq = hi + r / 2;
+        sd = r & 1;
+      }
+      side = sd;
+      if (sd == 0) {
+        const int i = p - 1 + l - sq;  // A side: Y_kl -= A_ki Y_il
+        prod = i * I.qmax + l;
+        kdim = rb[i + 1] - rb[i];
+      } else {
+        const int j = sq - (p - 1 - k);  // B side: Y_kl -= Y_kj B_jl
+        prod = k * I.qmax + j;
+        kdim = cb[j + 1] - cb[j];
+      }
+    };
+    auto opnorm = [&](int side, int prod) {
+      return (side == 0) ? an[(int64_t)k * I.pmax + prod / I.qmax] : bn[(int64_t)(prod % I.qmax) * I.qmax + l];
+    };
+    for (int q = 0; q < d && !sh.abort;) {
+      if (tid == 0) {
+        int side, prod, kdim;
+        producer(q, side, prod, kdim);
+        if (!wait_flag(&tflag[prod], ctrl, w.timeout_ns)) {
+          sh.abort = 1;
         } else {
-          if (s < p - 1 - k) continue;
-          const int j = s - (p - 1 - k);  // B side: Y_kl -= Y_kj B_jl
-          prod = k * I.qmax + j;
-          kdim = cb[j + 1] - cb[j];
+          int g = 1, ktot = kdim;
+          sh.gside[0] = side;
+          sh.gprod[0] = prod;
+          sh.gk[0] = kdim;
+          sh.goff[0] = 0;
+          while (g < DagSmem<TT, T>::G && q + g < d) {
+            producer(q + g, side, prod, kdim);
+            if (!ld_acquire(&tflag[prod])) break;
+            sh.gside[g] = side;
+            sh.gprod[g] = prod;
+            sh.gk[g] = kdim;
+            sh.goff[g] = ktot;
+            ktot += kdim;
+            ++g;
+          }
+          int fast = 1;
+          if (ROBUST) {
+            int emx = ub_log2(sh.nb_acc);
+            for (int u = 0; u < g; ++u) {
+              if (texp[sh.gprod[u]] != sh.e_acc) fast = 0;
+              emx = max(emx, ub_log2(opnorm(sh.gside[u], sh.gprod[u])) + ub_log2(tnorm[sh.gprod[u]]));
+            }
+            if (!(fast && emx + 2 <= eo)) {
+              fast = 0;
+              g = 1;
+              ktot = sh.gk[0];
+            } else {
+              double nb = sh.nb_acc;
+              for (int u = 0; u < g; ++u) nb += opnorm(sh.gside[u], sh.gprod[u]) * tnorm[sh.gprod[u]];
+              sh.nb_acc = nb;
+            }
+          }
+          sh.gn = g;
+          sh.gktot = ktot;
+          sh.gfast = fast;
+          sh.sacc = 0;
+          sh.sop = 0;
         }
-        if (tid == 0) {
-          if (!wait_flag(&tflag[prod], ctrl, w.timeout_ns)) sh.abort = 1;
-        }
-        __syncthreads();
-        if (sh.abort) break;
+      }
+      __syncthreads();
+      if (sh.abort) break;
+      const int g = sh.gn;
+      for (int u = 0; u < g; ++u) {
+        const int side = sh.gside[u], prod = sh.gprod[u], kdim = sh.gk[u];
+        T* Lu = sh.L + sh.goff[u] * DagSmem<TT, T>::LDG;
+        T* Ru = sh.R + sh.goff[u] * DagSmem<TT, T>::LDG;
         if (side == 0) {
           const int i = prod / I.qmax;
-          stage_left<TT, T, false>(sh.L, A + r0 + (int64_t)rb[i] * I.lda, I.lda, mt, kdim);
-          stage_right<TT, T, true>(sh.R, C + rb[i] + (int64_t)c0 * I.ldc, I.ldc, kdim, nt);
+          stage_left<TT, T, false>(Lu, A + r0 + (int64_t)rb[i] * I.lda, I.lda, mt, kdim);
+          stage_right<TT, T, true>(Ru, C + rb[i] + (int64_t)c0 * I.ldc, I.ldc, kdim, nt);
         } else {
           const int j = prod % I.qmax;
-          stage_left<TT, T, true>(sh.L, C + r0 + (int64_t)cb[j] * I.ldc, I.ldc, mt, kdim);
-          stage_right<TT, T, false>(sh.R, B + cb[j] + (int64_t)c0 * I.ldb, I.ldb, kdim, nt);
+          stage_left<TT, T, true>(Lu, C + r0 + (int64_t)cb[j] * I.ldc, I.ldc, mt, kdim);
+          stage_right<TT, T, false>(Ru, B + cb[j] + (int64_t)c0 * I.ldb, I.ldb, kdim, nt);
         }
-        if (ROBUST && tid == 0) {
-          const int ep = texp[prod];
-          const double yp = tnorm[prod];
-          const double on = (side == 0) ? an[(int64_t)k * I.pmax + prod / I.qmax]
-                                        : bn[(int64_t)(prod % I.qmax) * I.qmax + l];
-          const int eta = min(sh.e_acc, ep);
-          const double c = mul2(sh.nb_acc, eta - sh.e_acc);
-          const double x = mul2(yp, eta - ep);
-          const int z = (side == 0) ? protect_update(c, on, x, omega) : protect_update(c, x, on, omega);
-          const int delta = eta + z;
-          sh.sacc = delta - sh.e_acc;
-          sh.sop = delta - ep;
-          sh.nb_acc = mul2(sh.nb_acc, sh.sacc) + on * mul2(yp, sh.sop);
-          sh.e_acc = delta;
-          if (sh.sacc != 0 || sh.sop != 0) ++sh.nscale;
-        }
-        __syncthreads();
-        if (ROBUST) {
-          const int sop = sh.sop, sacc = sh.sacc;
-          if (sop != 0) {  // scale the Y operand (R on the A side, L on the B side)
-            T* Yop = (side == 0) ? sh.R : sh.L;
-            for (int idx = tid; idx < TT * DagSmem<TT, T>::LDG; idx += kThreads) Yop[idx] = mul2(Yop[idx], sop);
-            __syncthreads();
-          }
-          if (sacc != 0) {
-#pragma unroll
-            for (int i = 0; i < MR; ++i)
-#pragma unroll
-              for (int j = 0; j < NR; ++j) acc[i][j] = mul2(acc[i][j], sacc);
-          }
-        }
-        gemm_sub<TT, T, MR, NR>(acc, sh.L, sh.R, kdim, rbase, cbase);
-        __syncthreads();
       }
+      if (w.prio && tid == 0) {
+        // A diagonal solve on this SM is on the critical path: let it have the FP64
+        // pipe (bounded: at most ~200 us per group).
+        const int32_t* busy = w.smbusy + sm_id();
+        for (int it = 0; it < 400 && ld_volatile(busy) > 0; ++it) __nanosleep(500);
+      }
+      if (ROBUST && tid == 0 && !sh.gfast) {
+        const int side = sh.gside[0], prod = sh.gprod[0];
+        const int ep = texp[prod];
+        const double yp = tnorm[prod];
+        const double on = opnorm(side, prod);
+        const int eta = min(sh.e_acc, ep);
+        const double c = mul2(sh.nb_acc, eta - sh.e_acc);
+        const double x = mul2(yp, eta - ep);
+        const int z = (side == 0) ? protect_update(c, on, x, omega) : protect_update(c, x, on, omega);
+        const int delta = eta + z;
+        sh.sacc = delta - sh.e_acc;
+        sh.sop = delta - ep;
+        sh.nb_acc = mul2(sh.nb_acc, sh.sacc) + on * mul2(yp, sh.sop);
+        sh.e_acc = delta;
+        if (sh.sacc != 0 || sh.sop != 0) ++sh.nscale;
+      }
+      __syncthreads();
+      if (ROBUST) {
+        const int sop = sh.sop, sacc = sh.sacc;
+        if (sop != 0) {  // single producer: scale its Y operand (R on the A side, L on the B side)
+          T* Yop = (sh.gside[0] == 0) ? sh.R : sh.L;
+          const int nel = sh.gk[0] * DagSmem<TT, T>::LDG;
+          for (int idx = tid; idx < nel; idx += kThreads) Yop[idx] = mul2(Yop[idx], sop);
+          __syncthreads();
+        }
+        if (sacc != 0) {
+#pragma unroll
+          for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+              acc[i][j] = mul2(acc[i][j], sacc);
+              acc_lo[i][j] = mul2(acc_lo[i][j], sacc);
+            }
+        }
+      }
+      if constexpr (kComp) {
+        T part[MR][NR];
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+          for (int j = 0; j < NR; ++j) part[i][j] = T(0);
+        gemm_sub<TT, T, MR, NR>(part, sh.L, sh.R, sh.gktot, rbase, cbase);
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+          for (int j = 0; j < NR; ++j) {  // two-sum: acc + part = t + e exactly
+            const T t = acc[i][j] + part[i][j];
+            const T bp = t - acc[i][j];
+            const T e = (acc[i][j] - (t - bp)) + (part[i][j] - bp);
+            acc[i][j] = t;
+            acc_lo[i][j] += e;
+          }
+      } else {
+        gemm_sub<TT, T, MR, NR>(acc, sh.L, sh.R, sh.gktot, rbase, cbase);
+      }
+      __syncthreads();
+      q += g;
     }
     if (sh.abort) break;
 
@@ -789,14 +970,16 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
 #pragma unroll
     for (int i = 0; i < MR; ++i)
 #pragma unroll
-      for (int j = 0; j < NR; ++j) sh.Y[(rbase + i) + (cbase + j) * LDY] = acc[i][j];
+      for (int j = 0; j < NR; ++j) sh.Y[(rbase + i) + (cbase + j) * LDY] = acc[i][j] + acc_lo[i][j];
     for (int idx = tid; idx < TT * TT; idx += kThreads) {
       const int r = idx % TT, c = idx / TT;
       sh.L[r + c * LDY] = (r < mt && c < mt && r <= c + 1) ? __ldg(&A[(r0 + r) + (int64_t)(r0 + c) * I.lda]) : T(0);
       sh.R[r + c * LDY] = (r < nt && c < nt && r <= c + 1) ? __ldg(&B[(c0 + r) + (int64_t)(c0 + c) * I.ldb]) : T(0);
     }
+    if (w.prio && tid == 0) atomicAdd(w.smbusy + sm_id(), 1);
     __syncthreads();
     diag_solve<TT, T, ROBUST>(sh, mt, nt, omega, fact, factp);
+    if (w.prio && tid == 0) atomicSub(w.smbusy + sm_id(), 1);
 
     // ---- exact norm of the final tile, write back, publish
     if (tid == 0) sh.umax = 0ull;

@@ -208,9 +208,10 @@ __global__ void k_copy_max(const double* __restrict__ C, int64_t ldc, double* __
 
 // X += D where the FP32 correction solve left tile (k,l) of D' = 2^(sa-sr) D as
 // 2^e_kl-scaled floats in Rf: D = Rf * 2^(sr - sa - e_kl).  Records max|D|, max|X|.
-__global__ void k_accumulate(Work wf, double* __restrict__ X, int64_t ldx, const unsigned long long* slot_r,
-                             const unsigned long long* slot_a, const unsigned long long* slot_b,
-                             unsigned long long* dmax, unsigned long long* xmax, const int* skip) {
+__global__ void k_accumulate(Work wf, double* __restrict__ X, int64_t ldx, double* __restrict__ Dout,
+                             const unsigned long long* slot_r, const unsigned long long* slot_a,
+                             const unsigned long long* slot_b, unsigned long long* dmax, unsigned long long* xmax,
+                             const int* skip) {
   if (skip && ld_volatile(skip)) return;
   const int sr = norm_exp(slot_r);
   const unsigned long long a = *slot_a, b = *slot_b;
@@ -231,6 +232,7 @@ __global__ void k_accumulate(Work wf, double* __restrict__ X, int64_t ldx, const
       const double dv = mul2(static_cast<double>(Rf[r + c * I.ldc]), sr - sa - e);
       const double xv = X[r + c * ldx] + dv;
       X[r + c * ldx] = xv;
+      if (Dout) Dout[r + c * ldx] = dv;
       md = fmax(md, fabs(dv));
       mxv = fmax(mxv, fabs(xv));
     }
@@ -484,6 +486,181 @@ __global__ void k_maxabs(const double* __restrict__ X, int64_t ldx, int64_t m, i
     mx = fmax(mx, fabs(X[(t % m) + (t / m) * ldx]));
   mx = warp_max(mx);
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, mx);
+}
+
+}  // namespace sylv
+
+namespace sylv {
+
+// Batched gradient products (equation e = blockIdx.z): the same product and mask
+// as k_grad_product, with per-equation operands.
+struct GradDesc {
+  const double* P;
+  int64_t psi, psc;
+  const double* Q;
+  int64_t qsj, qsc;
+  int64_t N, K;
+  const double* T;
+  int64_t ldt;
+  double* D;
+  int64_t ldd;
+};
+
+__global__ void __launch_bounds__(256) k_grad_product_batched(const GradDesc* __restrict__ gd) {
+  const GradDesc g = gd[blockIdx.z];
+  __shared__ __align__(16) double Ls[GK * GLD];
+  __shared__ __align__(16) double Rs[GK * GLD];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * GT, j0 = static_cast<int64_t>(blockIdx.y) * GT;
+  if (i0 >= g.N || j0 >= g.N) return;
+  const bool active = i0 <= j0 + GT;
+  double acc[4][4] = {};
+  if (active) {
+    for (int64_t k0 = 0; k0 < g.K; k0 += GK) {
+      for (int idx = tid; idx < GK * GT; idx += 256) {
+        const int r = idx % GT, kk = idx / GT;
+        const int64_t gi = i0 + r, gk = k0 + kk, gj = j0 + r;
+        Ls[kk * GLD + r] = (gi < g.N && gk < g.K) ? g.P[gi * g.psi + gk * g.psc] : 0.0;
+        Rs[kk * GLD + r] = (gj < g.N && gk < g.K) ? g.Q[gj * g.qsj + gk * g.qsc] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < GK; ++kk) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = Ls[kk * GLD + tx * 4 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Rs[kk * GLD + ty * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(-a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t r = i0 + tx * 4 + i, c = j0 + ty * 4 + j;
+      if (r < g.N && c < g.N) {
+        const bool keep = (r <= c) || (r == c + 1 && g.T[r + c * g.ldt] != 0.0);
+        g.D[r + c * g.ldd] = keep ? acc[i][j] : 0.0;
+      }
+    }
+}
+
+// Batched power-of-two scaling: M_e *= 2^e_e (equation e = blockIdx.y).
+struct ScaleDesc {
+  double* M;
+  int64_t ld, m, n;
+  int e;
+  int pad;
+};
+__global__ void k_scale_pow2_batched(const ScaleDesc* __restrict__ sd) {
+  const ScaleDesc s = sd[blockIdx.y];
+  if (s.e == 0) return;
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < s.m * s.n;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t % s.m, c = t / s.m;
+    s.M[r + c * s.ld] = mul2(s.M[r + c * s.ld], s.e);
+  }
+}
+
+}  // namespace sylv
+
+namespace sylv {
+
+// R <- R - (A D + D B) in binary32 arithmetic, for a correction D that is small
+// compared to the solution: the products' rounding (~2^-24 |A| |D|) is far below
+// the binary64-accurate residual the recurrence starts from.  A, B: the binary32
+// parts of the scaled pair (AS = A 2^-sa); D (binary64) scaled by 2^-sd into binary32
+// range; R_new = R - 2^(sa+sd) (AS DS + DS BS) with the final subtraction in
+// binary64.  Records max |R_new|.  64 x 64 outputs per CTA, 4 x 4 per thread.
+__global__ void __launch_bounds__(256) k_residual_update(const float* __restrict__ Ah, int64_t lda,
+                                                         const float* __restrict__ Bh, int64_t ldb,
+                                                         const double* __restrict__ D, int64_t ldd,
+                                                         double* __restrict__ R, int64_t ldr, int64_t m, int64_t n,
+                                                         const unsigned long long* slot_a,
+                                                         const unsigned long long* slot_b,
+                                                         const unsigned long long* slot_d, unsigned long long* rmax,
+                                                         const int* skip) {
+  if (skip && ld_volatile(skip)) return;
+  constexpr int LD = GT + 4;
+  __shared__ __align__(16) float Ls[GK * LD], Rs[GK * LD];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * GT, j0 = static_cast<int64_t>(blockIdx.y) * GT;
+  const unsigned long long ua = *slot_a, ub = *slot_b;
+  const int sa = norm_exp(ua > ub ? slot_a : slot_b);
+  const int sd = norm_exp(slot_d);
+  float acc[4][4] = {};
+  const int64_t ka = i0 > 0 ? i0 - 1 : 0;
+  for (int64_t k0 = ka; k0 < m; k0 += GK) {
+    for (int idx = tid; idx < GK * GT; idx += 256) {
+      const int r = idx % GT, kk = idx / GT;
+      const int64_t gr = i0 + r, gk = k0 + kk;
+      Ls[kk * LD + r] = (gr < m && gk < m && gr <= gk + 1) ? Ah[gr + gk * lda] : 0.f;
+      const int kk2 = idx % GK, c = idx / GK;
+      const int64_t gk2 = k0 + kk2, gc = j0 + c;
+      Rs[kk2 * LD + c] = (gk2 < m && gc < n) ? static_cast<float>(mul2(D[gk2 + gc * ldd], -sd)) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = Ls[kk * LD + tx * 4 + i];
+        b[i] = Rs[kk * LD + ty * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  const int64_t kb_end = (j0 + GT + 1 < n) ? j0 + GT + 1 : n;
+  for (int64_t k0 = 0; k0 < kb_end; k0 += GK) {
+    for (int idx = tid; idx < GK * GT; idx += 256) {
+      const int r = idx % GT, kk = idx / GT;
+      const int64_t gr = i0 + r, gk = k0 + kk;
+      Ls[kk * LD + r] = (gr < m && gk < n) ? static_cast<float>(mul2(D[gr + gk * ldd], -sd)) : 0.f;
+      const int kk2 = idx % GK, c = idx / GK;
+      const int64_t gk2 = k0 + kk2, gc = j0 + c;
+      Rs[kk2 * LD + c] = (gk2 < n && gc < n && gk2 <= gc + 1) ? Bh[gk2 + gc * ldb] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = Ls[kk * LD + tx * 4 + i];
+        b[i] = Rs[kk * LD + ty * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double mx = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t r = i0 + tx * 4 + i, c = j0 + ty * 4 + j;
+      if (r < m && c < n) {
+        const double v = R[r + c * ldr] - mul2(static_cast<double>(acc[i][j]), sa + sd);
+        R[r + c * ldr] = v;
+        mx = fmax(mx, fabs(v));
+      }
+    }
+  mx = warp_max(mx);
+  if ((tid & 31) == 0 && rmax) atomic_max_nonneg(rmax, mx);
 }
 
 }  // namespace sylv

@@ -79,6 +79,8 @@ struct Work {
   double* fact;     // per-CTA store of factored small systems (fact_stride doubles each)
   int32_t* factp;   // per-CTA packed pivot data (TT*TT ints each)
   int64_t fact_stride;
+  int32_t* smbusy;  // per SM: CTAs of this launch inside a diagonal-tile solve (1024 slots)
+  int32_t prio;     // 1: update GEMMs yield the SM while a diagonal solve runs on it
   int64_t timeout_ns;
   int32_t max_tiles;  // max over equations of pmax * qmax
   int32_t pad;
@@ -228,5 +230,11 @@ __device__ __forceinline__ int warp_min(int v) {
 }
 
 __device__ __forceinline__ void set_err(InstState* st, int code) { atomicCAS(&st->err, 0, code); }
+
+__device__ __forceinline__ unsigned sm_id() {
+  unsigned id;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+  return id & 1023u;
+}
 
 }  // namespace sylv

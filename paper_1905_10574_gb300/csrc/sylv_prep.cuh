@@ -261,3 +261,62 @@ __global__ void k_flip(T* C, int64_t ldc, int64_t m, int64_t n, int dim) {
 }
 
 }  // namespace sylv
+
+namespace sylv {
+
+// ---------------------------------------------------------------------------
+// Batched forms of the transposition helpers (one launch for all equations).
+struct TransDesc {
+  const double* src;
+  int64_t lds;
+  double* dst;  // N x N, leading dimension N
+  int64_t N;
+};
+
+// dst_e = J src_e^T J (quasi-triangular part) for every equation e = blockIdx.z.
+__global__ void k_anti_transpose_batched(const TransDesc* __restrict__ d) {
+  __shared__ double tile[32][33];
+  const TransDesc D = d[blockIdx.z];
+  const int64_t N = D.N;
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * 32, j0 = static_cast<int64_t>(blockIdx.y) * 32;
+  if (i0 >= N || j0 >= N) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t i = i0 + yy, j = j0 + tx;
+    tile[yy][tx] = (i < N && j < N) ? D.src[(N - 1 - j) + (N - 1 - i) * D.lds] : 0.0;
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t j = j0 + yy, i = i0 + tx;
+    if (i < N && j < N) D.dst[i + j * N] = (i <= j + 1) ? tile[tx][yy] : 0.0;
+  }
+}
+
+// In-place reversal of the rows (dim 0) or columns (dim 1) of every equation's C
+// (equation e = blockIdx.y).
+__global__ void k_flip_batched(const Inst* __restrict__ inst, int dim) {
+  const Inst I = inst[blockIdx.y];
+  double* C = static_cast<double*>(I.C);
+  const int64_t m = I.m, n = I.n;
+  const int64_t half = dim == 0 ? (m / 2) * n : m * (n / 2);
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < half;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int64_t i, j, i2, j2;
+    if (dim == 0) {
+      i = t % (m / 2);
+      j = t / (m / 2);
+      i2 = m - 1 - i;
+      j2 = j;
+    } else {
+      i = t % m;
+      j = t / m;
+      i2 = i;
+      j2 = n - 1 - j;
+    }
+    const double a = C[i + j * I.ldc], b = C[i2 + j2 * I.ldc];
+    C[i + j * I.ldc] = b;
+    C[i2 + j2 * I.ldc] = a;
+  }
+}
+
+}  // namespace sylv

@@ -129,6 +129,7 @@ WORKLOADS = {
     "benign_4000": dict(m=4000, n=4000, seed=0, kind="benign", upper=1.0, tile=32),
     "benign_8000": dict(m=8000, n=8000, seed=0, kind="benign", upper=1.0, tile=32),
     "wellcond_8000": dict(m=8000, n=8000, seed=0, kind="wellcond", upper=1.0, tile=32),
+    "wellcond_4000": dict(m=4000, n=4000, seed=0, kind="wellcond", upper=1.0, tile=32),
 }
 
 

@@ -81,6 +81,9 @@ SIGNATURES = {
     "sylv_diag_wait_timeout": (ctypes.c_int, [_i64, _vp]),
     "sylv_tri_solve_noalloc": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _i64, _vp,
                                               ctypes.POINTER(sylv_result)]),
+    "sylv_tri_solve_backward_batched": (ctypes.c_int, [_i32, _P64, _P64, _PP, _P64, _PP, _P64, _PP, _P64, _P64, _PP,
+                                                       _P64, _PP, _P64, _PP, _P64, ctypes.POINTER(sylv_opts),
+                                                       ctypes.POINTER(sylv_result)]),
     "sylv_profile": (ctypes.c_int, [ctypes.c_int]),
     "sylv_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }
@@ -218,6 +221,21 @@ def sylv_tri_solve_batched(m, n, A, lda, B, ldb, C, ldc, opts: sylv_opts | None 
     return rc, [arr[i] for i in range(cnt)]
 
 
+def sylv_tri_solve_backward_batched(m, n, A, lda, B, ldb, Y, ldy, log2scale, G, ldg, dA, ldda, dB, lddb,
+                                    opts: sylv_opts | None = None):
+    """Lists of sizes / device pointers (dA, dB: lists with 0 for 'skip', or None);
+    returns (status, [sylv_result])."""
+    o = opts if opts is not None else sylv_default_opts()
+    cnt = len(m)
+    arr = (sylv_result * max(cnt, 1))()
+    rc = load().sylv_tri_solve_backward_batched(
+        cnt, _i64arr(m), _i64arr(n), _ptrarr(A), _i64arr(lda), _ptrarr(B), _i64arr(ldb), _ptrarr(Y), _i64arr(ldy),
+        _i64arr(log2scale), _ptrarr(G), _i64arr(ldg), _ptrarr(dA) if dA is not None else None,
+        _i64arr(ldda) if dA is not None else None, _ptrarr(dB) if dB is not None else None,
+        _i64arr(lddb) if dB is not None else None, ctypes.byref(o), arr)
+    return rc, [arr[i] for i in range(cnt)]
+
+
 def sylv_tri_solve_backward(m, n, A, lda, B, ldb, Y, ldy, log2scale, G, ldg, dA, ldda, dB, lddb,
                             opts: sylv_opts | None = None, result=None):
     o = opts if opts is not None else sylv_default_opts()
@@ -308,14 +326,15 @@ def solve(A, B, C, *, transa=False, transb=False, precision="fp64", tile=0, omeg
     return Y, Result(**res.as_dict())
 
 
-def batch_solve(As, Bs, Cs, *, tile=0, precision="fp64", timeout_ms=0):
-    """Solve a list of equations in one batched launch; Cs are overwritten when they are
-    column-major float64 CUDA tensors, else copies are solved.  Returns (Ys, [Result])."""
+def batch_solve(As, Bs, Cs, *, transa=False, transb=False, tile=0, precision="fp64", timeout_ms=0):
+    """Solve a list of equations op(A_i) Y_i + Y_i op(B_i) = alpha_i C_i in one batched
+    launch; Cs are overwritten when they are column-major float64 CUDA tensors, else
+    copies are solved.  Returns (Ys, [Result])."""
     torch = _torch()
     As = [fortran(a) for a in As]
     Bs = [fortran(b) for b in Bs]
     Ys = [fortran(c) for c in Cs]
-    o = make_opts(tile=tile, precision=precision, timeout_ms=timeout_ms,
+    o = make_opts(transa=transa, transb=transb, tile=tile, precision=precision, timeout_ms=timeout_ms,
                   stream=torch.cuda.current_stream().cuda_stream)
     plan = sylv_batch_create([y.shape[0] for y in Ys], [y.shape[1] for y in Ys], [a.data_ptr() for a in As],
                              [_ld(a) for a in As], [b.data_ptr() for b in Bs], [_ld(b) for b in Bs],
@@ -377,6 +396,88 @@ def _make_autograd_fn():
                 raise SylvError(rc, "sylv_tri_solve_backward")
             if res.log2scale != 0:  # undo the adjoint solve's own scaling
                 s = 2.0 ** (-res.log2scale)
+                G, dA, dB = G * s, dA * s, dB * s
+            return dA, dB, G, None, None, None
+
+    return _Fn
+
+
+class BatchSylvesterSolve:
+    """torch.autograd.Function over a batch of equations of one shape: A (b, m, m),
+    B (b, n, n), C (b, m, n) CUDA float64 tensors -> Y (b, m, n), each
+    op(A_i) Y_i + Y_i op(B_i) = alpha_i C_i solved robustly in one batched launch;
+    backward runs the batched adjoint (sylv_tri_solve_backward_batched).  Passing
+    one tensor as both A and B with transb=True gives Lyapunov equations."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, A, B, C, transa=False, transb=False, tile=0):
+        if cls._fn is None:
+            cls._fn = _make_batch_autograd_fn()
+        return cls._fn.apply(A, B, C, transa, transb, tile)
+
+
+def batch_fortran(t):
+    """(b, r, c) float64 tensor whose every [i] is column-major (strides (r*c, 1, r))."""
+    torch = _torch()
+    t = t.to(torch.float64)
+    b, r, c = t.shape
+    if t.stride(1) == 1 and t.stride(2) == max(r, 1) and t.stride(0) == r * c:
+        return t
+    return t.transpose(1, 2).contiguous().transpose(1, 2)
+
+
+def _make_batch_autograd_fn():
+    torch = _torch()
+
+    class _Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, A, B, C, transa, transb, tile):
+            Af, Bf = batch_fortran(A.detach()), batch_fortran(B.detach())
+            Y = batch_fortran(C.detach()).clone()
+            cnt, m, n = Y.shape
+            o = make_opts(transa=transa, transb=transb, tile=tile, stream=torch.cuda.current_stream().cuda_stream)
+            ea, eb, ey = Af.element_size(), Bf.element_size(), Y.element_size()
+            plan = sylv_batch_create([m] * cnt, [n] * cnt, [Af.data_ptr() + i * Af.stride(0) * ea for i in range(cnt)],
+                                     [max(m, 1)] * cnt, [Bf.data_ptr() + i * Bf.stride(0) * eb for i in range(cnt)],
+                                     [max(n, 1)] * cnt, [Y.data_ptr() + i * Y.stride(0) * ey for i in range(cnt)],
+                                     [max(m, 1)] * cnt, o)
+            try:
+                rc = sylv_batch_execute(plan, o.stream)
+                if rc != 0:
+                    raise SylvError(rc, "sylv_batch_execute")
+                rc, res = sylv_batch_results(plan, cnt)
+                if rc >= 100:
+                    raise SylvError(rc, "sylv_batch_results")
+            finally:
+                sylv_batch_destroy(plan)
+            ctx.save_for_backward(Af, Bf, Y)
+            ctx.cfg = (transa, transb, tile, [r.log2scale for r in res])
+            return Y
+
+        @staticmethod
+        def backward(ctx, gY):
+            Af, Bf, Y = ctx.saved_tensors
+            transa, transb, tile, es = ctx.cfg
+            G = batch_fortran(gY.detach()).clone()
+            cnt, m, n = G.shape
+            dA = torch.empty((cnt, m, m), dtype=torch.float64, device=G.device).transpose(1, 2)
+            dB = torch.empty((cnt, n, n), dtype=torch.float64, device=G.device).transpose(1, 2)
+            o = make_opts(transa=transa, transb=transb, tile=tile, stream=torch.cuda.current_stream().cuda_stream)
+
+            def ptrs(t):
+                return [t.data_ptr() + i * t.stride(0) * t.element_size() for i in range(cnt)]
+
+            rc, res = sylv_tri_solve_backward_batched([m] * cnt, [n] * cnt, ptrs(Af), [max(m, 1)] * cnt, ptrs(Bf),
+                                                      [max(n, 1)] * cnt, ptrs(Y), [max(m, 1)] * cnt, es, ptrs(G),
+                                                      [max(m, 1)] * cnt, ptrs(dA), [max(m, 1)] * cnt, ptrs(dB),
+                                                      [max(n, 1)] * cnt, o)
+            if rc >= 100 or rc < 0:
+                raise SylvError(rc, "sylv_tri_solve_backward_batched")
+            eg = [r.log2scale for r in res]
+            if any(eg):
+                s = torch.tensor([2.0 ** (-e) for e in eg], dtype=torch.float64, device=G.device).view(-1, 1, 1)
                 G, dA, dB = G * s, dA * s, dB * s
             return dA, dB, G, None, None, None
 

@@ -1,0 +1,98 @@
+"""GPU parity at the benchmark's full sizes, in the launch configuration bench.py
+times (tile 32, robust FP64; FP32 + refinement; the 4096-equation batch).
+
+The oracle cannot solve m = n = 4000 or 8000 in test time, but the bottom-left
+block Y[m-b:, :b] of the solution depends only on A[m-b:, m-b:], B[:b, :b] and
+C[m-b:, :b] (A and B are upper quasi-triangular, so the block equation of that
+corner involves nothing else): it is the solution of an independent b x b
+equation that the oracle solves in seconds.  The GPU's corner, shifted by the
+difference of the two scale exponents, must match it.  The residual of eq. (9)
+of the whole GPU solution is evaluated on the host where it is affordable.
+"""
+import numpy as np
+import pytest
+
+from paper_1905_10574_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FWD_TOL = 1e-12
+RESID_TOL = 1e-13
+
+
+@pytest.fixture(scope="module")
+def sy():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_10574_gb300 import build, sylv
+    build.build()
+    sylv.load()
+    return sylv
+
+
+def _rel(a, b):
+    s = max(float(np.max(np.abs(a))), float(np.max(np.abs(b))))
+    e = -int(np.frexp(s)[1]) if s > 0 else 0
+    a2, b2 = np.ldexp(a, e), np.ldexp(b, e)
+    return float(np.linalg.norm(a2 - b2) / np.linalg.norm(b2))
+
+
+def _corner(orc, A, B, C, b):
+    """Oracle solution of the bottom-left b x b corner equation."""
+    m = A.shape[0]
+    r0 = m - b
+    # do not cut a 2x2 block of A at row r0 or of B at column b
+    if A[r0, r0 - 1] != 0.0:
+        r0 -= 1
+    cb = b + 1 if B[b, b - 1] != 0.0 else b
+    out = orc.trsyl(A[r0:, r0:], B[:cb, :cb], C[r0:, :cb])
+    return r0, cb, out
+
+
+def _gpu(sy, A, B, C, **kw):
+    Y, res = sy.solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), torch.from_numpy(C).cuda(), **kw)
+    torch.cuda.synchronize()
+    return Y.cpu().numpy(), res
+
+
+def test_overflow_4000_full_size(orc, sy):
+    A, B, C, w = inputs.workload("overflow_4000")
+    Y, res = _gpu(sy, A, B, C, tile=w["tile"])
+    assert res.info == 0 and res.log2scale < 0
+    assert np.all(np.isfinite(Y)) and np.max(np.abs(Y)) <= 2.0 ** 1020
+    r0, cb, ref = _corner(orc, A, B, C, 400)
+    Yc = np.ldexp(Y[r0:, :cb], int(ref["log2scale"]) - int(res.log2scale))
+    assert _rel(Yc, ref["Y"]) <= FWD_TOL
+    assert orc.residual(A, B, Y, C, res.log2scale) <= RESID_TOL
+    _, res_nr = _gpu(sy, A, B, C, tile=w["tile"], precision="fp64_nonrobust", check=False)
+    assert res_nr.info == sy.SYLV_OVERFLOWED
+
+
+def test_mixed_8000_full_size(orc, sy):
+    A, B, C, w = inputs.workload("wellcond_8000")
+    Y, res = _gpu(sy, A, B, C, tile=w["tile"], precision="fp32_refine")
+    assert res.info == 0 and res.log2scale == 0
+    r0, cb, ref = _corner(orc, A, B, C, 300)
+    assert ref["log2scale"] == 0
+    assert _rel(Y[r0:, :cb], ref["Y"]) <= FWD_TOL
+
+
+def test_batched_4096_sampled(orc, sy):
+    shapes = inputs.batch_shapes(4096, 16, 512, seed=1234)
+    probs = [inputs.problem(m, n, 10000 + i, kind="wellcond") for i, (m, n) in enumerate(shapes)]
+    As = [torch.from_numpy(p[0]).cuda() for p in probs]
+    Bs = [torch.from_numpy(p[1]).cuda() for p in probs]
+    Cs = [torch.from_numpy(p[2]).cuda() for p in probs]
+    Ys, res = sy.batch_solve(As, Bs, Cs)
+    torch.cuda.synchronize()
+    assert all(r.info == 0 for r in res)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(len(probs), size=24, replace=False):
+        A, B, C = probs[i]
+        Yh = Ys[i].cpu().numpy()
+        assert np.all(np.isfinite(Yh))
+        ref = orc.trsyl(A, B, C)
+        assert orc.residual(A, B, Yh, C, res[i].log2scale) <= RESID_TOL
+        assert _rel(np.ldexp(Yh, int(ref["log2scale"]) - int(res[i].log2scale)), ref["Y"]) <= FWD_TOL

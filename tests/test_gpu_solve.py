@@ -308,3 +308,36 @@ def test_adjoint_finite_differences(sy):
         fd = (loss(*args_p) - loss(*args_m)) / (2 * h)
         g = float(host(grad)[idx])
         assert abs(g - fd) <= 1e-6 * max(1.0, abs(fd)), (M, idx, g, fd)
+
+
+@pytest.mark.parametrize("transa,transb", [(True, False), (False, True), (True, True)])
+def test_batched_transposes(orc, sy, transa, transb):
+    shapes = inputs.batch_shapes(10, 16, 200, seed=8)
+    probs = [inputs.problem(m, n, 300 + i, kind="benign") for i, (m, n) in enumerate(shapes)]
+    Ys, res = sy.batch_solve([dev(p[0]) for p in probs], [dev(p[1]) for p in probs], [dev(p[2]) for p in probs],
+                             transa=transa, transb=transb)
+    torch.cuda.synchronize()
+    for (A, B, C), Y, r in zip(probs, Ys, res):
+        assert r.info == 0
+        Yh = host(Y)
+        ref = orc.trsyl(A, B, C, transa=transa, transb=transb)
+        assert orc.residual(A, B, Yh, C, r.log2scale, transa, transb) <= RESID_TOL
+        assert rel(shifted(Yh, r.log2scale, ref["log2scale"]), ref["Y"]) <= FWD_TOL
+
+
+def test_batched_adjoint_lyapunov(orc, sy):
+    """A batch of Lyapunov equations A_i Y + Y A_i^T = C_i (m = n = 16) through the
+    batched autograd Function: gradients against the oracle's Kronecker form."""
+    b, m = 5, 16
+    As = np.stack([inputs.quasi_triangular(m, 50 + i, kind="wellcond") for i in range(b)])
+    Cs = np.stack([inputs.rhs(m, m, 60 + i) for i in range(b)])
+    Ws = np.stack([inputs.rhs(m, m, 70 + i) for i in range(b)])
+    At = torch.from_numpy(As).cuda().requires_grad_(True)
+    Ct = torch.from_numpy(Cs).cuda().requires_grad_(True)
+    Y = sy.BatchSylvesterSolve.apply(At, At, Ct, False, True, 0)
+    (torch.from_numpy(Ws).cuda() * Y).sum().backward()
+    for i in range(b):
+        dA1, dB1, dC, X = orc.kron_grad(As[i], As[i], Cs[i], Ws[i], False, True)
+        assert rel(host(Y[i].detach()), X) <= FWD_TOL
+        assert rel(host(At.grad[i]), dA1 + dB1) <= 1e-11
+        assert rel(host(Ct.grad[i]), dC) <= 1e-11

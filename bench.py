@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--tile", type=int, default=0, help="override the workload's tile size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary measurements (mixed precision, batched, adjoint)")
     ap.add_argument("--mode", default="solve", choices=["solve", "mixed", "batched", "adjoint"],
                     help="solve: the headline robust FP64 solve; mixed: FP32 + refinement vs FP64 at "
                          "m=n=8000; batched: 4096 uneven equations; adjoint: 256 Lyapunov forward+backward")
@@ -309,6 +311,8 @@ def run_ours(args):
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
+        if not args.no_extras and ws == 1:
+            line["secondary"] = secondary(args)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -368,14 +372,16 @@ def run_mixed(args):
             "data": "synthetic", "config": {"workload": name, "m": m, "n": n}, "fp64": out["fp64"],
             "fp32_refine": out["fp32_refine"],
             "speedup_vs_fp64": out["fp64"]["ms_per_solve"] / out["fp32_refine"]["ms_per_solve"]}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_batched(args):
-    """4096 independent equations, m, n log-uniform in [16, 512], one batched launch."""
+    """4096 independent equations, m, n log-uniform in [16, 512]: autotuned tile per
+    size bucket, one batched persistent launch captured in a CUDA graph and replayed;
+    against the plain path solving the same equations one call at a time (sampled)."""
     import numpy as np
     import torch
-    from paper_1905_10574_gb300 import build, inputs, sylv
+    from paper_1905_10574_gb300 import autotune, build, inputs, sylv
     build.build()
     count = 4096
     shapes = inputs.batch_shapes(count, 16, 512, seed=1234)
@@ -387,38 +393,71 @@ def run_batched(args):
         Bs.append(torch.from_numpy(B).to(dev))
         C0s.append(torch.from_numpy(C).to(dev))
     Cs = [c.clone() for c in C0s]
-    stream = torch.cuda.current_stream(dev)
-    opts = sylv.make_opts(tile=args.tile, stream=stream.cuda_stream)
-    plan = sylv.sylv_batch_create([m for m, _ in shapes], [n for _, n in shapes], [a.data_ptr() for a in As],
-                                  [a.stride(1) for a in As], [b.data_ptr() for b in Bs], [b.stride(1) for b in Bs],
-                                  [c.data_ptr() for c in Cs], [c.stride(1) for c in Cs], opts)
+    tiles = [args.tile] * count if args.tile else autotune.tune_batch(As, Bs, Cs)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        opts = sylv.make_opts(stream=stream.cuda_stream)
+        plan = sylv.sylv_batch_create([m for m, _ in shapes], [n for _, n in shapes], [a.data_ptr() for a in As],
+                                      [a.stride(1) for a in As], [b.data_ptr() for b in Bs],
+                                      [b.stride(1) for b in Bs], [c.data_ptr() for c in Cs],
+                                      [c.stride(1) for c in Cs], opts, tiles=tiles)
+        rc = sylv.sylv_batch_execute(plan, stream.cuda_stream)  # warm-up before capture
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            rc |= sylv.sylv_batch_execute(plan, torch.cuda.current_stream().cuda_stream)
+    if rc:
+        raise sylv.SylvError(rc, "batch")
     flops = sum(2.0 * m * n * (m + n) for m, n in shapes)
-
-    def refill():
+    ts = []
+    rs = torch.cuda.current_stream(dev)  # graph.replay() runs on the current stream
+    for i in range(args.warmup + args.steps):
         for c, c0 in zip(Cs, C0s):
             c.copy_(c0)
-
-    ts = []
-    for i in range(args.warmup + args.steps):
-        refill()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        rc = sylv.sylv_batch_execute(plan, stream.cuda_stream)
-        b.record(stream)
+        a.record(rs)
+        graph.replay()
+        b.record(rs)
         torch.cuda.synchronize()
-        if rc:
-            raise sylv.SylvError(rc, "batch")
         if i >= args.warmup:
             ts.append(a.elapsed_time(b))
     rc, res = sylv.sylv_batch_results(plan, count)
     sylv.sylv_batch_destroy(plan)
     ms = sum(ts) / len(ts)
+    # plain path, one call per equation, on a sample of 256 equations (scaled to 4096)
+    sample = list(range(0, count, count // 256))
+    cur = torch.cuda.current_stream(dev)
+    o1 = sylv.make_opts(stream=cur.cuda_stream, sync=False)
+    wsb = max(sylv.sylv_workspace_size(shapes[i][0], shapes[i][1], o1) for i in sample)
+    wsbuf = torch.empty(wsb + 256, dtype=torch.uint8, device=dev)
+    o1.workspace = (wsbuf.data_ptr() + 255) // 256 * 256
+    o1.workspace_bytes = wsb
+    rdev = torch.zeros(64, dtype=torch.uint8, device=dev)
+    Cp = [C0s[i].clone() for i in sample]
+    for j, i in enumerate(sample[:8]):
+        sylv.sylv_tri_solve_ex(shapes[i][0], shapes[i][1], As[i].data_ptr(), As[i].stride(1), Bs[i].data_ptr(),
+                               Bs[i].stride(1), Cp[j].data_ptr(), Cp[j].stride(1), o1, rdev.data_ptr())
+    Cp = [C0s[i].clone() for i in sample]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for j, i in enumerate(sample):
+        sylv.sylv_tri_solve_ex(shapes[i][0], shapes[i][1], As[i].data_ptr(), As[i].stride(1), Bs[i].data_ptr(),
+                               Bs[i].stride(1), Cp[j].data_ptr(), Cp[j].stride(1), o1, rdev.data_ptr())
+    e1.record(cur)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) * count / len(sample)
     line = {"metric": "batched solves/s", "value": count / (ms / 1000), "unit": "solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64",
-            "data": "synthetic", "config": {"count": count, "m_n": "log-uniform [16,512]", "tile": args.tile or 32},
-            "gflops_2mnmn": flops / (ms / 1000) / 1e9, "worst_info": max(r.info for r in res)}
-    print(json.dumps(line), flush=True)
+            "data": "synthetic",
+            "config": {"count": count, "m_n": "log-uniform [16,512]", "generator": "wellcond",
+                       "tiles": "autotuned per size bucket" if not args.tile else args.tile,
+                       "tile_mix": {str(t): tiles.count(t) for t in sorted(set(tiles))}, "cuda_graph": True},
+            "gflops_2mnmn": flops / (ms / 1000) / 1e9, "worst_info": max(r.info for r in res),
+            "one_call_per_equation_ms": seq_ms, "speedup_vs_one_call_per_equation": seq_ms / ms}
+    return line
 
 
 def run_adjoint(args):
@@ -445,7 +484,27 @@ def run_adjoint(args):
     line = {"metric": "differentiable Lyapunov solves/s (forward+backward)", "value": count / (ms / 1000),
             "unit": "solves/s", "n_gpus": 1, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64",
             "data": "synthetic", "config": {"count": count, "m": m, "n": m, "form": "A Y + Y A^T = C, batched"}}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def secondary(args):
+    """The other configurations, measured briefly beside the headline solve."""
+    import argparse as _ap
+    import torch
+    out = {}
+    sub = _ap.Namespace(**vars(args))
+    sub.workload, sub.tile = WORKLOAD, 0
+    sub.steps, sub.warmup = 2, 1
+    for name, fn in (("mixed_precision_8000", run_mixed), ("batched_4096", run_batched),
+                     ("adjoint_256x512", run_adjoint)):
+        try:
+            r = fn(sub)
+            r.pop("n_gpus", None)
+            out[name] = r
+        except Exception as exc:  # report, do not hide, a failing secondary measurement
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -453,11 +512,11 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "mixed":
-        run_mixed(args)
+        print(json.dumps(run_mixed(args)), flush=True)
     elif args.mode == "batched":
-        run_batched(args)
+        print(json.dumps(run_batched(args)), flush=True)
     elif args.mode == "adjoint":
-        run_adjoint(args)
+        print(json.dumps(run_adjoint(args)), flush=True)
     else:
         run_ours(args)
 

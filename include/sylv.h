@@ -153,6 +153,12 @@ int sylv_batch_create(sylv_batch_plan** plan, int32_t count, const int64_t* m, c
                       const double* const* A, const int64_t* lda, const double* const* B,
                       const int64_t* ldb, double* const* C, const int64_t* ldc,
                       const sylv_opts* opts);
+/* As sylv_batch_create, with a tile size per equation: tiles[i] in {0, 2..64}
+ * (0: opts->tile or the built-in choice), e.g. from an autotuner; NULL = none. */
+int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t* m, const int64_t* n,
+                            const double* const* A, const int64_t* lda, const double* const* B,
+                            const int64_t* ldb, double* const* C, const int64_t* ldc,
+                            const int32_t* tiles, const sylv_opts* opts);
 int sylv_batch_execute(sylv_batch_plan* plan, void* stream);
 int sylv_batch_results(sylv_batch_plan* plan, sylv_result* results);
 void sylv_batch_destroy(sylv_batch_plan* plan);

@@ -93,7 +93,6 @@ struct Layout {
   int64_t sum_tiles;
 };
 
-constexpr int kMaxCtasPerSm = 2;
 
 int sm_count();
 
@@ -106,7 +105,7 @@ int tt_of(const Seq& sh) {
 }
 
 template <class Seq>
-Layout make_layout_seq(const Seq& sh, size_t base, int cta_cap) {
+Layout make_layout_seq(const Seq& sh, size_t base, int cta_cap, int per_sm = 2) {
   Layout L{};
   int64_t tiles = 0, ib = 0, db = 0;
   int nlev = 1, mt = 0;
@@ -152,7 +151,7 @@ Layout make_layout_seq(const Seq& sh, size_t base, int cta_cap) {
   // Factor store of the diagonal-tile solves: per CTA, 5 TT^2 doubles bound
   // sum over block pairs of (s^2 + s), s = ma nb, and TT^2 packed pivot words.
   const int tt = tt_of(sh);
-  L.ncta = std::min<int64_t>(std::max<int64_t>(mt, 1), static_cast<int64_t>(sm_count()) * kMaxCtasPerSm);
+  L.ncta = std::min<int64_t>(std::max<int64_t>(mt, 1), static_cast<int64_t>(sm_count()) * per_sm);
   if (cta_cap > 0 && L.ncta > cta_cap) L.ncta = cta_cap;
   L.fstride = 5LL * tt * tt;
   L.fact = o;
@@ -166,8 +165,8 @@ Layout make_layout_seq(const Seq& sh, size_t base, int cta_cap) {
   return L;
 }
 
-Layout make_layout(const std::vector<Shape>& sh, size_t base, int cta_cap = 0) {
-  return make_layout_seq(sh, base, cta_cap);
+Layout make_layout(const std::vector<Shape>& sh, size_t base, int cta_cap = 0, int per_sm = 2) {
+  return make_layout_seq(sh, base, cta_cap, per_sm);
 }
 
 // Descriptors for each equation (host copies) given the layout.
@@ -385,7 +384,8 @@ SolvePlan plan_solve(int64_t m, int64_t n, const Opts& o) {
     P.off_rs = off;
     off = align_up(off + sizeof(RefineState));
   }
-  P.L = make_layout({P.shape}, off);
+  P.L = make_layout({P.shape}, off, 0,
+                    o.precision == SYLV_FP32_REFINE ? max_ctas_per_sm<float>() : max_ctas_per_sm<double>());
   P.total = P.L.total;
   return P;
 }
@@ -697,6 +697,13 @@ struct sylv_batch_plan {
 int sylv_batch_create(sylv_batch_plan** plan, int32_t count, const int64_t* m, const int64_t* n,
                       const double* const* A, const int64_t* lda, const double* const* B, const int64_t* ldb,
                       double* const* C, const int64_t* ldc, const sylv_opts* opts) {
+  return sylv_batch_create_tiles(plan, count, m, n, A, lda, B, ldb, C, ldc, nullptr, opts);
+}
+
+int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t* m, const int64_t* n,
+                            const double* const* A, const int64_t* lda, const double* const* B,
+                            const int64_t* ldb, double* const* C, const int64_t* ldc, const int32_t* tiles,
+                            const sylv_opts* opts) {
   if (!plan) return -1;
   *plan = nullptr;
   if (count < 0) return -2;
@@ -714,7 +721,11 @@ int sylv_batch_create(sylv_batch_plan** plan, int32_t count, const int64_t* m, c
   for (int i = 0; i < count; ++i) {
     rc = check_args(m[i], n[i], A[i], lda[i], B[i], ldb[i], C[i], ldc[i]);
     if (rc) return rc;
-    const int t = o.tile ? o.tile : auto_tile(m[i], n[i]);
+    int t = o.tile ? o.tile : auto_tile(m[i], n[i]);
+    if (tiles) {
+      if (tiles[i] < 0 || tiles[i] == 1 || tiles[i] > 64) return -11;
+      if (tiles[i]) t = tiles[i];
+    }
     if (t > 32) tt = 64;
     Shape s{m[i], n[i], t, tile_cap(m[i], t), tile_cap(n[i], t)};
     sh.push_back(s);

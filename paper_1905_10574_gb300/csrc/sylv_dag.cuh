@@ -37,14 +37,18 @@ template <int TT, typename T>
 struct DagSmem {
   static constexpr int LDG = TT + 2;  // row stride of the GEMM operands (16-byte aligned rows)
   static constexpr int LDY = TT + 1;  // leading dimension of the Y, A_kk, B_ll tiles
-  static constexpr int G = TT <= 32 ? 3 : 1;  // producers staged together in one GEMM pass
+  // Producers staged together in one GEMM pass: binary32 tiles are half the size,
+  // and the FP32 correction solves are bound by per-update latency, so they stage more.
+  static constexpr int G = sizeof(T) == 4 ? (TT <= 32 ? 6 : 2) : (TT <= 32 ? 3 : 1);
   T L[G * TT * LDG];                  // left GEMM operands, k-major; A_kk in the diagonal phases
   T R[G * TT * LDG];                  // right GEMM operands, k-major; B_ll in the diagonal phases
   int gside[G], gprod[G], gk[G], goff[G];  // the current group of producers
   int gn, gktot, gfast;
   T Y[TT * LDY];                      // the tile being solved (column-major)
   double zbuf[TT][4];                 // this step's solved 1x1/2x2 blocks, by block column
-  static constexpr bool kFactSmem = (TT <= 32);  // small-system factors kept in shared memory
+  // Small-system factors in shared memory for the FP64 tile-32 kernel; the FP32
+  // kernel keeps them in its global slot to fit more CTAs per SM.
+  static constexpr bool kFactSmem = (TT <= 32) && sizeof(T) == 8;
   double fact[kFactSmem ? 5 * TT * TT : 1];      // factor store (see pair_offset), if kFactSmem
   int factp[kFactSmem ? TT * TT : 1];            // packed pivots, if kFactSmem
   unsigned long long acolmax[TT];     // per A block kb: max_r<start(kb) sum_i in kb |A[r,i]| (bits)

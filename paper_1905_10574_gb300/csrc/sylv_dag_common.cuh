@@ -24,7 +24,8 @@ cudaError_t launch_dag_impl(const Work& w, int max_tasks, cudaStream_t stream, i
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dag_kernel<TT, T, ROBUST>, kThreads, smem);
     if (e != cudaSuccess) return e;
     per_sm = nb > 0 ? nb : 1;
-    if (per_sm > 2) per_sm = 2;  // the workspace holds factor stores for 2 CTAs per SM
+    // the workspace holds factor stores for kMaxCtasPerSm<T> CTAs per SM
+    if (per_sm > max_ctas_per_sm<T>()) per_sm = max_ctas_per_sm<T>();
     // Experiment knob: SYLV_CTAS_PER_SM=1 keeps one CTA per SM (no FP64-pipe sharing).
     if (const char* env = std::getenv("SYLV_CTAS_PER_SM")) {
       const int v = std::atoi(env);

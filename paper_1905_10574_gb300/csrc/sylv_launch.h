@@ -8,6 +8,14 @@
 
 namespace sylv {
 
+// CTAs per SM the tile kernel may use (and the workspace reserves factor stores for):
+// 2 for the FP64 kernel (FP64-pipe bound), 4 for the FP32 correction solves
+// (latency bound).
+template <typename T>
+constexpr int max_ctas_per_sm() {
+  return sizeof(T) == 4 ? 4 : 2;
+}
+
 // Launch the persistent DAG kernel for tile capacity tt (32 or 64) on `stream`.
 // max_tasks bounds the grid (no more CTAs than tiles).  Returns the launch error.
 cudaError_t launch_dag_f64(int tt, bool robust, const Work& w, int max_tasks, cudaStream_t stream);

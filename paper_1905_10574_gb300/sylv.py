@@ -69,6 +69,9 @@ SIGNATURES = {
     "sylv_workspace_size": (ctypes.c_size_t, [_i64, _i64, ctypes.POINTER(sylv_opts)]),
     "sylv_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _i32, _P64, _P64, _PP, _P64, _PP,
                                          _P64, _PP, _P64, ctypes.POINTER(sylv_opts)]),
+    "sylv_batch_create_tiles": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _i32, _P64, _P64, _PP, _P64, _PP,
+                                               _P64, _PP, _P64, ctypes.POINTER(ctypes.c_int32),
+                                               ctypes.POINTER(sylv_opts)]),
     "sylv_batch_execute": (ctypes.c_int, [_vp, _vp]),
     "sylv_batch_results": (ctypes.c_int, [_vp, ctypes.POINTER(sylv_result)]),
     "sylv_batch_destroy": (None, [_vp]),
@@ -186,13 +189,19 @@ def _ptrarr(v):
     return (ctypes.c_void_p * len(v))(*[int(x) for x in v])
 
 
-def sylv_batch_create(m, n, A, lda, B, ldb, C, ldc, opts: sylv_opts | None = None):
-    """Lists of sizes and device pointers; returns an opaque plan handle."""
+def sylv_batch_create(m, n, A, lda, B, ldb, C, ldc, opts: sylv_opts | None = None, tiles=None):
+    """Lists of sizes and device pointers (and optionally a tile size per equation);
+    returns an opaque plan handle."""
     o = opts if opts is not None else sylv_default_opts()
     h = ctypes.c_void_p()
     cnt = len(m)
-    rc = load().sylv_batch_create(ctypes.byref(h), cnt, _i64arr(m), _i64arr(n), _ptrarr(A), _i64arr(lda),
-                                  _ptrarr(B), _i64arr(ldb), _ptrarr(C), _i64arr(ldc), ctypes.byref(o))
+    if tiles is None:
+        rc = load().sylv_batch_create(ctypes.byref(h), cnt, _i64arr(m), _i64arr(n), _ptrarr(A), _i64arr(lda),
+                                      _ptrarr(B), _i64arr(ldb), _ptrarr(C), _i64arr(ldc), ctypes.byref(o))
+    else:
+        t = (ctypes.c_int32 * max(cnt, 1))(*[int(x) for x in tiles])
+        rc = load().sylv_batch_create_tiles(ctypes.byref(h), cnt, _i64arr(m), _i64arr(n), _ptrarr(A), _i64arr(lda),
+                                            _ptrarr(B), _i64arr(ldb), _ptrarr(C), _i64arr(ldc), t, ctypes.byref(o))
     if rc != 0:
         raise SylvError(rc, "sylv_batch_create")
     return h

@@ -341,3 +341,66 @@ def test_batched_adjoint_lyapunov(orc, sy):
         assert rel(host(Y[i].detach()), X) <= FWD_TOL
         assert rel(host(At.grad[i]), dA1 + dB1) <= 1e-11
         assert rel(host(Ct.grad[i]), dC) <= 1e-11
+
+
+def test_batched_cuda_graph_replay(orc, sy):
+    """A batch plan's execute captured once in a CUDA graph and replayed twice, with the
+    right-hand sides refilled before each replay, gives the oracle's solutions."""
+    shapes = inputs.batch_shapes(12, 16, 160, seed=21)
+    probs = [inputs.problem(m, n, 700 + i, kind="benign") for i, (m, n) in enumerate(shapes)]
+    As = [dev(p[0]) for p in probs]
+    Bs = [dev(p[1]) for p in probs]
+    C0 = [dev(p[2]) for p in probs]
+    Cs = [c.clone() for c in C0]
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        o = sy.make_opts(stream=stream.cuda_stream)
+        plan = sy.sylv_batch_create([m for m, _ in shapes], [n for _, n in shapes], [a.data_ptr() for a in As],
+                                    [a.stride(1) for a in As], [b.data_ptr() for b in Bs], [b.stride(1) for b in Bs],
+                                    [c.data_ptr() for c in Cs], [c.stride(1) for c in Cs], o)
+        assert sy.sylv_batch_execute(plan, stream.cuda_stream) == 0
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            assert sy.sylv_batch_execute(plan, torch.cuda.current_stream().cuda_stream) == 0
+    try:
+        for _ in range(2):
+            for c, c0 in zip(Cs, C0):
+                c.copy_(c0)
+            g.replay()
+            torch.cuda.synchronize()
+            rc, res = sy.sylv_batch_results(plan, len(shapes))
+            assert rc == 0
+            for (A, B, C), Y, r in zip(probs, Cs, res):
+                ref = orc.trsyl(A, B, C)
+                Yh = host(Y)
+                assert r.info == 0
+                assert rel(shifted(Yh, r.log2scale, ref["log2scale"]), ref["Y"]) <= FWD_TOL
+    finally:
+        sy.sylv_batch_destroy(plan)
+
+
+def test_autotuned_tiles_solve_correctly(orc, sy):
+    from paper_1905_10574_gb300 import autotune
+    shapes = inputs.batch_shapes(16, 16, 300, seed=33)
+    probs = [inputs.problem(m, n, 800 + i, kind="benign") for i, (m, n) in enumerate(shapes)]
+    As = [dev(p[0]) for p in probs]
+    Bs = [dev(p[1]) for p in probs]
+    Cs = [dev(p[2]) for p in probs]
+    tiles = autotune.tune_batch(As, Bs, Cs, use_cache=False, reps=1)
+    assert len(tiles) == len(shapes) and all(t in autotune.CANDIDATES for t in tiles)
+    for c, p in zip(Cs, probs):  # inputs restored after tuning
+        assert np.array_equal(host(c), p[2])
+    o = sy.make_opts(stream=torch.cuda.current_stream().cuda_stream)
+    plan = sy.sylv_batch_create([m for m, _ in shapes], [n for _, n in shapes], [a.data_ptr() for a in As],
+                                [a.stride(1) for a in As], [b.data_ptr() for b in Bs], [b.stride(1) for b in Bs],
+                                [c.data_ptr() for c in Cs], [c.stride(1) for c in Cs], o, tiles=tiles)
+    try:
+        assert sy.sylv_batch_execute(plan, o.stream) == 0
+        rc, res = sy.sylv_batch_results(plan, len(shapes))
+    finally:
+        sy.sylv_batch_destroy(plan)
+    for (A, B, C), Y, r in zip(probs, Cs, res):
+        ref = orc.trsyl(A, B, C)
+        assert rel(shifted(host(Y), r.log2scale, ref["log2scale"]), ref["Y"]) <= FWD_TOL

@@ -45,17 +45,17 @@ struct DagSmem {
   int gside[G], gprod[G], gk[G], goff[G];  // the current group of producers
   int gn, gktot, gfast;
   T Y[TT * LDY];                      // the tile being solved (column-major)
-  double zbuf[TT][4];                 // this step's solved 1x1/2x2 blocks, by block column
-  // Small-system factors in shared memory for the FP64 tile-32 kernel; the FP32
-  // kernel keeps them in its global slot to fit more CTAs per SM.
-  static constexpr bool kFactSmem = (TT <= 32) && sizeof(T) == 8;
-  double fact[kFactSmem ? 5 * TT * TT : 1];      // factor store (see pair_offset), if kFactSmem
-  int factp[kFactSmem ? TT * TT : 1];            // packed pivots, if kFactSmem
+  // Small-system inverses in shared memory for tile capacity 32; the tile-64 kernels
+  // keep them in the CTA's global slot.
+  static constexpr bool kFactSmem = (TT <= 32);
+  double fact[kFactSmem ? 5 * TT * TT : 1];      // inverse store (see pair_offset), if kFactSmem
+  int factp[kFactSmem ? TT * TT : 1];            // per pair: bit 16 = a pivot was raised, if kFactSmem
+  unsigned short eord[TT * TT];       // tile elements in wavefront order: row | col << 6 | vec index << 12
+  short sstart[2 * TT];               // first entry of each wavefront step in eord
   unsigned long long acolmax[TT];     // per A block kb: max_r<start(kb) sum_i in kb |A[r,i]| (bits)
   unsigned long long bcolmax[TT];     // per B block lb: max_c>=end(lb) sum_j in lb |B[j,c]| (bits)
   short pr0[TT], pma[TT];             // this step: first row and height of the block solved in column block lb
-  unsigned long long pzm[TT];         // max |z| of each solved block of this step (bit pattern)
-  unsigned long long wmax[kThreads / 32];  // per-warp max |y| over unsolved elements
+  unsigned wmax[kThreads / 32];       // per-warp bound on |y| over unsolved elements (high word, rounded up)
   int pe[TT];                         // scale exponent of each solved block of this step
   int pa[TT + 1];                     // factor-store offset of block row kb (see pair_offset)
   int qb2[TT + 1];                    // prefix sums of squared B block sizes
@@ -100,14 +100,19 @@ __device__ __forceinline__ int guard_division(double r, double d, double rcp, do
 // ----------------------------------------------------------------------------
 // Small Sylvester systems (Sec. 2.1): A11 Z + Z B11 = beta R with A11 ma x ma,
 // B11 nb x nb (ma, nb in {1,2}) is (I (x) A11 + B11^T (x) I) vec Z = beta vec R, an
-// s x s system (s = ma nb), solved by Gaussian elimination with complete pivoting.
-// The elimination of the matrix does not depend on the right-hand side, so it is
-// done once per tile (pair_factor) and stored: multipliers below the diagonal, U on
-// and above it (pivots below smin raised to smin), 1/pivot after the s*s entries,
-// and the row/column interchanges in a packed int (2 bits each; bit 16: a pivot was
-// raised).  pair_solve then applies the same row interchanges and eliminations to
-// the right-hand side, in the same order, with each update guarded by ProtectUpdate
-// and each division (a multiplication by the stored reciprocal) by ProtectDivision.
+// s x s system M vec Z = beta vec R (s = ma nb).  The matrix does not depend on the
+// right-hand side, so each tile factors it once per pair (Gaussian elimination
+// with complete pivoting, pivots below smin raised to smin) and stores its inverse
+// (pair_prepare).  In the common case a wavefront step then computes
+// every element of Z as one dot product, z_e = sum_u Minv[e][u] r_u, one thread per
+// element; that is safe from overflow whenever ||Minv||_inf max|r| stays below
+// omega by a margin (an exponent test).  Otherwise the block is solved by
+// pair_solve_guarded: the same eliminations applied to the right-hand side, each
+// update guarded by ProtectUpdate and each division (a multiplication by the stored
+// reciprocal) by ProtectDivision, as the robust small solve of Algorithm 2 requires.
+// pair_factor's layout: multipliers below the diagonal, U on and above it, 1/pivot
+// after the s*s entries; the row/column interchanges in a packed int (2 bits each;
+// bit 16: a pivot was raised).
 __device__ inline int pair_factor(int ma, int nb, const double* a, const double* b, double smin, double* out) {
   const int s = ma * nb;
   double M[4][4];
@@ -242,65 +247,142 @@ __device__ __noinline__ int pair_solve_guarded(const double* f, int pack, double
   return lb;
 }
 
-// The common case of pair_solve_guarded: the same eliminations without guards,
-// tracking in integers the exponent bound every guard would test (the fast test of
-// guard_update / guard_division).  If no bound reaches omega, every guard would have
-// returned 1 and the result is bitwise that of the guarded solve; otherwise the
-// guarded solve reruns from the saved right-hand side (rare, kept out of line).
-template <int S>
-__device__ __forceinline__ int pair_solve(const double* f, int pack, double (&r)[4], double omega, int eo,
-                                          bool robust) {
-  double r_in[4];
+// The factorization of pair_factor for a compile-time block shape (MA x MA with
+// NB x NB), in registers, followed by the inverse: column k of Minv solves
+// M x = e_k with the same interchanges, multipliers and reciprocals.  Writes Minv
+// row-major (Minv[e][u] at out[e*S+u]) and ||Minv||_inf at out[S*S]; a non-finite
+// entry (a raised pivot of a near-singular pair can overflow) stores an infinite
+// norm, which sends every solve of the pair to the guarded path.  Returns the
+// packed interchanges.
+template <int MA, int NB>
+__device__ __forceinline__ int pair_prepare(const double (&a)[4], const double (&b)[4], double smin, double* out) {
+  constexpr int S = MA * NB;
+  double M[S][S];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) r_in[u] = r[u];
-  int mx = -4096;
+  for (int u = 0; u < S; ++u)
+#pragma unroll
+    for (int v = 0; v < S; ++v) {
+      double e = 0.0;
+      if (u / MA == v / MA) e += a[(u % MA) + 2 * (v % MA)];
+      if (u % MA == v % MA) e += b[(v / MA) + 2 * (u / MA)];
+      M[u][v] = e;
+    }
+  int cperm[S];
+#pragma unroll
+  for (int u = 0; u < S; ++u) cperm[u] = u;
+  double rcp[S];
+  int pack = 0;
 #pragma unroll
   for (int st = 0; st < S; ++st) {
-    const int pr = (pack >> (2 * st)) & 3;
+    int pr = st, pc = st;
+    unsigned long long best = abs_bits(M[st][st]);
+#pragma unroll
+    for (int u = st; u < S; ++u)
+#pragma unroll
+      for (int v = st; v < S; ++v) {
+        const unsigned long long mag = abs_bits(M[u][v]);
+        if (mag > best) {
+          best = mag;
+          pr = u;
+          pc = v;
+        }
+      }
 #pragma unroll
     for (int k = st + 1; k < S; ++k)
-      if (pr == k) {
-        const double tmp = r[st];
-        r[st] = r[k];
-        r[k] = tmp;
-      }
-  }
+      if (pr == k)
 #pragma unroll
-  for (int st = 0; st < S; ++st)
+        for (int v = 0; v < S; ++v) {
+          const double t = M[st][v];
+          M[st][v] = M[k][v];
+          M[k][v] = t;
+        }
+#pragma unroll
+    for (int k = st + 1; k < S; ++k)
+      if (pc == k) {
+#pragma unroll
+        for (int u = 0; u < S; ++u) {
+          const double t = M[u][st];
+          M[u][st] = M[u][k];
+          M[u][k] = t;
+        }
+        const int ct = cperm[st];
+        cperm[st] = cperm[k];
+        cperm[k] = ct;
+      }
+    pack |= (pr & 3) << (2 * st);
+    if (fabs(M[st][st]) < smin) {
+      M[st][st] = smin;
+      pack |= 1 << 16;
+    }
+    rcp[st] = 1.0 / M[st][st];
 #pragma unroll
     for (int u = st + 1; u < S; ++u) {
-      const double l = f[u * S + st];
-      mx = max(mx, max(ub_log2(r[u]), ub_log2(l) + ub_log2(r[st])) + 1);
-      r[u] = fma(-l, r[st], r[u]);
+      const double l = M[u][st] * rcp[st];
+      M[u][st] = l;
+#pragma unroll
+      for (int v = st + 1; v < S; ++v) M[u][v] = fma(-l, M[st][v], M[u][v]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < S; ++u) pack |= (cperm[u] & 3) << (8 + 2 * u);
+  double inv[S][S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    double r[S];
+#pragma unroll
+    for (int u = 0; u < S; ++u) r[u] = (u == k) ? 1.0 : 0.0;
+#pragma unroll
+    for (int st = 0; st < S; ++st) {
+      const int pr = (pack >> (2 * st)) & 3;
+#pragma unroll
+      for (int kk = st + 1; kk < S; ++kk)
+        if (pr == kk) {
+          const double t = r[st];
+          r[st] = r[kk];
+          r[kk] = t;
+        }
     }
 #pragma unroll
-  for (int i = S - 1; i >= 0; --i) {
+    for (int st = 0; st < S; ++st)
 #pragma unroll
-    for (int v = i + 1; v < S; ++v) {
-      const double uiv = f[i * S + v];
-      mx = max(mx, max(ub_log2(r[i]), ub_log2(uiv) + ub_log2(r[v])) + 1);
-      r[i] = fma(-uiv, r[v], r[i]);
+      for (int u = st + 1; u < S; ++u) r[u] = fma(-M[u][st], r[st], r[u]);
+#pragma unroll
+    for (int i = S - 1; i >= 0; --i) {
+#pragma unroll
+      for (int v = i + 1; v < S; ++v) r[i] = fma(-M[i][v], r[v], r[i]);
+      r[i] = r[i] * rcp[i];
     }
-    const double rcp = f[S * S + i];
-    mx = max(mx, ub_log2(r[i]) + ub_log2(rcp));
-    r[i] = r[i] * rcp;
+#pragma unroll
+    for (int u = 0; u < S; ++u)
+#pragma unroll
+      for (int t = 0; t < S; ++t)
+        if (cperm[u] == t) inv[t][k] = r[u];
   }
-  if (robust && mx > eo) {
+  double nrm = 0.0;
+  bool finite = true;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) r[u] = r_in[u];
-    return pair_solve_guarded<S>(f, pack, r, omega, eo, robust);
+  for (int e = 0; e < S; ++e) {
+    double rs = 0.0;
+#pragma unroll
+    for (int u = 0; u < S; ++u) {
+      out[e * S + u] = inv[e][u];
+      rs += fabs(inv[e][u]);
+    }
+    finite = finite && (rs <= 1.7976931348623157e308);
+    nrm = rs > nrm ? rs : nrm;
   }
-  double x[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-  for (int u = 0; u < S; ++u) {
-    const int cu = (pack >> (8 + 2 * u)) & 3;
-#pragma unroll
-    for (int t = 0; t < S; ++t)
-      if (cu == t) x[t] = r[u];
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) r[u] = x[u];
-  return 0;
+  out[S * S] = finite ? nrm : __longlong_as_double(0x7ff0000000000000ll);
+  return pack;
+}
+
+// Upper bound of |v| kept in 32 bits: the high word of its bit pattern, plus one
+// unless the low word is zero (so the bound never falls below |v|).
+__device__ __forceinline__ unsigned hi_bound(double v) {
+  const unsigned long long b = abs_bits(v);
+  return static_cast<unsigned>(b >> 32) + ((b & 0xffffffffull) != 0ull ? 1u : 0u);
+}
+__device__ __forceinline__ double from_hi_bound(unsigned h) {
+  return bits_to_double(static_cast<unsigned long long>(h) << 32);
 }
 
 // Block structure of an upper quasi-triangular tile (Sec. 1, eq. (4)): a nonzero
@@ -415,30 +497,78 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
         a[i + 2 * j] = (i < ma && j < ma) ? static_cast<double>(Ak[(ra + i) + (ra + j) * LDY]) : 0.0;
         b[i + 2 * j] = (i < nb && j < nb) ? static_cast<double>(Bk[(cb0 + i) + (cb0 + j) * LDY]) : 0.0;
       }
-    factp[kb * TT + lb] = pair_factor(ma, nb, a, b, smin, fact + pair_offset(sh, kb, lb, ma));
+    double* o = fact + pair_offset(sh, kb, lb, ma);
+    int pack;
+    if (ma == 1 && nb == 1)
+      pack = pair_prepare<1, 1>(a, b, smin, o);
+    else if (ma == 2 && nb == 1)
+      pack = pair_prepare<2, 1>(a, b, smin, o);
+    else if (ma == 1)
+      pack = pair_prepare<1, 2>(a, b, smin, o);
+    else
+      pack = pair_prepare<2, 2>(a, b, smin, o);
+    factp[kb * TT + lb] = pack;
+  }
+  // Wavefront order of the tile's elements: step s holds the blocks (kb, lb) with
+  // (pb-1-kb) + lb = s, the 2x2-by-2x2 blocks first, then the 2-element ones, then
+  // the 1x1 ones, so that a warp's lanes mostly share one dot-product length.
+  const int nsteps = pb + qb - 1;
+  for (int s = tid; s < nsteps; s += kThreads) {
+    int cnt = 0;
+    for (int lb = max(0, s - (pb - 1)); lb <= min(s, qb - 1); ++lb) {
+      const int kb = pb - 1 - (s - lb);
+      cnt += (sh.astart[kb + 1] - sh.astart[kb]) * (sh.bstart[lb + 1] - sh.bstart[lb]);
+    }
+    sh.sstart[s + 1] = static_cast<short>(cnt);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    sh.sstart[0] = 0;
+    for (int s = 0; s < nsteps; ++s) sh.sstart[s + 1] = static_cast<short>(sh.sstart[s + 1] + sh.sstart[s]);
+  }
+  __syncthreads();
+  for (int s = tid; s < nsteps; s += kThreads) {
+    int pos = sh.sstart[s];
+    for (int want = 4; want >= 1; want >>= 1)
+      for (int lb = max(0, s - (pb - 1)); lb <= min(s, qb - 1); ++lb) {
+        const int kb = pb - 1 - (s - lb);
+        const int ra = sh.astart[kb], ma = sh.astart[kb + 1] - ra;
+        const int cb0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - cb0;
+        if (ma * nb != want) continue;
+        for (int jc = 0; jc < nb; ++jc)
+          for (int ir = 0; ir < ma; ++ir)
+            sh.eord[pos++] = static_cast<unsigned short>((ra + ir) | ((cb0 + jc) << 6) | ((ir + ma * jc) << 12));
+      }
   }
   __syncthreads();
 }
 
 // Diagonal-tile solve: Algorithm 2 applied to one tile, in wavefront order over its
 // 1x1/2x2 blocks.  The blocks (kb, lb) on the anti-diagonal s = (pb-1-kb) + lb are
-// independent; a step solves them (one thread per block, stored factors), agrees on
-// one tile-wide power of two, and every element's owner applies the step's
-// contributions (no element has two writers).
+// independent; a step solves them (Phase A: one thread per element, the stored
+// inverses; a block whose bound test fails is solved by its first thread with the
+// guarded elimination), agrees on one tile-wide power of two (Phase B, only when
+// some bound comes near omega), and every unsolved element's owner applies the
+// step's contributions (Phase C).  Unsolved elements live in their owners'
+// registers; an element is written to shared memory when it becomes the right-hand
+// side of the next step, and when it is solved.
 // Robustness, element-wise with omega' = omega/2 (so every 1x1/2x2 block's row sum
-// stays <= omega): U = max |y| over unsolved elements (exact, recomputed every
-// step); a step's blocks are solved with omega'; the step then scales the whole tile
-// by 2^g with g = e_min + zeta such that
+// stays <= omega): U bounds |y| over unsolved elements (recomputed every step); a
+// step's blocks are solved with omega'; the step then scales the whole tile by 2^g
+// with g = e_min + zeta such that
 //   2^zeta (2^e_min U + As Zm + Zm Bs) <= omega',
 // As = max over the step's blocks of the A row sums above them, Bs = max of the B
 // column sums right of them, Zm = max |z| of the step's blocks at the common scale.
 // When all exponents are far from omega' the decision is taken from the exponent
-// fields alone (g = e_min, no FP64 work); otherwise warp 0 evaluates ProtectUpdate.
+// fields alone (g = e_min = 0, no FP64 work); otherwise warp 0 evaluates
+// ProtectUpdate.
 template <int TT, typename T, bool ROBUST>
-__device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, const double* gfact, const int* gfactp) {
+__device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, double smin, const double* gfact,
+                           const int* gfactp) {
   constexpr int LDY = DagSmem<TT, T>::LDY;
   constexpr int CSTEP = kThreads / TT;
   constexpr int NC = TT / CSTEP;  // columns owned per thread
+  constexpr int NW = kThreads / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double* fact = DagSmem<TT, T>::kFactSmem ? sh.fact : gfact;
   const int* factp = DagSmem<TT, T>::kFactSmem ? sh.factp : gfactp;
@@ -449,56 +579,56 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
   const double omh = 0.5 * omega;
   const int eo = floor_log2(omh);
 
-  // Element ownership: row tid % TT, columns tid / TT + j * CSTEP (j < NC); the
-  // per-column data below is fixed for the whole solve.
+  // Element ownership: row tid % TT, columns tid / TT + j * CSTEP (j < NC).
   const int my_r = tid % TT;
   const int my_c0 = tid / TT;
   const bool row_ok = my_r < mt;
   const int kb_r = row_ok ? sh.rowblk[my_r] : 0;
-  const int dr = pb - 1 - kb_r;
-  const int ra_r = row_ok ? sh.astart[kb_r] : 0;
-  const int ma_r = row_ok ? sh.astart[kb_r + 1] - ra_r : 1;
-  const int rr_in = my_r - ra_r;  // row within its block
+  const int dr = pb - 1 - kb_r;  // distance of this row's block from the bottom
   bool okj[NC];
-  int lbcj[NC], offj[NC];
+  int lbcj[NC];
+  T yv[NC];
 #pragma unroll
   for (int j = 0; j < NC; ++j) {
     const int c = my_c0 + j * CSTEP;
     okj[j] = row_ok && c < nt;
     lbcj[j] = okj[j] ? sh.colblk[c] : 0;
-    offj[j] = okj[j] ? c - sh.bstart[lbcj[j]] : 0;
+    yv[j] = okj[j] ? Ys[my_r + c * LDY] : T(0);
   }
 
   // Initial U (and a pre-scaling if the tile exceeds omega').
-  unsigned long long um = 0;
+  if (ROBUST) {
+    unsigned um = 0;
 #pragma unroll
-  for (int j = 0; j < NC; ++j)
-    if (okj[j]) {
-      const unsigned long long b = abs_bits(static_cast<double>(Ys[my_r + (my_c0 + j * CSTEP) * LDY]));
-      um = b > um ? b : um;
-    }
-  um = warp_max_u64(um);
-  if (lane == 0) sh.wmax[warp] = um;
+    for (int j = 0; j < NC; ++j)
+      if (okj[j]) um = max(um, hi_bound(static_cast<double>(yv[j])));
+    um = __reduce_max_sync(0xffffffffu, um);
+    if (lane == 0) sh.wmax[warp] = um;
+  }
   if (tid == 0) {
     sh.e_diag = 0;
     sh.slow = 0;
   }
   __syncthreads();
   if (ROBUST) {
-    unsigned long long u0 = 0;
-    for (int w = 0; w < kThreads / 32; ++w) u0 = sh.wmax[w] > u0 ? sh.wmax[w] : u0;
-    const double U0 = bits_to_double(u0);
+    unsigned u0 = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) u0 = max(u0, sh.wmax[w]);
+    const double U0 = from_hi_bound(u0);
     if (U0 > omh) {  // keep every element within omega'
       const int z = floor_log2(omh) - ceil_log2(U0);
+      unsigned um = 0;
 #pragma unroll
       for (int j = 0; j < NC; ++j)
         if (okj[j]) {
-          T* yp = &Ys[my_r + (my_c0 + j * CSTEP) * LDY];
-          *yp = mul2(*yp, z);
+          yv[j] = mul2(yv[j], z);
+          Ys[my_r + (my_c0 + j * CSTEP) * LDY] = yv[j];
+          um = max(um, hi_bound(static_cast<double>(yv[j])));
         }
       if (tid == 0) sh.e_diag = z;
+      um = __reduce_max_sync(0xffffffffu, um);
       __syncthreads();
-      if (lane == 0) sh.wmax[warp] = abs_bits(mul2(U0, z));
+      if (lane == 0) sh.wmax[warp] = um;
       __syncthreads();
     }
   }
@@ -506,54 +636,89 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
   int local_scale_events = 0;
   const int nsteps = pb + qb - 1;
   for (int s = 0; s < nsteps; ++s) {
-    const int lb_lo = max(0, s - (pb - 1));
-    const int lb_hi = min(s, qb - 1);
-    // Phase A: this step's blocks, one thread each (block i of the step on warp
-    // i % 8, so the warps share the work); publish their geometry.
-    const int npairs = lb_hi - lb_lo + 1;
-    const int my_pair = (tid & 31) * (kThreads / 32) + (tid >> 5);
-    for (int lb = lb_lo + my_pair; lb <= lb_hi && my_pair < npairs; lb += kThreads) {
-      const int kb = pb - 1 - (s - lb);
-      const int r0 = sh.astart[kb], ma = sh.astart[kb + 1] - r0;
-      const int c0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - c0;
-      const int sz = ma * nb;
-      const int pack = factp[kb * TT + lb];
-      if (pack & (1 << 16)) near = true;
-      double rr[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        rr[u] = (u < sz) ? static_cast<double>(Ys[(r0 + (ma == 2 ? (u & 1) : 0)) + (c0 + (ma == 2 ? (u >> 1) : u)) * LDY])
-                         : 0.0;
+    // Phase A: the step's elements, one thread each.  All reads of the step's
+    // right-hand sides come before any write of a solution (__syncwarp).
+    const int e0 = sh.sstart[s];
+    const bool act = tid < sh.sstart[s + 1] - e0;
+    int r = 0, c = 0, e = 0, r0 = 0, c0 = 0, ma = 1, sz = 0, lb = 0, eb = 0, mode = 0;
+    double rv[4] = {0.0, 0.0, 0.0, 0.0};
+    double z = 0.0;
+    if (act) {
+      const unsigned code = sh.eord[e0 + tid];
+      r = code & 63;
+      c = (code >> 6) & 63;
+      e = code >> 12;
+      const int kb = sh.rowblk[r];
+      lb = sh.colblk[c];
+      r0 = sh.astart[kb];
+      ma = sh.astart[kb + 1] - r0;
+      c0 = sh.bstart[lb];
+      const int nb = sh.bstart[lb + 1] - c0;
+      sz = ma * nb;
       const double* f = fact + pair_offset(sh, kb, lb, ma);
-      int e;
-      if (sz == 1)
-        e = pair_solve<1>(f, pack, rr, omh, eo, ROBUST);
-      else if (sz == 2)
-        e = pair_solve<2>(f, pack, rr, omh, eo, ROBUST);
-      else
-        e = pair_solve<4>(f, pack, rr, omh, eo, ROBUST);
-      unsigned long long zm = 0;
+      if (factp[kb * TT + lb] & (1 << 16)) near = true;
+      unsigned long long rmb = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        sh.zbuf[lb][u] = rr[u];
-        const unsigned long long bv = abs_bits(rr[u]);
-        zm = bv > zm ? bv : zm;
+        rv[u] = (u < sz) ? static_cast<double>(Ys[(r0 + (ma == 2 ? (u & 1) : 0)) + (c0 + (ma == 2 ? (u >> 1) : u)) * LDY])
+                         : 0.0;
+        const unsigned long long bv = abs_bits(rv[u]);
+        rmb = bv > rmb ? bv : rmb;
       }
-      sh.pe[lb] = e;
-      sh.pzm[lb] = zm;
-      sh.pr0[lb] = static_cast<short>(r0);
-      sh.pma[lb] = static_cast<short>(ma);
-      if (ROBUST) {
-        unsigned long long u0 = 0;
-        for (int w = 0; w < kThreads / 32; ++w) u0 = sh.wmax[w] > u0 ? sh.wmax[w] : u0;
-        const int ez = ub_log2(bits_to_double(zm));
-        const bool fast = e == 0 && ub_log2(bits_to_double(u0)) + 2 <= eo &&
-                          ub_log2(bits_to_double(sh.acolmax[kb])) + ez + 2 <= eo &&
-                          ez + ub_log2(bits_to_double(sh.bcolmax[lb])) + 2 <= eo;
-        if (!fast) sh.slow = 1;
+      const bool ok = !ROBUST || ub_log2(f[sz * sz]) + ub_log2(bits_to_double(rmb)) + 1 <= eo;
+      if (ok) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (u < sz) z = fma(f[e * sz + u], rv[u], z);
+        mode = 1;
+        if (ROBUST) {
+          unsigned u0 = 0;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) u0 = max(u0, sh.wmax[w]);
+          const int ez = ub_log2(z);
+          const bool fast = ub_log2(from_hi_bound(u0)) + 2 <= eo &&
+                            ub_log2(bits_to_double(sh.acolmax[kb])) + ez + 2 <= eo &&
+                            ez + ub_log2(bits_to_double(sh.bcolmax[lb])) + 2 <= eo;
+          if (!fast) sh.slow = 1;
+        }
+      } else if (e == 0) {
+        // Guarded small solve of the whole block by its first thread (rare).
+        double a[4], b[4];
+        for (int i = 0; i < 2; ++i)
+          for (int jj = 0; jj < 2; ++jj) {
+            a[i + 2 * jj] = (i < ma && jj < ma) ? static_cast<double>(Ak[(r0 + i) + (r0 + jj) * LDY]) : 0.0;
+            b[i + 2 * jj] = (i < nb && jj < nb) ? static_cast<double>(Bk[(c0 + i) + (c0 + jj) * LDY]) : 0.0;
+          }
+        double lu[20];
+        const int pack = pair_factor(ma, nb, a, b, smin, lu);
+        double rg[4] = {rv[0], rv[1], rv[2], rv[3]};  // the guarded solve takes its own copy
+        if (sz == 1)
+          eb = pair_solve_guarded<1>(lu, pack, rg, omh, eo, true);
+        else if (sz == 2)
+          eb = pair_solve_guarded<2>(lu, pack, rg, omh, eo, true);
+        else
+          eb = pair_solve_guarded<4>(lu, pack, rg, omh, eo, true);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) rv[u] = rg[u];
+        mode = 2;
+        sh.slow = 1;
       }
     }
+    __syncwarp();
+    if (mode == 1) {
+      Ys[r + c * LDY] = static_cast<T>(z);
+    } else if (mode == 2) {
+      for (int u = 0; u < sz; ++u)
+        Ys[(r0 + (ma == 2 ? (u & 1) : 0)) + (c0 + (ma == 2 ? (u >> 1) : u)) * LDY] = static_cast<T>(rv[u]);
+    }
+    if (mode != 0 && e == 0) {
+      sh.pe[lb] = eb;
+      sh.pr0[lb] = static_cast<short>(r0);
+      sh.pma[lb] = static_cast<short>(ma);
+    }
     __syncthreads();
+    const int lb_lo = max(0, s - (pb - 1));
+    const int lb_hi = min(s, qb - 1);
     int g = 0;
     if (ROBUST && sh.slow) {
       // Phase B (rare): exact tile-wide factor of this step.
@@ -564,7 +729,12 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
         double zs = 0.0, as = 0.0, bs = 0.0;
         for (int lb = lb_lo + lane; lb <= lb_hi; lb += 32) {
           const int kb = pb - 1 - (s - lb);
-          zs = fmax(zs, mul2(bits_to_double(sh.pzm[lb]), emin - sh.pe[lb]));
+          const int r0 = sh.astart[kb], ma = sh.astart[kb + 1] - r0;
+          const int c0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - c0;
+          double zm = 0.0;
+          for (int jj = 0; jj < nb; ++jj)
+            for (int i = 0; i < ma; ++i) zm = fmax(zm, fabs(static_cast<double>(Ys[(r0 + i) + (c0 + jj) * LDY])));
+          zs = fmax(zs, mul2(zm, emin - sh.pe[lb]));
           as = fmax(as, bits_to_double(sh.acolmax[kb]));
           bs = fmax(bs, bits_to_double(sh.bcolmax[lb]));
         }
@@ -572,9 +742,9 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
         as = warp_max(as);
         bs = warp_max(bs);
         if (lane == 0) {
-          unsigned long long u0 = 0;
-          for (int w = 0; w < kThreads / 32; ++w) u0 = sh.wmax[w] > u0 ? sh.wmax[w] : u0;
-          const double U1 = mul2(bits_to_double(u0), emin);
+          unsigned u0 = 0;
+          for (int w = 0; w < NW; ++w) u0 = max(u0, sh.wmax[w]);
+          const double U1 = mul2(from_hi_bound(u0), emin);
           const int z1 = protect_update(U1, as, zs, omh);
           const double zs1 = mul2(zs, z1);
           const double U2 = mul2(U1, z1) + as * zs1;
@@ -589,65 +759,66 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, con
         const int gg = sh.g;
         for (int lb = lb_lo + lane; lb <= lb_hi; lb += 32) {
           const int sc = gg - sh.pe[lb];
-          if (sc != 0)
-            for (int u = 0; u < 4; ++u) sh.zbuf[lb][u] = mul2(sh.zbuf[lb][u], sc);
+          if (sc != 0) {
+            const int kb = pb - 1 - (s - lb);
+            const int r0 = sh.astart[kb], ma = sh.astart[kb + 1] - r0;
+            const int c0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - c0;
+            for (int jj = 0; jj < nb; ++jj)
+              for (int i = 0; i < ma; ++i) {
+                T* yp = &Ys[(r0 + i) + (c0 + jj) * LDY];
+                *yp = mul2(*yp, sc);
+              }
+          }
         }
       }
       __syncthreads();
       g = sh.g;
     }
-    // Phase C: every owned element takes its scale and this step's contributions;
-    // U for the next step is the max over unsolved elements.  The B-side block of
-    // this row (lbs) is the same for all of the thread's columns.
+    // Phase C: every owned unsolved element takes the scale and this step's
+    // contributions: the block solved in its column block below it (A side) and the
+    // block solved in its row block left of it (B side).
     const int lbs = s - dr;
     const bool bs_ok = row_ok && lbs >= 0 && lbs < qb;
     int cs0 = 0, nbs = 0;
-    double zb0 = 0.0, zb1 = 0.0;
+    T zb0 = T(0), zb1 = T(0);
     if (bs_ok) {
       cs0 = sh.bstart[lbs];
       nbs = sh.bstart[lbs + 1] - cs0;
-      zb0 = sh.zbuf[lbs][rr_in];
-      zb1 = (nbs == 2) ? sh.zbuf[lbs][rr_in + ma_r] : 0.0;
+      zb0 = Ys[my_r + cs0 * LDY];
+      if (nbs == 2) zb1 = Ys[my_r + (cs0 + 1) * LDY];
     }
-    // Element arithmetic in T: binary64 for the FP64 solve, binary32 for the FP32
-    // correction solves (only the small systems and the bounds stay binary64).
-    unsigned long long wm = 0;
-    T yv[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) yv[j] = okj[j] ? Ys[my_r + (my_c0 + j * CSTEP) * LDY] : T(0);
+    unsigned wm = 0;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
       const int c = my_c0 + j * CSTEP;
       const int lbc = lbcj[j];
       const int dd = dr + lbc;
-      T y = yv[j];
+      if (!okj[j]) continue;
       if (dd < s) {
-        if (g != 0) y = mul2(y, g);
-      } else if (dd == s) {
-        y = static_cast<T>(sh.zbuf[lbc][rr_in + ma_r * offj[j]]);
-      } else {
-        if (g != 0) y = mul2(y, g);
-        T tb = T(0);
-        if (bs_ok && lbs < lbc) {  // block (kb_r, lbs) left of this column, solved now
-          tb = static_cast<T>(zb0) * Bk[cs0 + c * LDY];
-          if (nbs == 2) tb = fma(static_cast<T>(zb1), Bk[cs0 + 1 + c * LDY], tb);
+        if (g != 0) {  // solved earlier: rescale in place (rare)
+          T* yp = &Ys[my_r + c * LDY];
+          *yp = mul2(*yp, g);
         }
-        if (s >= lbc && s - lbc < dr) {  // block below this row in column block lbc, solved now
-          const int rs0 = sh.pr0[lbc], mas = sh.pma[lbc];
-          y = fma(-Ak[my_r + rs0 * LDY], static_cast<T>(sh.zbuf[lbc][mas * offj[j]]), y);
-          if (mas == 2) y = fma(-Ak[my_r + (rs0 + 1) * LDY], static_cast<T>(sh.zbuf[lbc][1 + 2 * offj[j]]), y);
+      } else if (dd > s) {
+        T y = yv[j];
+        if (g != 0) y = mul2(y, g);
+        const int ia = s - lbc;
+        if (ia >= 0 && ia < dr) {  // block of column block lbc solved now, below this row
+          const int rs0 = sh.pr0[lbc];
+          y = fma(-Ak[my_r + rs0 * LDY], Ys[rs0 + c * LDY], y);
+          if (sh.pma[lbc] == 2) y = fma(-Ak[my_r + (rs0 + 1) * LDY], Ys[rs0 + 1 + c * LDY], y);
         }
-        y -= tb;
-        const unsigned long long bb = abs_bits(static_cast<double>(y));
-        wm = (okj[j] && bb > wm) ? bb : wm;
+        if (bs_ok && lbs < lbc) {  // block of this row block solved now, left of this column
+          y = fma(-zb0, Bk[cs0 + c * LDY], y);
+          if (nbs == 2) y = fma(-zb1, Bk[cs0 + 1 + c * LDY], y);
+        }
+        yv[j] = y;
+        if (dd == s + 1) Ys[my_r + c * LDY] = y;  // right-hand side of the next step
+        if (ROBUST) wm = max(wm, hi_bound(static_cast<double>(y)));
       }
-      yv[j] = y;
     }
-#pragma unroll
-    for (int j = 0; j < NC; ++j)
-      if (okj[j]) Ys[my_r + (my_c0 + j * CSTEP) * LDY] = yv[j];
     if (ROBUST) {
-      wm = warp_max_u64(wm);
+      wm = __reduce_max_sync(0xffffffffu, wm);
       if (lane == 0) sh.wmax[warp] = wm;
     }
     __syncthreads();
@@ -842,49 +1013,66 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
       return (side == 0) ? an[(int64_t)k * I.pmax + prod / I.qmax] : bn[(int64_t)(prod % I.qmax) * I.qmax + l];
     };
     for (int q = 0; q < d && !sh.abort;) {
-      if (tid == 0) {
-        int side, prod, kdim;
-        producer(q, side, prod, kdim);
-        if (!wait_flag(&tflag[prod], ctrl, w.timeout_ns)) {
-          sh.abort = 1;
+      if (tid < 32) {
+        // Warp 0 forms the group: lane u looks at producer q + u; lane 0 waits for
+        // its flag (bounded), the others only test theirs, and the group is the
+        // ready prefix.  Flags, exponents and norms are fetched by all lanes at once.
+        constexpr int G = DagSmem<TT, T>::G;
+        const int lane = tid;
+        int side = 0, prod = 0, kdim = 0;
+        const bool cand = lane < G && q + lane < d;
+        if (cand) producer(q + lane, side, prod, kdim);
+        int okw = 1;
+        if (lane == 0) okw = wait_flag(&tflag[prod], ctrl, w.timeout_ns) ? 1 : 0;
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (!okw) {
+          if (lane == 0) sh.abort = 1;
         } else {
-          int g = 1, ktot = kdim;
-          sh.gside[0] = side;
-          sh.gprod[0] = prod;
-          sh.gk[0] = kdim;
-          sh.goff[0] = 0;
-          while (g < DagSmem<TT, T>::G && q + g < d) {
-            producer(q + g, side, prod, kdim);
-            if (!ld_acquire(&tflag[prod])) break;
-            sh.gside[g] = side;
-            sh.gprod[g] = prod;
-            sh.gk[g] = kdim;
-            sh.goff[g] = ktot;
-            ktot += kdim;
-            ++g;
-          }
+          const bool ready = cand && (lane == 0 || ld_acquire(&tflag[prod]) != 0);
+          const unsigned nr = ~__ballot_sync(0xffffffffu, ready);
+          int g = nr ? __ffs(nr) - 1 : 32;  // the ready prefix (lane 0 is ready)
           int fast = 1;
+          int ep = 0;
+          double pn = 0.0, on = 0.0;
+          if (ROBUST && lane < g) {
+            ep = texp[prod];
+            pn = tnorm[prod];
+            on = opnorm(side, prod);
+          }
           if (ROBUST) {
-            int emx = ub_log2(sh.nb_acc);
-            for (int u = 0; u < g; ++u) {
-              if (texp[sh.gprod[u]] != sh.e_acc) fast = 0;
-              emx = max(emx, ub_log2(opnorm(sh.gside[u], sh.gprod[u])) + ub_log2(tnorm[sh.gprod[u]]));
-            }
-            if (!(fast && emx + 2 <= eo)) {
+            const bool same = __all_sync(0xffffffffu, lane >= g || ep == sh.e_acc);
+            int emx = lane < g ? ub_log2(on) + ub_log2(pn) : -4096;
+            for (int o = 16; o > 0; o >>= 1) emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
+            emx = max(emx, ub_log2(sh.nb_acc));
+            if (!(same && emx + 2 <= eo)) {
               fast = 0;
               g = 1;
-              ktot = sh.gk[0];
             } else {
+              double inc = lane < g ? on * pn : 0.0;  // summed in producer order by lane 0
               double nb = sh.nb_acc;
-              for (int u = 0; u < g; ++u) nb += opnorm(sh.gside[u], sh.gprod[u]) * tnorm[sh.gprod[u]];
-              sh.nb_acc = nb;
+              for (int u = 0; u < g; ++u) nb += __shfl_sync(0xffffffffu, inc, u);
+              if (lane == 0) sh.nb_acc = nb;
             }
           }
-          sh.gn = g;
-          sh.gktot = ktot;
-          sh.gfast = fast;
-          sh.sacc = 0;
-          sh.sop = 0;
+          int ko = lane < g ? kdim : 0;  // exclusive prefix of the K extents
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, ko, o);
+            if (lane >= o) ko += v;
+          }
+          const int ktot = __shfl_sync(0xffffffffu, ko, g - 1);
+          if (lane < g) {
+            sh.gside[lane] = side;
+            sh.gprod[lane] = prod;
+            sh.gk[lane] = kdim;
+            sh.goff[lane] = ko - kdim;
+          }
+          if (lane == 0) {
+            sh.gn = g;
+            sh.gktot = ktot;
+            sh.gfast = fast;
+            sh.sacc = 0;
+            sh.sop = 0;
+          }
         }
       }
       __syncthreads();
@@ -982,7 +1170,7 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
     }
     if (w.prio && tid == 0) atomicAdd(w.smbusy + sm_id(), 1);
     __syncthreads();
-    diag_solve<TT, T, ROBUST>(sh, mt, nt, omega, fact, factp);
+    diag_solve<TT, T, ROBUST>(sh, mt, nt, omega, st->smin, fact, factp);
     if (w.prio && tid == 0) atomicSub(w.smbusy + sm_id(), 1);
 
     // ---- exact norm of the final tile, write back, publish

@@ -4,7 +4,7 @@
 //
 // Work decomposition.  Tile (k,l) of Y (0-based, p x q tiles) depends on tiles
 // (i,l), i > k, through Y_kl -= A_ki Y_il and on tiles (k,j), j < l, through
-// Y_kl -= Y_kj B_jl (the block form of eq. (6)/(7), with the index ranges that an
+// Y_kl -= Y_kj B_jl (the block form of eqs. (6) and (8), with the index ranges that an
 // upper-triangular A and B imply).  Instead of tasks with locks (Sec. 2.2), one
 // CTA owns a tile from start to finish ("owner computes"): it pulls every
 // incoming update in a fixed order (producers sorted by their anti-diagonal,

@@ -238,6 +238,31 @@ int sylv_tri_solve_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, c
                            sylv_result* result);
 
 /*
+ * sylv_residual -- R = C - (A X + X B) to binary64 accuracy, the residual of
+ * eq. (7) with alpha = 1 that the refinement of SYLV_FP32_REFINE evaluates for its
+ * first correction (Sec. 2 defines the equation; the residual is the numerator of
+ * eq. (9) without norms).
+ *
+ * A (m x m, lda) and B (n x n, ldb) are read in their upper quasi-triangular parts
+ * only (upper triangle and first subdiagonal); X (m x n, ldx) and C (m x n, ldc) are
+ * read in full; R (m x n, ldr) is written.  All are device pointers, column-major,
+ * caller-owned; R may not overlap the inputs.  The products run on the bf16 tensor
+ * cores by an error-free splitting of A and B by rows/columns and of X by
+ * columns/rows into seven 8-bit slices each (Ozaki et al. 2012): each product term
+ * is exact to within 2^-54 of (row maximum) x (column maximum), so R is within
+ * about 2^-48 (|A||X| + |X||B|)_ij of the exact value when rows and columns are
+ * balanced (a normwise guarantee otherwise).  The call uses the library's cached
+ * device workspace (about 14 (m^2 + n^2 + 2mn) bytes), runs on
+ * `stream` (null: the default stream) and synchronizes it.  Returns SYLV_OK, a
+ * negative argument index, SYLV_ERR_UNSUPPORTED for m or n beyond the solver's
+ * limit, SYLV_ERR_CUDA, or SYLV_ERR_TIMEOUT if a pipeline wait of the GEMM kernel
+ * ran out (20 s).
+ */
+int sylv_residual(int64_t m, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb,
+                  const double* X, int64_t ldx, const double* C, int64_t ldc, double* R, int64_t ldr,
+                  void* stream);
+
+/*
  * sylv_diag_wait_timeout -- diagnostic of the solver's bounded waits (not in the
  * paper).  Launches one CTA that waits, with the same bounded wait the tile-DAG
  * kernel uses for its ready flags, on a flag that nothing ever sets, and returns

@@ -16,6 +16,9 @@ Contents, each written from the paper (Schwarz & Kjelgaard Mikkelsen 2019):
                       power-of-two shift so that tiny alpha or huge Y cannot
                       under/overflow it.
   * ``smin_of``    -- the pivot floor for near-singular small systems.
+  * ``residual_matrix`` -- R = C - (A X + X B) from its definition (eq. (7) with
+                      alpha = 1) in extended precision, and ``residual_matrix_exact``
+                      in exact rational arithmetic for tiny cases.
 """
 from __future__ import annotations
 
@@ -262,3 +265,34 @@ def kron_grad(A, B, C, W, transa: bool = False, transb: bool = False):
     dA = np.where(quasi_mask(A), dA, 0.0)
     dB = np.where(quasi_mask(B), dB, 0.0)
     return dA, dB, lam.reshape((m, n), order="F"), x.reshape((m, n), order="F")
+
+
+def residual_matrix(A, B, X, C) -> np.ndarray:
+    """R = C - (A X + X B) with A, B read in their quasi-triangular parts (upper triangle
+    and first subdiagonal), evaluated in numpy's long double (x87 extended or binary128,
+    64 or 113 significand bits) and rounded once to binary64 at the end."""
+    ld = np.longdouble
+    Aq = np.triu(np.asarray(A, dtype=np.float64), -1).astype(ld)
+    Bq = np.triu(np.asarray(B, dtype=np.float64), -1).astype(ld)
+    Xl = np.asarray(X, dtype=np.float64).astype(ld)
+    Cl = np.asarray(C, dtype=np.float64).astype(ld)
+    return (Cl - (Aq @ Xl + Xl @ Bq)).astype(np.float64)
+
+
+def residual_matrix_exact(A, B, X, C) -> np.ndarray:
+    """The same residual in exact rational arithmetic (Python fractions), rounded once
+    to binary64: for tiny cases only."""
+    from fractions import Fraction
+    A, B, X, C = (np.asarray(t, dtype=np.float64) for t in (A, B, X, C))
+    m, n = C.shape
+    F = lambda v: Fraction(float(v))  # noqa: E731  (a double is an exact rational)
+    R = np.empty((m, n))
+    for i in range(m):
+        for j in range(n):
+            acc = F(C[i, j])
+            for k in range(max(0, i - 1), m):
+                acc -= F(A[i, k]) * F(X[k, j])
+            for k in range(0, min(n, j + 2)):
+                acc -= F(X[i, k]) * F(B[k, j])
+            R[i, j] = float(acc)
+    return R

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsylv.so")
-SOURCES = ["sylv_api.cu", "sylv_dag_f64.cu", "sylv_dag_f32.cu"]
+SOURCES = ["sylv_api.cu", "sylv_dag_f64.cu", "sylv_dag_f32.cu", "sylv_oz.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -350,6 +350,7 @@ struct SolvePlan {
   Layout L;            // tile workspace (FP64 solve, or the FP32 correction solves)
   size_t off_at, off_bt;  // anti-transposed A, B (FP64) when transposed
   size_t off_a32, off_b32, off_al, off_bl, off_rf, off_r, off_x, off_d, off_slots, off_rs;  // FP32 + refinement
+  size_t off_oz;                                   // tensor-core residual operands
   size_t total;
 };
 
@@ -383,6 +384,8 @@ SolvePlan plan_solve(int64_t m, int64_t n, const Opts& o) {
     off = align_up(off + sizeof(unsigned long long) * (2 + 3 * (o.maxit + 1)));
     P.off_rs = off;
     off = align_up(off + sizeof(RefineState));
+    P.off_oz = off;
+    off = align_up(off + oz_workspace_bytes(m, n));
   }
   P.L = make_layout({P.shape}, off, 0,
                     o.precision == SYLV_FP32_REFINE ? max_ctas_per_sm<float>() : max_ctas_per_sm<double>());
@@ -439,6 +442,17 @@ int enqueue_fp64(const SolvePlan& P, char* ws, const double* A, int64_t lda, con
 //   FP32 pipes, until max|D_k| <= tol max|X| or, once the corrections contract,
 //   max|D_k| * (max|D_k| / max|D_{k-1}|) <= tol max|X| (the size the next
 //   correction would have).
+// The first refinement residual runs on the tensor cores unless SYLV_RESIDUAL=df
+// selects the double-float kernel on the FP32 pipe (kept for comparison).
+bool residual_on_tensor_cores() {
+  static int v = -1;
+  if (v < 0) {
+    const char* env = std::getenv("SYLV_RESIDUAL");
+    v = (env && std::strcmp(env, "df") == 0) ? 0 : 1;
+  }
+  return v != 0;
+}
+
 int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, const double* B, int64_t ldb,
                    double* C, int64_t ldc, const Opts& o, sylv_result* dres) {
   const int64_t m = P.shape.m, n = P.shape.n;
@@ -468,6 +482,9 @@ int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, c
   k_maxabs_quasi<<<grid_for(n * n), 256, 0, s>>>(B, ldb, n, bmax);
   k_split_df<<<grid_for(m * m), 256, 0, s>>>(A, lda, Ah, Al, m, m, m, amax, bmax, 1);
   k_split_df<<<grid_for(n * n), 256, 0, s>>>(B, ldb, Bh, Bl, n, n, n, amax, bmax, 1);
+  OzBuffers ob{};
+  oz_carve(ws + P.off_oz, m, n, &ob);
+  if (residual_on_tensor_cores() && oz_split_ab(ob, A, lda, B, ldb, nullptr, s) != cudaSuccess) return SYLV_ERR_CUDA;
   std::vector<Inst> I = make_insts({P.shape}, L, {Ah}, {m}, {Bh}, {n}, {Rf}, {m}, 1, o.omega);
   k_set_inst<<<1, 1, 0, s>>>(w.inst, I[0]);
   cudaError_t e = run_prep<float>(w, L, 1, std::max(m, n), std::max(P.shape.pmax, P.shape.qmax), s);
@@ -479,15 +496,28 @@ int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, c
     if (it == 0) {
       k_copy_max<<<grid_for(m * n), 256, 0, s>>>(C, ldc, R, m, m, n, rmax);
     } else if (it == 1) {
-      // First residual of the solution: binary64-accurate (double-float products).
-      const unsigned long long* xprev = slots + 2 + 3 * (it - 1) + 2;
-      k_residual_df<<<dim3((m + GT - 1) / GT, (n + GT - 1) / GT), 256, 0, s>>>(
-          Ah, Al, m, Bh, Bl, n, C, ldc, X, m, R, m, m, n, amax, bmax, xprev, rmax, &rs->conv);
+      // First residual of the solution, binary64-accurate: error-free bf16 splitting on
+      // the tensor cores (or double-float products on the FP32 pipe, SYLV_RESIDUAL=df).
+      if (residual_on_tensor_cores()) {
+        if (oz_residual(ob, X, m, C, ldc, R, m, rmax, &w.ctrl->err, o.timeout_ns, &rs->conv, s, true) != cudaSuccess)
+          return SYLV_ERR_CUDA;
+      } else {
+        const unsigned long long* xprev = slots + 2 + 3 * (it - 1) + 2;
+        k_residual_df<<<dim3((m + GT - 1) / GT, (n + GT - 1) / GT), 256, 0, s>>>(
+            Ah, Al, m, Bh, Bl, n, C, ldc, X, m, R, m, m, n, amax, bmax, xprev, rmax, &rs->conv);
+      }
     } else {
-      // Later ones by the recurrence R_k = R_{k-1} - (A D + D B): D is small, binary32 suffices.
-      const unsigned long long* dprev = slots + 2 + 3 * (it - 1) + 1;
-      k_residual_update<<<dim3((m + GT - 1) / GT, (n + GT - 1) / GT), 256, 0, s>>>(
-          Ah, m, Bh, n, Dlast, m, R, m, m, n, amax, bmax, dprev, rmax, &rs->conv);
+      // Later ones by the recurrence R_k = R_{k-1} - (A D + D B): D is small, binary32
+      // accuracy suffices (tensor cores, the binary32 pairs of the splitting; in place).
+      if (residual_on_tensor_cores()) {
+        if (oz_residual(ob, Dlast, m, R, m, R, m, rmax, &w.ctrl->err, o.timeout_ns, &rs->conv, s, false) !=
+            cudaSuccess)
+          return SYLV_ERR_CUDA;
+      } else {
+        const unsigned long long* dprev = slots + 2 + 3 * (it - 1) + 1;
+        k_residual_update<<<dim3((m + GT - 1) / GT, (n + GT - 1) / GT), 256, 0, s>>>(
+            Ah, m, Bh, n, Dlast, m, R, m, m, n, amax, bmax, dprev, rmax, &rs->conv);
+      }
     }
     k_to_float<<<grid_for(m * n), 256, 0, s>>>(R, m, Rf, m, m, n, rmax, nullptr, 0, &rs->conv);
     if (it > 0) {
@@ -605,6 +635,36 @@ int sylv_profile_read(double* dag_ms, int64_t* dag_launches) {
   if (dag_launches) *dag_launches = static_cast<int64_t>(p.ev.size());
   p.ev.clear();
   return rc;
+}
+
+int sylv_residual(int64_t m, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb,
+                  const double* X, int64_t ldx, const double* C, int64_t ldc, double* R, int64_t ldr,
+                  void* stream) {
+  const int rc0 = check_args(m, n, A, lda, B, ldb, C, ldc);
+  if (rc0 == -7 || rc0 == -8) return rc0 - 2;  // C and ldc are arguments 9 and 10 here
+  if (rc0) return rc0;
+  if (m > 0 && n > 0 && !X) return -7;
+  if (ldx < (m > 1 ? m : 1)) return -8;
+  if (m > 0 && n > 0 && !R) return -11;
+  if (ldr < (m > 1 ? m : 1)) return -12;
+  if (m == 0 || n == 0) return SYLV_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t need = align_up(oz_workspace_bytes(m, n)) + kAlign;
+  void* p = nullptr;
+  const int rc = get_workspace(need, &p);
+  if (rc) return rc;
+  char* ws = static_cast<char*>(p);
+  int* err = reinterpret_cast<int*>(ws + align_up(oz_workspace_bytes(m, n)));
+  OzBuffers ob{};
+  oz_carve(ws, m, n, &ob);
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return SYLV_ERR_CUDA;
+  if (oz_split_ab(ob, A, lda, B, ldb, nullptr, s) != cudaSuccess) return SYLV_ERR_CUDA;
+  if (oz_residual(ob, X, ldx, C, ldc, R, ldr, nullptr, err, 20000000000ll, nullptr, s, true) != cudaSuccess)
+    return SYLV_ERR_CUDA;
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SYLV_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SYLV_ERR_CUDA;
+  return herr ? herr : SYLV_OK;
 }
 
 int sylv_diag_wait_timeout(int64_t timeout_ms, void* stream) {

@@ -381,6 +381,29 @@ __device__ __forceinline__ unsigned hi_bound(double v) {
   const unsigned long long b = abs_bits(v);
   return static_cast<unsigned>(b >> 32) + ((b & 0xffffffffull) != 0ull ? 1u : 0u);
 }
+// The same bound for a binary32 value from its bit pattern alone (no FP64 instruction,
+// which would occupy the 1/64-rate FP64 pipe): the double's high word is the float's
+// exponent rebiased and its mantissa's top 20 bits, plus one when the 3 low mantissa
+// bits (the double's low word) are nonzero.  Subnormal floats are bounded by 2^-126,
+// infinities and NaNs map to the infinite bound.
+__device__ __forceinline__ unsigned hi_bound(float v) {
+  const unsigned b = __float_as_uint(v) & 0x7fffffffu;
+  const unsigned e = b >> 23, m = b & 0x7fffffu;
+  if (e == 0) return m ? ((1023u - 126u) << 20) : 0u;
+  if (e == 255) return 0x7ff00000u;
+  return ((e + 896u) << 20) + (m >> 3) + ((m & 7u) ? 1u : 0u);
+}
+// Exact binary32 -> binary64 conversion by rebiasing the bit pattern (normal values;
+// zeros, subnormals, infinities and NaNs take the conversion instruction).
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0 || e == 255) return static_cast<double>(v);
+  return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(b & 0x80000000u) << 32) |
+                                                     (static_cast<unsigned long long>(e + 896u) << 52) |
+                                                     (static_cast<unsigned long long>(b & 0x7fffffu) << 29)));
+}
 __device__ __forceinline__ double from_hi_bound(unsigned h) {
   return bits_to_double(static_cast<unsigned long long>(h) << 32);
 }
@@ -601,7 +624,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
     unsigned um = 0;
 #pragma unroll
     for (int j = 0; j < NC; ++j)
-      if (okj[j]) um = max(um, hi_bound(static_cast<double>(yv[j])));
+      if (okj[j]) um = max(um, hi_bound(yv[j]));
     um = __reduce_max_sync(0xffffffffu, um);
     if (lane == 0) sh.wmax[warp] = um;
   }
@@ -623,7 +646,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
         if (okj[j]) {
           yv[j] = mul2(yv[j], z);
           Ys[my_r + (my_c0 + j * CSTEP) * LDY] = yv[j];
-          um = max(um, hi_bound(static_cast<double>(yv[j])));
+          um = max(um, hi_bound(yv[j]));
         }
       if (tid == 0) sh.e_diag = z;
       um = __reduce_max_sync(0xffffffffu, um);
@@ -660,8 +683,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
       unsigned long long rmb = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        rv[u] = (u < sz) ? static_cast<double>(Ys[(r0 + (ma == 2 ? (u & 1) : 0)) + (c0 + (ma == 2 ? (u >> 1) : u)) * LDY])
-                         : 0.0;
+        rv[u] = (u < sz) ? to_f64(Ys[(r0 + (ma == 2 ? (u & 1) : 0)) + (c0 + (ma == 2 ? (u >> 1) : u)) * LDY]) : 0.0;
         const unsigned long long bv = abs_bits(rv[u]);
         rmb = bv > rmb ? bv : rmb;
       }
@@ -814,7 +836,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
         }
         yv[j] = y;
         if (dd == s + 1) Ys[my_r + c * LDY] = y;  // right-hand side of the next step
-        if (ROBUST) wm = max(wm, hi_bound(static_cast<double>(y)));
+        if (ROBUST) wm = max(wm, hi_bound(y));
       }
     }
     if (ROBUST) {

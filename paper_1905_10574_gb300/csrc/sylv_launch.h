@@ -9,11 +9,10 @@
 namespace sylv {
 
 // CTAs per SM the tile kernel may use (and the workspace reserves factor stores for):
-// 2 for the FP64 kernel (FP64-pipe bound), 4 for the FP32 correction solves
-// (latency bound).
+// both instantiations hold 2 per SM (registers and shared memory).
 template <typename T>
 constexpr int max_ctas_per_sm() {
-  return sizeof(T) == 4 ? 4 : 2;
+  return 2;
 }
 
 // Launch the persistent DAG kernel for tile capacity tt (32 or 64) on `stream`.
@@ -27,5 +26,25 @@ void profile_end(cudaStream_t stream);
 
 // Resident CTAs per SM of an instantiation (for reporting and grid sizing).
 int dag_ctas_per_sm_f64(int tt, bool robust);
+
+// Tensor-core residual R = C - (A X + X B) of the refinement (sylv_oz.cuh): operand
+// slices in four packed arrays (A; X by columns; X by rows; B by columns) with their
+// per-row exponents.
+struct OzBuffers {
+  void* p[4];
+  int* e[4];
+  int64_t m, n;
+};
+size_t oz_workspace_bytes(int64_t m, int64_t n);
+void oz_carve(char* base, int64_t m, int64_t n, OzBuffers* b);
+// Slices of A and B (once per solve).
+cudaError_t oz_split_ab(const OzBuffers& b, const double* A, int64_t lda, const double* B, int64_t ldb,
+                        const int* skip, cudaStream_t s);
+// Slices of X, then R = C - (A X + X B) and max |R| (into rmax); a timeout sets *err.
+// binary64: all slice pairs of the binary64-accurate residual; otherwise the pairs of
+// a binary32-accurate product.  R may equal C (in place).
+cudaError_t oz_residual(const OzBuffers& b, const double* X, int64_t ldx, const double* C, int64_t ldc, double* R,
+                        int64_t ldr, unsigned long long* rmax, int* err, long long timeout_ns, const int* skip,
+                        cudaStream_t s, bool binary64);
 
 }  // namespace sylv

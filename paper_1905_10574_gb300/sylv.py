@@ -82,6 +82,7 @@ SIGNATURES = {
     "sylv_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sylv_version": (ctypes.c_char_p, []),
     "sylv_diag_wait_timeout": (ctypes.c_int, [_i64, _vp]),
+    "sylv_residual": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _vp]),
     "sylv_tri_solve_noalloc": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _i64, _vp,
                                               ctypes.POINTER(sylv_result)]),
     "sylv_tri_solve_backward_batched": (ctypes.c_int, [_i32, _P64, _P64, _PP, _P64, _PP, _P64, _PP, _P64, _P64, _PP,
@@ -163,6 +164,12 @@ def sylv_tri_solve_noalloc(m, n, A, lda, B, ldb, C, ldc, tile=0, stream=None):
     res = sylv_result()
     rc = load().sylv_tri_solve_noalloc(m, n, A, lda, B, ldb, C, ldc, tile, stream, ctypes.byref(res))
     return rc, res
+
+
+def sylv_residual(m, n, A, lda, B, ldb, X, ldx, C, ldc, R, ldr, stream=None) -> int:
+    """Device pointers (ints).  R <- C - (A X + X B) to binary64 accuracy (tensor cores);
+    synchronizes the stream and returns the status code."""
+    return load().sylv_residual(m, n, A, lda, B, ldb, X, ldx, C, ldc, R, ldr, stream)
 
 
 def sylv_tri_solve_ex(m, n, A, lda, B, ldb, C, ldc, opts: sylv_opts | None = None, result=None):
@@ -333,6 +340,21 @@ def solve(A, B, C, *, transa=False, transb=False, precision="fp64", tile=0, omeg
     if check and (rc >= 100 or rc < 0):
         raise SylvError(rc, "sylv_tri_solve_ex")
     return Y, Result(**res.as_dict())
+
+
+def residual(A, B, X, C, *, stream=None):
+    """R = C - (A X + X B) for float64 CUDA tensors (A, B read in their quasi-triangular
+    parts), computed by sylv_residual; returns a new column-major tensor."""
+    torch = _torch()
+    A, B, X, C = (fortran(t) for t in (A, B, X, C))
+    m, n = C.shape
+    R = empty_fortran(m, n, C.device, torch.float64)
+    s = stream if stream is not None else torch.cuda.current_stream(C.device).cuda_stream
+    rc = sylv_residual(m, n, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), X.data_ptr(), _ld(X), C.data_ptr(), _ld(C),
+                       R.data_ptr(), _ld(R), s)
+    if rc != 0:
+        raise SylvError(rc, "sylv_residual")
+    return R
 
 
 def batch_solve(As, Bs, Cs, *, transa=False, transb=False, tile=0, precision="fp64", timeout_ms=0):

@@ -299,3 +299,32 @@ def test_kron_grad_matches_finite_differences(orc, transa, transb):
         E[i, j] = h
         fd = (loss(A, B, C + E) - loss(A, B, C - E)) / (2 * h)
         assert abs(dC[i, j] - fd) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_residual_matrix_against_exact_rationals(orc):
+    """The extended-precision residual R = C - (A X + X B) agrees with exact rational
+    arithmetic (independent evaluation: fractions, explicit quasi-triangular index
+    ranges) on a tiny case with 2x2 blocks and a wide magnitude range."""
+    rng = np.random.default_rng(5)
+    m, n = 9, 7
+    A = orc.quasi_tri(np.triu(rng.uniform(-1, 1, (m, m)), -1))
+    A[3, 2] = 0.75
+    B = orc.quasi_tri(np.triu(rng.uniform(-1, 1, (n, n)), -1))
+    B[5, 4] = -1.25
+    X = rng.uniform(-1, 1, (m, n)) * np.exp2(rng.integers(-30, 30, (m, n)))
+    C = rng.uniform(-1, 1, (m, n))
+    R = orc.residual_matrix(A, B, X, C)
+    Rx = orc.residual_matrix_exact(A, B, X, C)
+    scale = np.abs(np.triu(A, -1)) @ np.abs(X) + np.abs(X) @ np.abs(np.triu(B, -1)) + np.abs(C)
+    assert np.all(np.abs(R - Rx) <= 2.0 ** -52 * np.abs(Rx) + 2.0 ** -60 * scale)
+
+
+def test_residual_matrix_diagonal_closed_form(orc):
+    """Diagonal A, B: R_ij = C_ij - (a_i + b_j) X_ij."""
+    rng = np.random.default_rng(6)
+    a, b = rng.uniform(1, 5, 6), rng.uniform(1, 5, 4)
+    X, C = rng.uniform(-1, 1, (6, 4)), rng.uniform(-1, 1, (6, 4))
+    R = orc.residual_matrix(np.diag(a), np.diag(b), X, C)
+    ref = C - (a[:, None] + b[None, :]) * X  # three roundings in binary64
+    bound = 4 * 2.0 ** -53 * (np.abs(a[:, None] + b[None, :]) * np.abs(X) + np.abs(C))
+    assert np.all(np.abs(R - ref) <= bound)

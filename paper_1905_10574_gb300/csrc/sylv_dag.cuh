@@ -659,6 +659,51 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
   int local_scale_events = 0;
   const int nsteps = pb + qb - 1;
   for (int s = 0; s < nsteps; ++s) {
+    // Phase C's coefficients do not depend on this step's solutions: the binary32
+    // tile-32 kernel (latency bound, with registers to spare) fetches them now, while
+    // Phase A runs; the others read them after the barrier.  The block solved in
+    // column block lbc lies at block row pb-1-(s-lbc); the one solved in this row's
+    // block row at column block s-dr.
+    constexpr bool kPre = sizeof(T) == 4 && TT <= 32;
+    constexpr int NP = kPre ? NC : 1;
+    const int lbs = s - dr;
+    const bool bs_ok = row_ok && lbs >= 0 && lbs < qb;
+    int cs0 = 0, nbs = 0;
+    if (bs_ok) {
+      cs0 = sh.bstart[lbs];
+      nbs = sh.bstart[lbs + 1] - cs0;
+    }
+    T ca0[NP], ca1[NP], cb0[NP], cb1[NP];
+    int rsj[NP];
+    unsigned amask = 0, a2mask = 0, bmask = 0;  // per slot: A side present / 2 rows; B side present
+    if constexpr (kPre) {
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const int c = my_c0 + j * CSTEP;
+        const int lbc = lbcj[j];
+        const int ia = s - lbc;
+        ca0[j] = ca1[j] = cb0[j] = cb1[j] = T(0);
+        rsj[j] = 0;
+        if (okj[j] && dr + lbc > s) {
+          if (ia >= 0 && ia < dr) {
+            const int kbs = pb - 1 - ia;
+            const int rs0 = sh.astart[kbs];
+            rsj[j] = rs0;
+            amask |= 1u << j;
+            ca0[j] = Ak[my_r + rs0 * LDY];
+            if (sh.astart[kbs + 1] - rs0 == 2) {
+              a2mask |= 1u << j;
+              ca1[j] = Ak[my_r + (rs0 + 1) * LDY];
+            }
+          }
+          if (bs_ok && lbs < lbc) {
+            bmask |= 1u << j;
+            cb0[j] = Bk[cs0 + c * LDY];
+            if (nbs == 2) cb1[j] = Bk[cs0 + 1 + c * LDY];
+          }
+        }
+      }
+    }
     // Phase A: the step's elements, one thread each.  All reads of the step's
     // right-hand sides come before any write of a solution (__syncwarp).
     const int e0 = sh.sstart[s];
@@ -799,13 +844,8 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
     // Phase C: every owned unsolved element takes the scale and this step's
     // contributions: the block solved in its column block below it (A side) and the
     // block solved in its row block left of it (B side).
-    const int lbs = s - dr;
-    const bool bs_ok = row_ok && lbs >= 0 && lbs < qb;
-    int cs0 = 0, nbs = 0;
     T zb0 = T(0), zb1 = T(0);
     if (bs_ok) {
-      cs0 = sh.bstart[lbs];
-      nbs = sh.bstart[lbs + 1] - cs0;
       zb0 = Ys[my_r + cs0 * LDY];
       if (nbs == 2) zb1 = Ys[my_r + (cs0 + 1) * LDY];
     }
@@ -824,15 +864,26 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
       } else if (dd > s) {
         T y = yv[j];
         if (g != 0) y = mul2(y, g);
-        const int ia = s - lbc;
-        if (ia >= 0 && ia < dr) {  // block of column block lbc solved now, below this row
-          const int rs0 = sh.pr0[lbc];
-          y = fma(-Ak[my_r + rs0 * LDY], Ys[rs0 + c * LDY], y);
-          if (sh.pma[lbc] == 2) y = fma(-Ak[my_r + (rs0 + 1) * LDY], Ys[rs0 + 1 + c * LDY], y);
-        }
-        if (bs_ok && lbs < lbc) {  // block of this row block solved now, left of this column
-          y = fma(-zb0, Bk[cs0 + c * LDY], y);
-          if (nbs == 2) y = fma(-zb1, Bk[cs0 + 1 + c * LDY], y);
+        if constexpr (kPre) {
+          if (amask & (1u << j)) {  // block of column block lbc solved now, below this row
+            y = fma(-ca0[j], Ys[rsj[j] + c * LDY], y);
+            if (a2mask & (1u << j)) y = fma(-ca1[j], Ys[rsj[j] + 1 + c * LDY], y);
+          }
+          if (bmask & (1u << j)) {  // block of this row block solved now, left of this column
+            y = fma(-zb0, cb0[j], y);
+            if (nbs == 2) y = fma(-zb1, cb1[j], y);
+          }
+        } else {
+          const int ia = s - lbc;
+          if (ia >= 0 && ia < dr) {  // block of column block lbc solved now, below this row
+            const int rs0 = sh.pr0[lbc];
+            y = fma(-Ak[my_r + rs0 * LDY], Ys[rs0 + c * LDY], y);
+            if (sh.pma[lbc] == 2) y = fma(-Ak[my_r + (rs0 + 1) * LDY], Ys[rs0 + 1 + c * LDY], y);
+          }
+          if (bs_ok && lbs < lbc) {  // block of this row block solved now, left of this column
+            y = fma(-zb0, Bk[cs0 + c * LDY], y);
+            if (nbs == 2) y = fma(-zb1, Bk[cs0 + 1 + c * LDY], y);
+          }
         }
         yv[j] = y;
         if (dd == s + 1) Ys[my_r + c * LDY] = y;  // right-hand side of the next step
@@ -881,17 +932,40 @@ __device__ __forceinline__ void stage_right(T* R, const T* P, int64_t ld, int kd
 }
 
 // acc -= L * R over kk < kdim; thread (tx, ty) owns rows tx*MR.., columns ty*NR..
+// Operands are read two elements at a time (rbase, cbase and LDG are even, so each
+// pair is 8-byte aligned in binary32 and 16-byte aligned in binary64): half the
+// shared-memory load instructions of scalar reads, which bound this loop.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
 template <int TT, typename T, int MR, int NR>
 __device__ __forceinline__ void gemm_sub(T (&acc)[MR][NR], const T* L, const T* R, int kdim, int rbase,
                                          int cbase) {
   constexpr int LDG = DagSmem<TT, T>::LDG;
+  static_assert(MR % 2 == 0 && NR % 2 == 0 && LDG % 2 == 0, "paired operand reads");
+  using V2 = typename Vec2<T>::type;
 #pragma unroll 4
   for (int kk = 0; kk < kdim; ++kk) {
     T a[MR], b[NR];
 #pragma unroll
-    for (int i = 0; i < MR; ++i) a[i] = L[kk * LDG + rbase + i];
+    for (int i = 0; i < MR; i += 2) {
+      const V2 v = *reinterpret_cast<const V2*>(&L[kk * LDG + rbase + i]);
+      a[i] = v.x;
+      a[i + 1] = v.y;
+    }
 #pragma unroll
-    for (int j = 0; j < NR; ++j) b[j] = R[kk * LDG + cbase + j];
+    for (int j = 0; j < NR; j += 2) {
+      const V2 v = *reinterpret_cast<const V2*>(&R[kk * LDG + cbase + j]);
+      b[j] = v.x;
+      b[j + 1] = v.y;
+    }
 #pragma unroll
     for (int i = 0; i < MR; ++i)
 #pragma unroll
@@ -1100,18 +1174,79 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
       __syncthreads();
       if (sh.abort) break;
       const int g = sh.gn;
-      for (int u = 0; u < g; ++u) {
-        const int side = sh.gside[u], prod = sh.gprod[u], kdim = sh.gk[u];
-        T* Lu = sh.L + sh.goff[u] * DagSmem<TT, T>::LDG;
-        T* Ru = sh.R + sh.goff[u] * DagSmem<TT, T>::LDG;
-        if (side == 0) {
-          const int i = prod / I.qmax;
-          stage_left<TT, T, false>(Lu, A + r0 + (int64_t)rb[i] * I.lda, I.lda, mt, kdim);
-          stage_right<TT, T, true>(Ru, C + rb[i] + (int64_t)c0 * I.ldc, I.ldc, kdim, nt);
-        } else {
-          const int j = prod % I.qmax;
-          stage_left<TT, T, true>(Lu, C + r0 + (int64_t)cb[j] * I.ldc, I.ldc, mt, kdim);
-          stage_right<TT, T, false>(Ru, B + cb[j] + (int64_t)c0 * I.ldb, I.ldb, kdim, nt);
+      if constexpr (TT == 32 && sizeof(T) == 8) {
+        // All of the group's global loads are issued before any shared-memory store
+        // (through generic pointers the compiler cannot reorder them), so the group
+        // costs one memory round trip instead of one per operand tile.  (The binary32
+        // kernel has no registers to spare for it.)
+        constexpr int GM = DagSmem<TT, T>::G;
+        constexpr int PT = TT * TT / kThreads;  // elements per thread of one operand tile
+        constexpr int LDG = DagSmem<TT, T>::LDG;
+        T vl[GM][PT], vr[GM][PT];
+#pragma unroll
+        for (int u = 0; u < GM; ++u) {
+          if (u < g) {
+            const int side = sh.gside[u], prod = sh.gprod[u], kdim = sh.gk[u];
+            const T* PL;
+            const T* PR;
+            int64_t ldl, ldr;
+            if (side == 0) {  // A_ki (rows of tile k) and Y_il
+              const int i = prod / I.qmax;
+              PL = A + r0 + (int64_t)rb[i] * I.lda;
+              ldl = I.lda;
+              PR = C + rb[i] + (int64_t)c0 * I.ldc;
+              ldr = I.ldc;
+            } else {  // Y_kj and B_jl
+              const int j = prod % I.qmax;
+              PL = C + r0 + (int64_t)cb[j] * I.ldc;
+              ldl = I.ldc;
+              PR = B + cb[j] + (int64_t)c0 * I.ldb;
+              ldr = I.ldb;
+            }
+#pragma unroll
+            for (int e = 0; e < PT; ++e) {
+              const int idx = tid + e * kThreads;
+              const int r = idx % TT, kk = idx / TT;
+              T v = T(0);
+              if (r < mt && kk < kdim) v = side ? __ldcg(PL + r + kk * ldl) : __ldg(PL + r + kk * ldl);
+              vl[u][e] = v;
+              const int kk2 = idx % kdim, c = idx / kdim;
+              T v2 = T(0);
+              if (c < nt && idx < TT * kdim) v2 = side ? __ldg(PR + kk2 + c * ldr) : __ldcg(PR + kk2 + c * ldr);
+              vr[u][e] = v2;
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < GM; ++u) {
+          if (u < g) {
+            const int kdim = sh.gk[u];
+            T* Lu = sh.L + sh.goff[u] * LDG;
+            T* Ru = sh.R + sh.goff[u] * LDG;
+#pragma unroll
+            for (int e = 0; e < PT; ++e) {
+              const int idx = tid + e * kThreads;
+              if (idx < TT * kdim) {
+                Lu[(idx / TT) * LDG + idx % TT] = vl[u][e];
+                Ru[(idx % kdim) * LDG + idx / kdim] = vr[u][e];
+              }
+            }
+          }
+        }
+      } else {
+        for (int u = 0; u < g; ++u) {
+          const int side = sh.gside[u], prod = sh.gprod[u], kdim = sh.gk[u];
+          T* Lu = sh.L + sh.goff[u] * DagSmem<TT, T>::LDG;
+          T* Ru = sh.R + sh.goff[u] * DagSmem<TT, T>::LDG;
+          if (side == 0) {
+            const int i = prod / I.qmax;
+            stage_left<TT, T, false>(Lu, A + r0 + (int64_t)rb[i] * I.lda, I.lda, mt, kdim);
+            stage_right<TT, T, true>(Ru, C + rb[i] + (int64_t)c0 * I.ldc, I.ldc, kdim, nt);
+          } else {
+            const int j = prod % I.qmax;
+            stage_left<TT, T, true>(Lu, C + r0 + (int64_t)cb[j] * I.ldc, I.ldc, mt, kdim);
+            stage_right<TT, T, false>(Ru, B + cb[j] + (int64_t)c0 * I.ldb, I.ldb, kdim, nt);
+          }
         }
       }
       if (w.prio && tid == 0) {

@@ -303,7 +303,7 @@ def run_ours(args):
                                       "1184 GFLOP/s at ~1.98 GHz"},
             "e2e": {"value": ws * flops_2(m, n) / (e2e_ms / 1000) / 1e9, "unit": "GFLOP/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 9 * args.steps,
+            "gpu_launches": 10 * args.steps,  # per solve: set_inst, scan, norms, 3 level kernels, pack, DAG, consistency, results
             "clocks": clocks,
             "result": {"info": res.info, "log2scale": res.log2scale, "scale_events": res.scale_events,
                        "ok": ok},

@@ -85,6 +85,9 @@ struct Layout {
   // zero-initialised region [zero_lo, zero_hi)
   size_t ctrl, st, lvl_cnt, lvl_cur, tflag, smbusy, zero_lo, zero_hi;
   size_t lvl_off, inst, res, tasks, ibuf, texp, tnorm, dbuf, fact, factp;
+  size_t pack;       // packed operand tiles (pack_elem != 0)
+  int pack_elem;     // element size of the packed tiles, 0: no packing
+  int64_t pack_slot; // bytes per packed tile
   size_t total;
   int ncta;          // CTAs the DAG kernel may run (factor-store slots)
   int64_t fstride;   // doubles per CTA slot
@@ -105,9 +108,9 @@ int tt_of(const Seq& sh) {
 }
 
 template <class Seq>
-Layout make_layout_seq(const Seq& sh, size_t base, int cta_cap, int per_sm = 2) {
+Layout make_layout_seq(const Seq& sh, size_t base, int cta_cap, int per_sm = 2, int pack_elem = 0) {
   Layout L{};
-  int64_t tiles = 0, ib = 0, db = 0;
+  int64_t tiles = 0, ib = 0, db = 0, slots = 0;
   int nlev = 1, mt = 0;
   for (const Shape& s : sh) {
     tiles += static_cast<int64_t>(s.pmax) * s.qmax;
@@ -115,6 +118,7 @@ Layout make_layout_seq(const Seq& sh, size_t base, int cta_cap, int per_sm = 2) 
     db += static_cast<int64_t>(s.pmax) * s.pmax + static_cast<int64_t>(s.qmax) * s.qmax;
     nlev = std::max(nlev, s.pmax + s.qmax);
     mt = std::max(mt, s.pmax * s.qmax);
+    slots += pack_slots(s.pmax, s.qmax);
   }
   const size_t count = sh.size();
   size_t o = align_up(base);
@@ -158,6 +162,10 @@ Layout make_layout_seq(const Seq& sh, size_t base, int cta_cap, int per_sm = 2) 
   o = align_up(o + static_cast<size_t>(L.ncta) * L.fstride * sizeof(double));
   L.factp = o;
   o = align_up(o + static_cast<size_t>(L.ncta) * tt * tt * sizeof(int32_t));
+  L.pack_elem = pack_elem;
+  L.pack_slot = static_cast<int64_t>(tt) * (tt + 2) * pack_elem;
+  L.pack = o;
+  if (pack_elem) o = align_up(o + static_cast<size_t>(slots) * L.pack_slot);
   L.total = o;
   L.nlevels_max = nlev;
   L.max_tiles = mt;
@@ -165,8 +173,8 @@ Layout make_layout_seq(const Seq& sh, size_t base, int cta_cap, int per_sm = 2) 
   return L;
 }
 
-Layout make_layout(const std::vector<Shape>& sh, size_t base, int cta_cap = 0, int per_sm = 2) {
-  return make_layout_seq(sh, base, cta_cap, per_sm);
+Layout make_layout(const std::vector<Shape>& sh, size_t base, int cta_cap = 0, int per_sm = 2, int pack_elem = 0) {
+  return make_layout_seq(sh, base, cta_cap, per_sm, pack_elem);
 }
 
 // Descriptors for each equation (host copies) given the layout.
@@ -175,7 +183,7 @@ std::vector<Inst> make_insts(const std::vector<Shape>& sh, const Layout& L, cons
                              const std::vector<int64_t>& ldb, const std::vector<void*>& C,
                              const std::vector<int64_t>& ldc, int robust, double omega) {
   std::vector<Inst> v(sh.size());
-  int64_t tile = 0, ib = 0, db = 0;
+  int64_t tile = 0, ib = 0, db = 0, pk = 0;
   for (size_t i = 0; i < sh.size(); ++i) {
     Inst& I = v[i];
     I.m = sh[i].m;
@@ -199,6 +207,8 @@ std::vector<Inst> make_insts(const std::vector<Shape>& sh, const Layout& L, cons
     I.bn = db + static_cast<int64_t>(sh[i].pmax) * sh[i].pmax;
     db += static_cast<int64_t>(sh[i].pmax) * sh[i].pmax + static_cast<int64_t>(sh[i].qmax) * sh[i].qmax;
     I.omega = omega;
+    I.pk = pk;
+    pk += pack_slots(sh[i].pmax, sh[i].qmax);
   }
   (void)L;
   return v;
@@ -229,6 +239,8 @@ Work make_work(char* ws, const Layout& L, int count, int64_t timeout_ns) {
   w.skip = nullptr;
   w.timeout_ns = timeout_ns;
   w.max_tiles = L.max_tiles;
+  w.pack = L.pack_elem ? ws + L.pack : nullptr;
+  w.pack_slot = L.pack_slot;
   return w;
 }
 
@@ -275,7 +287,12 @@ cudaError_t run_prep(const Work& w, const Layout& L, int count, int64_t maxN, in
   k_level_count<<<count, 256, 0, s>>>(w);
   k_level_scan<<<1, 32, 0, s>>>(w);
   k_level_scatter<<<count, 256, 0, s>>>(w);
-  (void)L;
+  if (w.pack) {
+    const int tt = static_cast<int>(L.pack_slot / L.pack_elem) >= 64 * 66 ? 64 : 32;
+    const int64_t per = static_cast<int64_t>(pmax_all) * pmax_all * 2;
+    const int gy = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(per / 4 + 1, 8LL * sm_count() / std::max(count, 1) + 1)));
+    k_pack<T><<<dim3(count, gy), 256, 0, s>>>(w, tt);
+  }
   return cudaGetLastError();
 }
 
@@ -388,7 +405,8 @@ SolvePlan plan_solve(int64_t m, int64_t n, const Opts& o) {
     off = align_up(off + oz_workspace_bytes(m, n));
   }
   P.L = make_layout({P.shape}, off, 0,
-                    o.precision == SYLV_FP32_REFINE ? max_ctas_per_sm<float>() : max_ctas_per_sm<double>());
+                    o.precision == SYLV_FP32_REFINE ? max_ctas_per_sm<float>() : max_ctas_per_sm<double>(),
+                    o.precision == SYLV_FP32_REFINE ? static_cast<int>(sizeof(float)) : static_cast<int>(sizeof(double)));
   P.total = P.L.total;
   return P;
 }
@@ -805,7 +823,7 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
   P->precision = o.precision;
   P->transa = o.transa;
   P->transb = o.transb;
-  P->L = make_layout(sh, 0);
+  P->L = make_layout(sh, 0, 0, 2, static_cast<int>(sizeof(double)));
   P->maxN = maxN;
   P->pmax_all = pmax_all;
   if (count > 0) {

@@ -62,6 +62,7 @@ struct DagSmem {
   short rowblk[TT], colblk[TT];       // block index of every row / column of the tile
   short astart[TT + 1], bstart[TT + 1];
   unsigned long long umax;
+  unsigned long long stage_bar;        // mbarrier of the bulk-copy staging (packed tiles)
   double nb_acc;
   int task, abort, e_acc, sacc, sop, g, e_diag, pb, qb, nscale, flags, slow;
 };
@@ -82,6 +83,34 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     v = u > v ? u : v;
   }
   return v;
+}
+
+// Shared-memory address, bulk copy global -> shared completing on an mbarrier, and a
+// bounded wait on an mbarrier phase (false on timeout or when a CTA recorded an error).
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+template <typename T>
+__device__ __forceinline__ void bulk_copy_g2s(T* dst, const char* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity, const Ctrl* ctrl,
+                                                  long long timeout_ns) {
+  const unsigned long long t0 = global_ns();
+  for (int it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 63) == 63) {
+      if (ld_volatile(&ctrl->err)) return false;
+      if (static_cast<long long>(global_ns() - t0) > timeout_ns) return false;
+    }
+  }
 }
 
 // ProtectUpdate with an integer fast path: when c + t x < 2^e_omega is evident from
@@ -985,6 +1014,15 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
   const int rbase = tx * MR, cbase = ty * NR;
   Ctrl* ctrl = w.ctrl;
   if (w.skip && ld_volatile(w.skip)) return;
+  const bool packed = w.pack != nullptr;
+  uint32_t stage_phase = 0;
+  if (packed) {
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sh.stage_bar)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+  }
 
   for (;;) {
     if (tid == 0) {
@@ -1155,12 +1193,41 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
             const int v = __shfl_up_sync(0xffffffffu, ko, o);
             if (lane >= o) ko += v;
           }
-          const int ktot = __shfl_sync(0xffffffffu, ko, g - 1);
+          // Packed tiles are zero-padded to TT rows of k and staged in fixed slots.
+          const int ktot = packed ? g * TT : __shfl_sync(0xffffffffu, ko, g - 1);
           if (lane < g) {
             sh.gside[lane] = side;
             sh.gprod[lane] = prod;
             sh.gk[lane] = kdim;
-            sh.goff[lane] = ko - kdim;
+            sh.goff[lane] = packed ? lane * TT : ko - kdim;
+          }
+          if (packed) {
+            // One thread stages the whole group by bulk copies (async proxy) after
+            // every lane's flag acquire (__syncwarp orders them before the copies).
+            __syncwarp();
+            if (lane == 0) {
+              asm volatile("fence.proxy.async.global;" ::: "memory");
+              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the last GEMM's reads
+              const uint32_t bytes = static_cast<uint32_t>(w.pack_slot);
+              const uint32_t bar = smem_addr(&sh.stage_bar);
+              asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2u * g * bytes)
+                           : "memory");
+              for (int u = 0; u < g; ++u) {
+                const int pu = sh.gprod[u];
+                int64_t sl, sr;
+                if (sh.gside[u] == 0) {  // A_ki and Y_il
+                  const int i = pu / I.qmax;
+                  sl = pack_a(I, k, i);
+                  sr = pack_yr(I, i, l);
+                } else {  // Y_kj and B_jl
+                  const int j = pu % I.qmax;
+                  sl = pack_yl(I, k, j);
+                  sr = pack_b(I, j, l);
+                }
+                bulk_copy_g2s(sh.L + u * TT * DagSmem<TT, T>::LDG, w.pack + sl * w.pack_slot, bytes, bar);
+                bulk_copy_g2s(sh.R + u * TT * DagSmem<TT, T>::LDG, w.pack + sr * w.pack_slot, bytes, bar);
+              }
+            }
           }
           if (lane == 0) {
             sh.gn = g;
@@ -1174,7 +1241,15 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
       __syncthreads();
       if (sh.abort) break;
       const int g = sh.gn;
-      if constexpr (TT == 32 && sizeof(T) == 8) {
+      if (packed) {
+        const bool ok = mbar_wait_bounded(&sh.stage_bar, stage_phase, ctrl, w.timeout_ns);
+        stage_phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+          if (tid == 0) atomicCAS(&ctrl->err, 0, SYLV_ERR_TIMEOUT);
+          sh.abort = 1;
+          break;
+        }
+      } else if constexpr (TT == 32 && sizeof(T) == 8) {
         // All of the group's global loads are issued before any shared-memory store
         // (through generic pointers the compiler cannot reorder them), so the group
         // costs one memory round trip instead of one per operand tile.  (The binary32
@@ -1341,6 +1416,21 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
     for (int idx = tid; idx < mt * nt; idx += kThreads) {
       const int r = idx % mt, c = idx / mt;
       C[(r0 + r) + (int64_t)(c0 + c) * I.ldc] = sh.Y[r + c * LDY];
+    }
+    if (packed) {
+      // The tile as a left operand (column-major, YL[c][r]) and as a right operand
+      // (row-major, YR[r][c]), zero-padded, for its consumers' bulk copies; the proxy
+      // fence orders these generic stores before the async-proxy reads that follow
+      // the flag.
+      constexpr int LDG = DagSmem<TT, T>::LDG;
+      T* yl = reinterpret_cast<T*>(w.pack + pack_yl(I, k, l) * w.pack_slot);
+      T* yr = reinterpret_cast<T*>(w.pack + pack_yr(I, k, l) * w.pack_slot);
+      for (int idx = tid; idx < TT * LDG; idx += kThreads) {
+        const int kk = idx / LDG, x = idx % LDG;
+        yl[idx] = (x < mt && kk < nt) ? sh.Y[x + kk * LDY] : T(0);
+        yr[idx] = (x < nt && kk < mt) ? sh.Y[kk + x * LDY] : T(0);
+      }
+      asm volatile("fence.proxy.async.global;" ::: "memory");
     }
     __syncthreads();
     if (tid == 0) {

@@ -34,6 +34,7 @@ struct Inst {
   int64_t tile;        // offset (elements) of this equation's per-tile arrays
   int64_t an, bn;      // offsets (doubles) of the tile-norm tables in Work::dbuf
   double omega;        // overflow threshold
+  int64_t pk;          // first slot of this equation's packed tiles in Work::pack (see below)
 };
 
 // Per-equation results and bookkeeping, written by the kernels.
@@ -84,7 +85,29 @@ struct Work {
   int64_t timeout_ns;
   int32_t max_tiles;  // max over equations of pmax * qmax
   int32_t pad;
+  // Packed operand tiles (null: the kernel stages tiles from A, B, C directly).  One
+  // slot holds a tile in the shared-memory operand layout of the update GEMM (TT rows
+  // of k, row stride TT + 2, zero-padded), so one bulk copy stages it.  Per equation,
+  // from slot pk: A_ki (pmax x pmax slots, left operand), B_jl (qmax x qmax, right
+  // operand), then every final Y_kl twice (pmax x qmax each): as a left operand
+  // (column-major) and as a right operand (row-major).
+  char* pack;
+  int64_t pack_slot;  // bytes per slot
 };
+
+// Slot numbers within an equation's packed region.
+__host__ __device__ inline int64_t pack_a(const Inst& I, int k, int i) { return I.pk + static_cast<int64_t>(k) * I.pmax + i; }
+__host__ __device__ inline int64_t pack_b(const Inst& I, int j, int l) {
+  return I.pk + static_cast<int64_t>(I.pmax) * I.pmax + static_cast<int64_t>(j) * I.qmax + l;
+}
+__host__ __device__ inline int64_t pack_yl(const Inst& I, int k, int l) {
+  return I.pk + static_cast<int64_t>(I.pmax) * I.pmax + static_cast<int64_t>(I.qmax) * I.qmax +
+         static_cast<int64_t>(k) * I.qmax + l;
+}
+__host__ __device__ inline int64_t pack_yr(const Inst& I, int k, int l) {
+  return pack_yl(I, k, l) + static_cast<int64_t>(I.pmax) * I.qmax;
+}
+__host__ __device__ inline int64_t pack_slots(int64_t pmax, int64_t qmax) { return (pmax + qmax) * (pmax + qmax); }
 
 // ---------------------------------------------------------------- power-of-two scaling
 // 2^e as binary64 for e in [-1022, 1023]: biased exponent e + 1023, zero fraction.

@@ -157,6 +157,52 @@ __global__ void k_level_scatter(Work w) {
 // ---------------------------------------------------------------------------
 // Consistency scaling (end of Algorithm 4): alpha = min_kl alpha_kl, and every
 // tile with a larger local factor is multiplied by alpha / alpha_kl = 2^(E - e_kl).
+// Packed operand tiles (see Work::pack): A_ki for i > k in the left-operand layout
+// (L[kk * LDG + r] = A[row r of tile k, column kk of tile i]) and B_jl for j < l in
+// the right-operand layout (R[kk * LDG + c] = B[row kk of tile j, column c of tile
+// l]), zero outside the tiles, LDG = tt + 2.  Grid (equations, blocks per
+// equation); B tiles go through shared memory so that reads and writes coalesce.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pack(Work w, int tt) {
+  __shared__ T tb[64 * 65];
+  const Inst I = w.inst[blockIdx.x];
+  const int p = w.st[blockIdx.x].p, q = w.st[blockIdx.x].q;
+  const int32_t* rb = w.ibuf + I.rb;
+  const int32_t* cb = w.ibuf + I.cb;
+  const int LDG = tt + 2, nel = tt * LDG;
+  const T* A = static_cast<const T*>(I.A);
+  const T* B = static_cast<const T*>(I.B);
+  const int64_t na = static_cast<int64_t>(p) * p, nb = static_cast<int64_t>(q) * q;
+  for (int64_t sidx = blockIdx.y; sidx < na + nb; sidx += gridDim.y) {
+    if (sidx < na) {
+      const int k = static_cast<int>(sidx / p), i = static_cast<int>(sidx % p);
+      if (i <= k) continue;
+      const int r0 = rb[k], mt = rb[k + 1] - r0, k0 = rb[i], kd = rb[i + 1] - k0;
+      T* dst = reinterpret_cast<T*>(w.pack + pack_a(I, k, i) * w.pack_slot);
+      for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+        const int kk = idx / LDG, r = idx % LDG;
+        dst[idx] = (r < mt && kk < kd) ? A[(r0 + r) + static_cast<int64_t>(k0 + kk) * I.lda] : T(0);
+      }
+    } else {
+      const int64_t s2 = sidx - na;
+      const int j = static_cast<int>(s2 / q), l = static_cast<int>(s2 % q);
+      if (l <= j) continue;
+      const int k0 = cb[j], kd = cb[j + 1] - k0, c0 = cb[l], nt = cb[l + 1] - c0;
+      __syncthreads();  // the previous tile's reads of tb are done
+      for (int idx = threadIdx.x; idx < tt * tt; idx += blockDim.x) {
+        const int kk = idx % tt, c = idx / tt;
+        tb[c * (tt + 1) + kk] = (kk < kd && c < nt) ? B[(k0 + kk) + static_cast<int64_t>(c0 + c) * I.ldb] : T(0);
+      }
+      __syncthreads();
+      T* dst = reinterpret_cast<T*>(w.pack + pack_b(I, j, l) * w.pack_slot);
+      for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+        const int kk = idx / LDG, c = idx % LDG;
+        dst[idx] = (c < tt) ? tb[c * (tt + 1) + kk] : T(0);
+      }
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_consistency(Work w) {
   const int ntasks = w.ctrl->ntasks;

@@ -55,7 +55,7 @@ oz::Packed packed(const OzBuffers& b, int i) {
 }
 cudaError_t split(const oz::View& v, const oz::Packed& P, const int* skip, cudaStream_t s) {
   oz::k_oz_rowexp<<<grid_elems(P.RB * P.R * 32), 256, 0, s>>>(v, P.e, P.RB * P.R, skip);
-  oz::k_oz_split<<<grid_elems(P.slice_elems()), 256, 0, s>>>(v, P, skip);
+  oz::k_oz_split<<<static_cast<int>(std::min<int64_t>(P.RB * P.KB, 152 * 8)), 256, 0, s>>>(v, P, skip);
   return cudaGetLastError();
 }
 }  // namespace

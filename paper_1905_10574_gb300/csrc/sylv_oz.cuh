@@ -55,21 +55,21 @@ namespace oz {
 constexpr int kSlices = 7;             // 8-bit slices per operand (56 bits below the maximum)
 constexpr int kMaxW = kSlices + 1;     // binary64 residual: pairs (s, t), 1-based, with s + t <= kMaxW
 constexpr int kMaxW32 = 6;             // products for the binary32 recurrence: s + t <= 6 (40 bits)
-constexpr int BM = 128, BN = 64, BK = 64;
-constexpr int kChunk = 4;              // K blocks per exact binary32 chunk: 4 * 64 * 2^16 = 2^24
-constexpr int kFlush = 64;             // chunks per int32 sum: 64 * 2^24 = 2^30 < 2^31
-constexpr int NST = 4;                 // shared-memory stages
-constexpr int kTileA = BM * BK;        // bf16 elements of a left-operand tile (16 KB)
-constexpr int kTileB = BN * BK;        // of a right-operand tile (8 KB)
-constexpr int kThreads = 192;
-constexpr int LDR = BN + 1;            // row stride of the binary64 accumulator in shared memory
+constexpr int BM = 128, BN = 64, BK = 32;
+constexpr int kLeadW = 4;              // weights 2..4 are accumulated exactly (chunked)
+constexpr int kLeadStages = 6;         // 6 K blocks of 32 per exact binary32 chunk (< 2^24, see below)
+constexpr int kFlushLead = 64;         // chunks per int32 sum: 64 * 2^24 = 2^30 < 2^31
+constexpr int NST = 2;                 // shared-memory stages (all slices of one K block each)
+constexpr int kTileA = BM * BK;        // bf16 elements of a left-operand tile (8 KB)
+constexpr int kTileB = BN * BK;        // of a right-operand tile (4 KB)
+constexpr int kEpiWarps = 8;           // two per TMEM lane quarter, 32 columns each
+constexpr int kThreads = 32 * (kEpiWarps + 2);
 
 struct Smem {
-  __nv_bfloat16 a[NST][kTileA];
-  __nv_bfloat16 b[NST][kTileB];
-  double racc[BM * LDR];
+  __nv_bfloat16 a[NST][kSlices][kTileA];
+  __nv_bfloat16 b[NST][kSlices][kTileB];
   int ecol[2][BN];
-  unsigned long long full[NST], empty[NST], accfull[2], accempty[2];
+  unsigned long long full[NST], empty[NST], accfull, accempty;
   uint32_t tmem;
 };
 
@@ -121,26 +121,36 @@ __global__ void k_oz_rowexp(View v, int* e, int64_t rows_padded, const int* skip
   }
 }
 
-// Slices of every element: one thread per position of slice 0's packed layout,
-// writing the same position of all kSlices slices.
-__global__ void k_oz_split(View v, Packed P, const int* skip) {
+// Slices of every element, one block per packed tile: the tile is read along its
+// contiguous dimension into shared memory (rows when rs == 1, else K), then each
+// thread takes positions of the packed layout and writes all kSlices slices of each.
+__global__ void __launch_bounds__(256) k_oz_split(View v, Packed P, const int* skip) {
   if (skip && ld_volatile(skip)) return;
+  __shared__ double tile[BM * (BK + 1)];
   const int64_t per = P.slice_elems();
   const int tsz = P.R * BK;
-  for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < per;
-       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t tile = idx / tsz;
-    const int o = static_cast<int>(idx % tsz);
-    const int cm = o >> 6, w = o & 63;
-    const int rr = (cm >> 3) * 8 + (w >> 3), kk = (cm & 7) * 8 + (w & 7);
-    const int64_t r = (tile / P.KB) * P.R + rr, k = (tile % P.KB) * BK + kk;
-    const double x = view_at(v, r, k);
-    double u = (x == 0.0) ? 0.0 : mul2(x, 8 - P.e[r]);  // |u| < 256
+  const bool rcontig = v.rs == 1;
+  for (int64_t t = blockIdx.x; t < P.RB * P.KB; t += gridDim.x) {
+    const int64_t r0 = (t / P.KB) * P.R, k0 = (t % P.KB) * BK;
+    __syncthreads();  // the previous tile's reads are done
+    for (int idx = threadIdx.x; idx < tsz; idx += blockDim.x) {
+      const int r = rcontig ? idx % P.R : idx / BK;
+      const int kk = rcontig ? idx / P.R : idx % BK;
+      tile[r * (BK + 1) + kk] = view_at(v, r0 + r, k0 + kk);
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < tsz; o += blockDim.x) {
+      const int cm = o >> 6, w = o & 63;  // core matrix (rr/8) * (BK/8) + kk/8, then row-major 8 x 8
+      const int rr = (cm / (BK / 8)) * 8 + (w >> 3), kk = (cm % (BK / 8)) * 8 + (w & 7);
+      const double x = tile[rr * (BK + 1) + kk];
+      double u = (x == 0.0) ? 0.0 : mul2(x, 8 - P.e[r0 + rr]);  // |u| < 256
+      const int64_t idx = t * tsz + o;
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s) {
-      const double q = rint(u);
-      P.p[idx + s * per] = __float2bfloat16_rn(static_cast<float>(q));  // exact: |q| <= 256, an integer
-      u = (u - q) * 256.0;                                              // exact
+      for (int s = 0; s < kSlices; ++s) {
+        const double q = rint(u);
+        P.p[idx + s * per] = __float2bfloat16_rn(static_cast<float>(q));  // exact: |q| <= 256, an integer
+        u = (u - q) * 256.0;                                              // exact
+      }
     }
   }
 }
@@ -213,6 +223,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&v)[32]) {
       : "r"(ta));
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(ta));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // The two products of one launch: left operands (R = 128) and right operands (R = 64).
 struct Gemm {
   Packed a[2];
@@ -231,6 +250,19 @@ __device__ __forceinline__ void kb_range(int p, const Gemm& g, int64_t i0, int64
   }
 }
 
+// Exactness of the leading weights.  Per K block of 32, weight 2 (pair (1,1)) adds at
+// most 32 * 2^16 = 2^21 in magnitude, weight 3 (pairs (1,2), (2,1)) 2 * 32 * 2^15 =
+// 2^21, weight 4 ((1,3), (3,1), (2,2)) 32 * (2^15 + 2^15 + 2^14) < 2^21.33; six blocks
+// stay below 2^24, so those accumulators are taken out of TMEM exactly every six
+// blocks (integers, exact in binary32).  Weights >= 5 are accumulated over the whole
+// K range in binary32: their rounding is below 2^-24 of a sum that is itself below
+// 2^-24 of the leading term, so below 2^-48 of the result.
+//
+// The kernel.  One CTA per 128 x 64 tile of R; warp 8 loads, one thread of warp 9
+// issues the MMAs, warps 0-7 drain TMEM (warp w: TMEM lanes 32 (w & 3).., tile
+// columns 32 (w >> 2)..).  Per K block a stage holds all slices of both operands,
+// and every slice pair of weight <= maxw goes into the accumulator of its weight
+// (TMEM columns 64 (w - 2)..).  R starts as C and every flush subtracts its terms.
 __global__ void __launch_bounds__(kThreads, 1)
     k_oz_gemm(Gemm g, int maxw, const double* C, int64_t ldc, double* R, int64_t ldr, int64_t m, int64_t n,
               unsigned long long* rmax, int* err, long long timeout_ns, const int* skip) {
@@ -240,170 +272,229 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t i0 = static_cast<int64_t>(blockIdx.x) * BM, j0 = static_cast<int64_t>(blockIdx.y) * BN;
   const int mb = blockIdx.x, nb = blockIdx.y;
+  const int smax = min(kSlices, maxw - 1);  // slices in use
 
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(&sh.full[s], 1);
       mbar_init(&sh.empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&sh.accfull[b], 1);
-      mbar_init(&sh.accempty[b], 128);
-    }
+    mbar_init(&sh.accfull, 1);
+    mbar_init(&sh.accempty, 32 * kEpiWarps);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid < 2 * BN) sh.ecol[tid / BN][tid % BN] = g.b[tid / BN].e[static_cast<int64_t>(nb) * BN + tid % BN];
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&sh.tmem)), "r"(128));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&sh.tmem)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  for (int idx = tid; idx < BM * LDR; idx += kThreads) sh.racc[idx] = 0.0;
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = sh.tmem;
 
-  if (warp == 4) {
-    // ---- loads
+  if (warp == kEpiWarps) {
+    // ---- loads: all slices in use of one K block per stage
     if (lane == 0) {
-      int gk = 0;
+      int gs = 0;
       bool ok = true;
+      const uint32_t bytes = static_cast<uint32_t>(smax) * (kTileA + kTileB) * 2;
       for (int p = 0; p < 2 && ok; ++p) {
         int lo, hi;
         kb_range(p, g, i0, j0, lo, hi);
         const Packed& A = g.a[p];
         const Packed& B = g.b[p];
-        for (int w = maxw; w >= 2 && ok; --w)
-          for (int s = max(1, w - kSlices); s <= min(kSlices, w - 1) && ok; ++s) {
-            const int t = w - s;
-            const __nv_bfloat16* as = A.p + (s - 1) * A.slice_elems() + (static_cast<int64_t>(mb) * A.KB) * kTileA;
-            const __nv_bfloat16* bs = B.p + (t - 1) * B.slice_elems() + (static_cast<int64_t>(nb) * B.KB) * kTileB;
-            for (int kb = lo; kb < hi; ++kb, ++gk) {
-              const int st = gk % NST;
-              const uint32_t round = static_cast<uint32_t>(gk / NST);
-              if (!mbar_wait(&sh.empty[st], (round & 1u) ^ 1u, err, timeout_ns)) {
-                ok = false;
-                break;
-              }
-              mbar_expect_tx(&sh.full[st], (kTileA + kTileB) * 2);
-              bulk_g2s(sh.a[st], as + static_cast<int64_t>(kb) * kTileA, kTileA * 2, &sh.full[st]);
-              bulk_g2s(sh.b[st], bs + static_cast<int64_t>(kb) * kTileB, kTileB * 2, &sh.full[st]);
-            }
+        const __nv_bfloat16* ab = A.p + (static_cast<int64_t>(mb) * A.KB) * kTileA;
+        const __nv_bfloat16* bb = B.p + (static_cast<int64_t>(nb) * B.KB) * kTileB;
+        for (int kb = lo; kb < hi; ++kb, ++gs) {
+          const int st = gs & 1;
+          if (!mbar_wait(&sh.empty[st], ((gs >> 1) & 1) ^ 1, err, timeout_ns)) {
+            ok = false;
+            break;
           }
+          mbar_expect_tx(&sh.full[st], bytes);
+          for (int sl = 0; sl < smax; ++sl) {
+            bulk_g2s(sh.a[st][sl], ab + sl * A.slice_elems() + static_cast<int64_t>(kb) * kTileA, kTileA * 2,
+                     &sh.full[st]);
+            bulk_g2s(sh.b[st][sl], bb + sl * B.slice_elems() + static_cast<int64_t>(kb) * kTileB, kTileB * 2,
+                     &sh.full[st]);
+          }
+        }
       }
       if (!ok) atomicCAS(err, 0, SYLV_ERR_TIMEOUT);
     }
-  } else if (warp == 5) {
+  } else if (warp == kEpiWarps + 1) {
     // ---- MMAs
     if (lane == 0) {
-      int gk = 0, cc = 0;
-      bool ok = true;
+      int gs = 0, ev = 0, pend = -1;  // pend: event whose drain must end before the accumulators it frees are reused
+      bool pend_all = false, ok = true;
       for (int p = 0; p < 2 && ok; ++p) {
         int lo, hi;
         kb_range(p, g, i0, j0, lo, hi);
-        for (int w = maxw; w >= 2 && ok; --w)
-          for (int s = max(1, w - kSlices); s <= min(kSlices, w - 1) && ok; ++s)
-            for (int kc = lo; kc < hi && ok; kc += kChunk, ++cc) {
-              const int b = cc & 1;
-              const uint32_t use = static_cast<uint32_t>(cc >> 1);
-              if (!mbar_wait(&sh.accempty[b], (use & 1u) ^ 1u, err, timeout_ns)) {
+        unsigned written = 0;  // weights written since their last drain
+        int since = 0;
+        for (int kb = lo; kb < hi && ok; ++kb, ++gs) {
+          const int st = gs & 1;
+          if (!mbar_wait(&sh.full[st], (gs >> 1) & 1, err, timeout_ns)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          if (pend >= 0 && pend_all) {  // a product ended: every accumulator is being drained
+            if (!mbar_wait(&sh.accempty, pend & 1, err, timeout_ns)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            pend = -1;
+          }
+          for (int pass = 0; pass < 2; ++pass) {  // weights >= 5 first, then the leading ones
+            if (pass == 1 && pend >= 0) {  // the leading accumulators are being drained
+              if (!mbar_wait(&sh.accempty, pend & 1, err, timeout_ns)) {
                 ok = false;
                 break;
               }
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              const uint32_t dtm = tbase + static_cast<uint32_t>(b * BN);
-              for (int kb = kc; kb < min(kc + kChunk, hi); ++kb, ++gk) {
-                const int st = gk % NST;
-                const uint32_t round = static_cast<uint32_t>(gk / NST);
-                if (!mbar_wait(&sh.full[st], round & 1u, err, timeout_ns)) {
-                  ok = false;
-                  break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t aa = su32(sh.a[st]), ba = su32(sh.b[st]);
-#pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk)
-                  umma(dtm, sdesc(aa + kk * 256, 128, 1024), sdesc(ba + kk * 256, 128, 1024),
-                       (kb > kc || kk > 0) ? 1u : 0u);
-                umma_commit(&sh.empty[st]);
-              }
-              if (ok) umma_commit(&sh.accfull[b]);
+              pend = -1;
             }
+            for (int w = pass ? 2 : kLeadW + 1; w <= (pass ? kLeadW : maxw); ++w)
+              for (int sl = max(1, w - smax); sl <= min(smax, w - 1); ++sl) {
+                const int t = w - sl;
+                const uint32_t aa = su32(sh.a[st][sl - 1]), ba = su32(sh.b[st][t - 1]);
+                const uint32_t dtm = tbase + static_cast<uint32_t>((w - 2) * BN);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                  const bool acc = ((written >> w) & 1u) != 0;
+                  umma(dtm, sdesc(aa + kk * 256, 128, (BK / 8) * 128), sdesc(ba + kk * 256, 128, (BK / 8) * 128),
+                       acc ? 1u : 0u);
+                  written |= 1u << w;
+                }
+              }
+          }
+          if (!ok) break;
+          umma_commit(&sh.empty[st]);
+          ++since;
+          const bool last = kb == hi - 1;
+          if (last || since == kLeadStages) {
+            umma_commit(&sh.accfull);
+            pend = ev++;
+            pend_all = last;
+            written = last ? 0u : (written & ~((1u << (kLeadW + 1)) - 1u));
+            since = 0;
+          }
+        }
       }
       if (!ok) atomicCAS(err, 0, SYLV_ERR_TIMEOUT);
     }
   } else {
-    // ---- epilogue: warps 0-3, row 32 * warp + lane of the tile
-    const int row = 32 * warp + lane;
+    // ---- drain: row 32 (warp & 3) + lane, columns 32 (warp >> 2)..
+    const int row = 32 * (warp & 3) + lane;
+    const int cb0 = 32 * (warp >> 2);
     const int64_t gi = i0 + row;
-    int iacc[BN];
+    const uint32_t tl = tbase + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+    if (gi < m && C != R)
+      for (int j = 0; j < 32; ++j) {
+        const int64_t gj = j0 + cb0 + j;
+        if (gj < n) R[gi + gj * ldr] = C[gi + gj * ldc];
+      }
+    int iacc[kLeadW - 1][32];
 #pragma unroll
-    for (int j = 0; j < BN; ++j) iacc[j] = 0;
-    int cc = 0;
+    for (int a = 0; a < kLeadW - 1; ++a)
+#pragma unroll
+      for (int j = 0; j < 32; ++j) iacc[a][j] = 0;
+    int ev = 0;
     bool ok = true;
     for (int p = 0; p < 2 && ok; ++p) {
       int lo, hi;
       kb_range(p, g, i0, j0, lo, hi);
       const int erow = g.a[p].e[gi];
-      for (int w = maxw; w >= 2 && ok; --w) {
-        int nacc = 0;
-        for (int s = max(1, w - kSlices); s <= min(kSlices, w - 1) && ok; ++s)
-          for (int kc = lo; kc < hi; kc += kChunk, ++cc) {
-            const int b = cc & 1;
-            const uint32_t use = static_cast<uint32_t>(cc >> 1);
-            if (!mbar_wait(&sh.accfull[b], use & 1u, err, timeout_ns)) {
-              ok = false;
-              break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint32_t v0[32], v1[32];
-            const uint32_t ta = tbase + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(b * BN);
-            tmem_ld32(ta, v0);
-            tmem_ld32(ta + 32, v1);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(&sh.accempty[b]);
+      const int nst = hi - lo;
+      const int nlead = (nst - 1) / kLeadStages;  // drains of the leading weights before the last
+      int nacc = 0;
+      for (int d = 0; d <= nlead && ok; ++d, ++ev) {
+        const bool last = d == nlead;
+        if (!mbar_wait(&sh.accfull, ev & 1, err, timeout_ns)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              iacc[j] += __float2int_rn(__uint_as_float(v0[j]));
-              iacc[32 + j] += __float2int_rn(__uint_as_float(v1[j]));
-            }
-            ++nacc;
-            const bool last = (kc + kChunk >= hi) && (s == min(kSlices, w - 1));
-            if (nacc == kFlush || (last && ok)) {
-              // add the integer sums, scaled by 2^(e_row + e_col - 8w), to the binary64 accumulator
+        for (int a = 0; a < kLeadW - 1; ++a) {
+          uint32_t v0[16], v1[16];
+          tmem_ld16(tl + static_cast<uint32_t>(a * BN + cb0), v0);
+          tmem_ld16(tl + static_cast<uint32_t>(a * BN + cb0 + 16), v1);
+          tmem_wait_ld();
 #pragma unroll
-              for (int j = 0; j < BN; ++j) {
-                if (iacc[j] != 0)
-                  sh.racc[row * LDR + j] += mul2(static_cast<double>(iacc[j]), erow + sh.ecol[p][j] - 8 * w);
-                iacc[j] = 0;
-              }
-              nacc = 0;
-            }
+          for (int j = 0; j < 16; ++j) {
+            iacc[a][j] += __float2int_rn(__uint_as_float(v0[j]));
+            iacc[a][16 + j] += __float2int_rn(__uint_as_float(v1[j]));
           }
+        }
+        ++nacc;
+        const bool flush = last || nacc == kFlushLead;  // the same in every lane (TMEM loads are warp-collective)
+        if (flush) {
+          // R -= 2^(e_row + e_col) * (sum over weights w of 2^(-8w) * sum_w), smallest weights first
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            double dsum[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) dsum[j] = 0.0;
+            if (last)
+              for (int w = maxw; w > kLeadW; --w) {
+                uint32_t v[16];
+                tmem_ld16(tl + static_cast<uint32_t>((w - 2) * BN + cb0 + 16 * h), v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                  const float f = __uint_as_float(v[j]);
+                  if (f != 0.0f)
+                    dsum[j] += mul2(static_cast<double>(f), erow + sh.ecol[p][cb0 + 16 * h + j] - 8 * w);
+                }
+              }
+#pragma unroll
+            for (int a = kLeadW - 2; a >= 0; --a)
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if (iacc[a][16 * h + j] != 0)
+                  dsum[j] += mul2(static_cast<double>(iacc[a][16 * h + j]),
+                                  erow + sh.ecol[p][cb0 + 16 * h + j] - 8 * (a + 2));
+            if (gi < m)
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const int64_t gj = j0 + cb0 + 16 * h + j;
+                if (gj < n) R[gi + gj * ldr] -= dsum[j];
+              }
+          }
+        }
+        if (flush) {
+#pragma unroll
+          for (int a = 0; a < kLeadW - 1; ++a)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) iacc[a][j] = 0;
+          nacc = 0;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&sh.accempty);
       }
     }
     if (!ok) atomicCAS(err, 0, SYLV_ERR_TIMEOUT);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(128));
-  if (ld_volatile(err)) return;
-  // ---- R = C - (A X + X B), and max |R|
-  if (warp < 4) {
-    const int row = 32 * warp + lane;
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
+  if (ld_volatile(err) || !rmax) return;
+  // ---- max |R| of the tile
+  if (warp < kEpiWarps) {
+    const int row = 32 * (warp & 3) + lane;
+    const int cb0 = 32 * (warp >> 2);
     const int64_t gi = i0 + row;
     double mx = 0.0;
     if (gi < m)
-      for (int j = 0; j < BN; ++j) {
-        const int64_t gj = j0 + j;
-        if (gj < n) {
-          const double v = C[gi + gj * ldc] - sh.racc[row * LDR + j];
-          R[gi + gj * ldr] = v;
-          mx = fmax(mx, fabs(v));
-        }
+      for (int j = 0; j < 32; ++j) {
+        const int64_t gj = j0 + cb0 + j;
+        if (gj < n) mx = fmax(mx, fabs(R[gi + gj * ldr]));
       }
     mx = warp_max(mx);
-    if (lane == 0 && rmax) atomic_max_nonneg(rmax, mx);
+    if (lane == 0) atomic_max_nonneg(rmax, mx);
   }
 }
 

@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (mixed precision, batched, adjoint)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "mixed", "batched", "adjoint"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "mixed", "batched", "adjoint", "smscale"],
                     help="solve: the headline robust FP64 solve; mixed: FP32 + refinement vs FP64 at "
                          "m=n=8000; batched: 4096 uneven equations; adjoint: 256 Lyapunov forward+backward")
     return ap.parse_args()
@@ -375,6 +375,49 @@ def run_mixed(args):
     return line
 
 
+def run_smscale(args):
+    """SM scaling of the robust FP64 solve (the GPU analogue of the paper's core-scaling
+    study, Sec. 4): the persistent tile kernel capped at N SMs (2 CTAs each), the
+    rest of the solve unchanged.  Efficiency = T(1 SM) / (N * T(N SMs))."""
+    import torch
+    from paper_1905_10574_gb300 import build, inputs, sylv
+    build.build()
+    name = args.workload if args.workload != WORKLOAD else "benign_1000"
+    A, B, C, w = inputs.workload(name)
+    m, n = w["m"], w["n"]
+    dev = torch.device("cuda", 0)
+    Ad, Bd, C0 = (torch.from_numpy(x).to(dev) for x in (A, B, C))
+    stream = torch.cuda.current_stream(dev)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    rows = []
+    for sms in [1, 2, 4, 8, 19, 38, 76, nsm]:
+        opts = sylv.make_opts(tile=args.tile or w["tile"], stream=stream.cuda_stream, sync=True, max_sms=sms)
+        wsb = sylv.sylv_workspace_size(m, n, opts)
+        wsbuf = torch.empty(wsb + 256, dtype=torch.uint8, device=dev)
+        opts.workspace = (wsbuf.data_ptr() + 255) // 256 * 256
+        opts.workspace_bytes = wsb
+        steps = 2 if sms < 8 else args.steps
+        Cs = [C0.clone() for _ in range(1 + steps)]
+        res = sylv.sylv_result()
+
+        def fn(i):
+            rc = sylv.sylv_tri_solve_ex(m, n, Ad.data_ptr(), Ad.stride(1), Bd.data_ptr(), Bd.stride(1),
+                                        Cs[i].data_ptr(), Cs[i].stride(1), opts, res)
+            if rc not in (0, 1):
+                raise sylv.SylvError(rc, "smscale")
+
+        ms, _ = _timed(fn, steps, 1, stream)
+        rows.append({"sms": sms, "ms_per_solve": ms, "gflops_2mnmn": flops_2(m, n) / ms / 1e6})
+        del Cs, wsbuf
+    t1 = rows[0]["ms_per_solve"]
+    for r in rows:
+        r["speedup"] = t1 / r["ms_per_solve"]
+        r["efficiency"] = r["speedup"] / r["sms"]
+    return {"metric": "SM-scaling efficiency of the robust FP64 solve", "value": rows[-1]["efficiency"],
+            "unit": "fraction", "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "m": m, "n": n, "tile": args.tile or w["tile"]}, "rows": rows}
+
+
 def run_batched(args):
     """4096 independent equations, m, n log-uniform in [16, 512]: autotuned tile per
     size bucket, one batched persistent launch captured in a CUDA graph and replayed;
@@ -517,6 +560,8 @@ def main():
         print(json.dumps(run_batched(args)), flush=True)
     elif args.mode == "adjoint":
         print(json.dumps(run_adjoint(args)), flush=True)
+    elif args.mode == "smscale":
+        print(json.dumps(run_smscale(args)), flush=True)
     else:
         run_ours(args)
 

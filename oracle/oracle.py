@@ -176,9 +176,9 @@ def trsyl(A, B, C, robust: bool = True, transa: bool = False, transb: bool = Fal
             "peak": float(peak.value), "nan_seen": bool(nan_seen.value)}
 
 
-def kron_solve(A, B, C, transa: bool = False, transb: bool = False) -> np.ndarray:
-    """X with op(A) X + X op(B) = C from the Kronecker form of eq. (2):
-    (I_n (x) op(A) + op(B)^T (x) I_m) vec(X) = vec(C), vec stacking columns."""
+def kron_solve(A, B, C, transa: bool = False, transb: bool = False, isgn: int = 1) -> np.ndarray:
+    """X with op(A) X + isgn X op(B) = C from the Kronecker form of eq. (2):
+    (I_n (x) op(A) + isgn op(B)^T (x) I_m) vec(X) = vec(C), vec stacking columns."""
     A = quasi_tri(A)
     B = quasi_tri(B)
     if transa:
@@ -187,7 +187,7 @@ def kron_solve(A, B, C, transa: bool = False, transb: bool = False) -> np.ndarra
         B = B.T
     C = np.asarray(C, dtype=np.float64)
     m, n = C.shape
-    K = np.kron(np.eye(n), A) + np.kron(B.T, np.eye(m))
+    K = np.kron(np.eye(n), A) + (1.0 if isgn >= 0 else -1.0) * np.kron(B.T, np.eye(m))
     x = np.linalg.solve(K, C.reshape(-1, order="F"))
     return x.reshape((m, n), order="F")
 
@@ -233,9 +233,9 @@ def quasi_mask(T) -> np.ndarray:
     return (r <= c) | ((r == c + 1) & (T != 0.0))
 
 
-def kron_grad(A, B, C, W, transa: bool = False, transb: bool = False):
-    """Gradients of L = sum(W * X), op(A) X + X op(B) = C, from the Kronecker form
-    K vec(X) = vec(C), K = I_n (x) op(A) + op(B)^T (x) I_m (eq. (2) vectorised).
+def kron_grad(A, B, C, W, transa: bool = False, transb: bool = False, isgn: int = 1):
+    """Gradients of L = sum(W * X), op(A) X + isgn X op(B) = C, from the Kronecker form
+    K vec(X) = vec(C), K = I_n (x) op(A) + isgn op(B)^T (x) I_m (eq. (2) vectorised).
 
     dL/dvec(C) = K^-T vec(W) =: lam and dL/dK = -lam vec(X)^T.  op(A)[i,k] sits in K
     at (i + m j, k + m j) for every j; op(B)[k,j] sits at (i + m j, i + m k) for every
@@ -248,7 +248,8 @@ def kron_grad(A, B, C, W, transa: bool = False, transb: bool = False):
     opB = B.T if transb else B
     C = np.asarray(C, dtype=np.float64)
     m, n = C.shape
-    K = np.kron(np.eye(n), opA) + np.kron(opB.T, np.eye(m))
+    sg = 1.0 if isgn >= 0 else -1.0
+    K = np.kron(np.eye(n), opA) + sg * np.kron(opB.T, np.eye(m))
     x = np.linalg.solve(K, C.reshape(-1, order="F"))
     lam = np.linalg.solve(K.T, np.asarray(W, dtype=np.float64).reshape(-1, order="F"))
     GK = -np.outer(lam, x)
@@ -259,7 +260,7 @@ def kron_grad(A, B, C, W, transa: bool = False, transb: bool = False):
     dopB = np.zeros((n, n))
     for k in range(n):
         for j in range(n):
-            dopB[k, j] = sum(GK[i + m * j, i + m * k] for i in range(m))
+            dopB[k, j] = sg * sum(GK[i + m * j, i + m * k] for i in range(m))
     dA = dopA.T if transa else dopA
     dB = dopB.T if transb else dopB
     dA = np.where(quasi_mask(A), dA, 0.0)

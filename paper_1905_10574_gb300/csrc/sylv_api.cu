@@ -332,6 +332,8 @@ int get_workspace(size_t need, void** out) {
 
 struct Opts {
   int transa, transb, precision, tile, maxit, sync;
+  int isgn;     // +1 or -1: sign of the B term
+  int max_sms;  // 0: all SMs
   double omega, tol;
   int64_t timeout_ns;
   cudaStream_t stream;
@@ -346,6 +348,9 @@ int read_opts(const sylv_opts* o, Opts* out) {
   if (o->transa < 0 || o->transa > 1 || o->transb < 0 || o->transb > 1) return SYLV_ERR_UNSUPPORTED;
   if (o->precision < SYLV_FP64 || o->precision > SYLV_FP32_REFINE) return SYLV_ERR_UNSUPPORTED;
   if (o->tile < 0 || o->tile == 1 || o->tile > 64) return SYLV_ERR_UNSUPPORTED;
+  if (o->isgn < -1 || o->isgn > 1 || o->max_sms < 0) return SYLV_ERR_UNSUPPORTED;
+  out->isgn = o->isgn < 0 ? -1 : 1;
+  out->max_sms = o->max_sms;
   out->transa = o->transa;
   out->transb = o->transb;
   out->precision = o->precision;
@@ -378,8 +383,8 @@ SolvePlan plan_solve(int64_t m, int64_t n, const Opts& o) {
   size_t off = 0;
   P.off_at = off;
   if (o.transa) off = align_up(off + sizeof(double) * m * m);
-  P.off_bt = off;
-  if (o.transb) off = align_up(off + sizeof(double) * n * n);
+  P.off_bt = off;  // op(B) copied: anti-transposed (transb) and/or negated (isgn = -1)
+  if (o.transb || o.isgn < 0) off = align_up(off + sizeof(double) * n * n);
   if (o.precision == SYLV_FP32_REFINE) {
     P.off_a32 = off;
     off = align_up(off + sizeof(float) * m * m);
@@ -425,6 +430,9 @@ int check_args(int64_t m, int64_t n, const void* A, int64_t lda, const void* B, 
   return SYLV_OK;
 }
 
+// Grid cap of the persistent tile kernel for an SM budget (0: none): two CTAs per SM.
+int cap_ctas(int ctas, int max_sms) { return max_sms > 0 ? std::min(ctas, 2 * max_sms) : ctas; }
+
 int grid_for(int64_t elems) {
   int64_t g = (elems + 255) / 256;
   const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
@@ -443,7 +451,7 @@ int enqueue_fp64(const SolvePlan& P, char* ws, const double* A, int64_t lda, con
   k_set_inst<<<1, 1, 0, s>>>(w.inst, I[0]);
   cudaError_t e = run_prep<double>(w, L, 1, std::max(P.shape.m, P.shape.n), std::max(P.shape.pmax, P.shape.qmax), s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
-  e = launch_dag_f64(P.shape.t, robust, w, std::min(L.max_tiles, L.ncta), s);
+  e = launch_dag_f64(P.shape.t, robust, w, cap_ctas(std::min(L.max_tiles, L.ncta), o.max_sms), s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
   k_consistency<double><<<grid_for(static_cast<int64_t>(L.max_tiles) * 256), 256, 0, s>>>(w);
   k_results<<<1, 32, 0, s>>>(w);
@@ -542,7 +550,7 @@ int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, c
       if (cudaMemsetAsync(w.tflag, 0, sizeof(int32_t) * L.sum_tiles, s) != cudaSuccess) return SYLV_ERR_CUDA;
       if (cudaMemsetAsync(&w.ctrl->ticket, 0, sizeof(int32_t), s) != cudaSuccess) return SYLV_ERR_CUDA;
     }
-    e = launch_dag_f32(P.shape.t, w, std::min(L.max_tiles, L.ncta), s);
+    e = launch_dag_f32(P.shape.t, w, cap_ctas(std::min(L.max_tiles, L.ncta), o.max_sms), s);
     if (e != cudaSuccess) return SYLV_ERR_CUDA;
     k_accumulate<<<grid_for(static_cast<int64_t>(L.max_tiles) * 256), 256, 0, s>>>(w, X, m, Dlast, rmax, amax, bmax,
                                                                                    dmax, xmax, &rs->conv);
@@ -590,10 +598,11 @@ int solve_impl(int64_t m, int64_t n, const double* A, int64_t lda, const double*
     Ae = At;
     ldae = m;
   }
-  if (o.transb) {
+  if (o.transb || o.isgn < 0) {
     double* Bt = reinterpret_cast<double*>(ws + P.off_bt);
-    k_anti_transpose<double><<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, s>>>(B, ldb, Bt, n, n);
-    k_flip<double><<<grid_for(m * n / 2 + 1), 256, 0, s>>>(C, ldc, m, n, 1);
+    k_operand_copy<double><<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, s>>>(B, ldb, Bt, n, n, o.transb,
+                                                                              o.isgn < 0 ? -1.0 : 1.0);
+    if (o.transb) k_flip<double><<<grid_for(m * n / 2 + 1), 256, 0, s>>>(C, ldc, m, n, 1);
     Be = Bt;
     ldbe = n;
   }
@@ -763,6 +772,8 @@ struct sylv_batch_plan {
   int tt = 32;
   int precision = SYLV_FP64;
   int transa = 0, transb = 0;
+  int isgn = 1;     // -1: the B copies are negated
+  int max_sms = 0;  // cap on the SMs of the tile kernel (0: all)
   char* ws = nullptr;
   Layout L{};
   Work w{};
@@ -823,6 +834,8 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
   P->precision = o.precision;
   P->transa = o.transa;
   P->transb = o.transb;
+  P->isgn = o.isgn;
+  P->max_sms = o.max_sms;
   P->L = make_layout(sh, 0, 0, 2, static_cast<int>(sizeof(double)));
   P->maxN = maxN;
   P->pmax_all = pmax_all;
@@ -836,7 +849,7 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
         oa[i] = off;
         off = align_up(off + sizeof(double) * sh[i].m * sh[i].m);
       }
-    if (o.transb)
+    if (o.transb || o.isgn < 0)
       for (int i = 0; i < count; ++i) {
         ob[i] = off;
         off = align_up(off + sizeof(double) * sh[i].n * sh[i].n);
@@ -856,12 +869,14 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
     std::vector<TransDesc> ta(count), tb(count);
     for (int i = 0; i < count; ++i) {
       if (o.transa) {
-        ta[i] = TransDesc{static_cast<const double*>(Av[i]), la[i], reinterpret_cast<double*>(P->ws + oa[i]), sh[i].m};
+        ta[i] = TransDesc{static_cast<const double*>(Av[i]), la[i], reinterpret_cast<double*>(P->ws + oa[i]), sh[i].m,
+                          1, 0, 1.0};
         Av[i] = ta[i].dst;
         la[i] = std::max<int64_t>(sh[i].m, 1);
       }
-      if (o.transb) {
-        tb[i] = TransDesc{static_cast<const double*>(Bv[i]), lb[i], reinterpret_cast<double*>(P->ws + ob[i]), sh[i].n};
+      if (o.transb || o.isgn < 0) {
+        tb[i] = TransDesc{static_cast<const double*>(Bv[i]), lb[i], reinterpret_cast<double*>(P->ws + ob[i]), sh[i].n,
+                          o.transb, 0, o.isgn < 0 ? -1.0 : 1.0};
         Bv[i] = tb[i].dst;
         lb[i] = std::max<int64_t>(sh[i].n, 1);
       }
@@ -872,7 +887,7 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
     bool ok = cudaMemcpy(P->w.inst, I.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice) == cudaSuccess;
     if (ok && o.transa)
       ok = cudaMemcpy(P->dta, ta.data(), sizeof(TransDesc) * count, cudaMemcpyHostToDevice) == cudaSuccess;
-    if (ok && o.transb)
+    if (ok && (o.transb || o.isgn < 0))
       ok = cudaMemcpy(P->dtb, tb.data(), sizeof(TransDesc) * count, cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) {
       cudaFree(P->ws);
@@ -895,14 +910,13 @@ int sylv_batch_execute(sylv_batch_plan* P, void* stream) {
     k_anti_transpose_batched<<<dim3(nt32, nt32, P->count), 256, 0, s>>>(P->dta);
     k_flip_batched<<<dim3(flip_grid, P->count), 256, 0, s>>>(P->w.inst, 0);
   }
-  if (P->transb) {
-    k_anti_transpose_batched<<<dim3(nt32, nt32, P->count), 256, 0, s>>>(P->dtb);
-    k_flip_batched<<<dim3(flip_grid, P->count), 256, 0, s>>>(P->w.inst, 1);
-  }
+  if (P->transb || P->isgn < 0) k_anti_transpose_batched<<<dim3(nt32, nt32, P->count), 256, 0, s>>>(P->dtb);
+  if (P->transb) k_flip_batched<<<dim3(flip_grid, P->count), 256, 0, s>>>(P->w.inst, 1);
   if (cudaMemsetAsync(P->ws + L.zero_lo, 0, L.zero_hi - L.zero_lo, s) != cudaSuccess) return SYLV_ERR_CUDA;
   cudaError_t e = run_prep<double>(P->w, L, P->count, P->maxN, P->pmax_all, s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
-  e = launch_dag_f64(P->tt, P->precision == SYLV_FP64, P->w, static_cast<int>(std::min<int64_t>(L.sum_tiles, L.ncta)), s);
+  e = launch_dag_f64(P->tt, P->precision == SYLV_FP64, P->w,
+                     cap_ctas(static_cast<int>(std::min<int64_t>(L.sum_tiles, L.ncta)), P->max_sms), s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
   k_consistency<double><<<grid_for(L.sum_tiles * 256), 256, 0, s>>>(P->w);
   k_results<<<(P->count + 255) / 256, 256, 0, s>>>(P->w);
@@ -994,7 +1008,7 @@ int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, 
     const double* Qp = o.transa ? G : Y;
     const int64_t lp = o.transa ? ldy : ldg, lq = o.transa ? ldg : ldy;
     k_grad_product<<<dim3((m + GT - 1) / GT, (m + GT - 1) / GT), 256, 0, s>>>(Pp, 1, lp, Qp, 1, lq, m, n, A, lda,
-                                                                                dA, ldda);
+                                                                                dA, ldda, 1.0);
   }
   if (dB) {
     // op(B) = B: dB = -Y^T Gamma: P(i,r) = Y[r + i ldy], Q(j,r) = G[r + j ldg]
@@ -1002,8 +1016,9 @@ int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, 
     const double* Pp = o.transb ? G : Y;
     const double* Qp = o.transb ? Y : G;
     const int64_t lp = o.transb ? ldg : ldy, lq = o.transb ? ldy : ldg;
+    // With op(A) Y - Y op(B) = alpha C the B term carries -1: dB changes sign.
     k_grad_product<<<dim3((n + GT - 1) / GT, (n + GT - 1) / GT), 256, 0, s>>>(Pp, lp, 1, Qp, lq, 1, n, m, B, ldb,
-                                                                                dB, lddb);
+                                                                                dB, lddb, o.isgn < 0 ? -1.0 : 1.0);
   }
   if (e != 0) k_scale_pow2<<<grid_for(m * n), 256, 0, s>>>(G, ldg, m, n, static_cast<int>(e));
   if (cudaGetLastError() != cudaSuccess) return SYLV_ERR_CUDA;
@@ -1079,6 +1094,7 @@ int sylv_tri_solve_backward_batched(int32_t count, const int64_t* m, const int64
       g.ldt = lda[i];
       g.D = dA[i];
       g.ldd = ldda[i];
+      g.sign = 1.0;
       gd.push_back(g);
     }
     if (dB && dB[i]) {
@@ -1095,6 +1111,7 @@ int sylv_tri_solve_backward_batched(int32_t count, const int64_t* m, const int64
       g.ldt = ldb[i];
       g.D = dB[i];
       g.ldd = lddb[i];
+      g.sign = o.isgn < 0 ? -1.0 : 1.0;  // op(A) Y - Y op(B) = alpha C: dB changes sign
       gd.push_back(g);
     }
     sd.push_back(ScaleDesc{G[i], ldg[i], m[i], n[i], static_cast<int>(log2scale[i]), 0});

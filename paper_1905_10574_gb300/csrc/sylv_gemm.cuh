@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(256) k_residual(const double* __restrict__ A, 
 __global__ void __launch_bounds__(256) k_grad_product(const double* __restrict__ P, int64_t psi, int64_t psc,
                                                       const double* __restrict__ Q, int64_t qsj, int64_t qsc,
                                                       int64_t N, int64_t K, const double* __restrict__ T,
-                                                      int64_t ldt, double* __restrict__ D, int64_t ldd) {
+                                                      int64_t ldt, double* __restrict__ D, int64_t ldd,
+                                                      double sign) {
   __shared__ __align__(16) double Ls[GK * GLD];
   __shared__ __align__(16) double Rs[GK * GLD];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(256) k_grad_product(const double* __restrict__
       const int64_t r = i0 + tx * 4 + i, c = j0 + ty * 4 + j;
       if (r < N && c < N) {
         const bool keep = (r <= c) || (r == c + 1 && T[r + c * ldt] != 0.0);
-        D[r + c * ldd] = keep ? acc[i][j] : 0.0;
+        D[r + c * ldd] = keep ? sign * acc[i][j] : 0.0;
       }
     }
 }
@@ -504,6 +505,7 @@ struct GradDesc {
   int64_t ldt;
   double* D;
   int64_t ldd;
+  double sign;  // -1 for dB of op(A) Y - Y op(B) = alpha C
 };
 
 __global__ void __launch_bounds__(256) k_grad_product_batched(const GradDesc* __restrict__ gd) {
@@ -546,7 +548,7 @@ __global__ void __launch_bounds__(256) k_grad_product_batched(const GradDesc* __
       const int64_t r = i0 + tx * 4 + i, c = j0 + ty * 4 + j;
       if (r < g.N && c < g.N) {
         const bool keep = (r <= c) || (r == c + 1 && g.T[r + c * g.ldt] != 0.0);
-        g.D[r + c * g.ldd] = keep ? acc[i][j] : 0.0;
+        g.D[r + c * g.ldd] = keep ? g.sign * acc[i][j] : 0.0;
       }
     }
 }

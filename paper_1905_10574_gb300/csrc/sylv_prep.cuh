@@ -261,13 +261,12 @@ __global__ void k_results(Work w) {
 // A^T Y + Y B = C  <=>  (J A^T J)(J Y) + (J Y) B = J C,  J the reversal permutation;
 // J A^T J is upper quasi-triangular when A is.  dst = J src^T J restricted to the
 // quasi-triangular part (other entries 0), through a 32x32 shared-memory tile.
+// dst(i, j) = sign * src(N-1-j, N-1-i) on the quasi-triangular part; one block
+// covers dst rows i0.., cols j0.. (32 x 8 threads).
 template <typename T>
-__global__ void k_anti_transpose(const T* __restrict__ src, int64_t lds, T* __restrict__ dst, int64_t ldd,
-                                 int64_t N) {
-  __shared__ T tile[32][33];
-  // dst(i, j) = src(N-1-j, N-1-i).  Block covers dst rows i0.., cols j0..
-  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * 32, j0 = static_cast<int64_t>(blockIdx.y) * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+__device__ __forceinline__ void k_anti_transpose_body(const T* __restrict__ src, int64_t lds, T* __restrict__ dst,
+                                                      int64_t ldd, int64_t N, T sign, T (&tile)[32][33], int64_t i0,
+                                                      int64_t j0, int tx, int ty) {
   // source rows N-1-j (j in j0..j0+31), source cols N-1-i (i in i0..i0+31)
   for (int yy = ty; yy < 32; yy += 8) {
     const int64_t i = i0 + yy, j = j0 + tx;  // read coalesced along source rows = N-1-j
@@ -278,7 +277,34 @@ __global__ void k_anti_transpose(const T* __restrict__ src, int64_t lds, T* __re
   __syncthreads();
   for (int yy = ty; yy < 32; yy += 8) {
     const int64_t j = j0 + yy, i = i0 + tx;
-    if (i < N && j < N) dst[i + j * ldd] = (i <= j + 1) ? tile[tx][yy] : T(0);
+    if (i < N && j < N) dst[i + j * ldd] = (i <= j + 1) ? sign * tile[tx][yy] : T(0);
+  }
+}
+template <typename T>
+__global__ void k_anti_transpose(const T* __restrict__ src, int64_t lds, T* __restrict__ dst, int64_t ldd,
+                                 int64_t N) {
+  __shared__ T tile[32][33];
+  k_anti_transpose_body(src, lds, dst, ldd, N, T(1), tile, static_cast<int64_t>(blockIdx.x) * 32,
+                        static_cast<int64_t>(blockIdx.y) * 32, static_cast<int>(threadIdx.x & 31),
+                        static_cast<int>(threadIdx.x >> 5));
+}
+
+// dst = sign * op(src) on the quasi-triangular part: op = J src^T J (trans) or the
+// identity.  The anti-transpose turns op(B) = B^T into an upper quasi-triangular
+// matrix; the sign turns A Y - Y B into A Y + Y (-B).
+template <typename T>
+__global__ void k_operand_copy(const T* __restrict__ src, int64_t lds, T* __restrict__ dst, int64_t ldd, int64_t N,
+                               int trans, T sign) {
+  __shared__ T tile[32][33];
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * 32, j0 = static_cast<int64_t>(blockIdx.y) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (trans) {
+    k_anti_transpose_body(src, lds, dst, ldd, N, sign, tile, i0, j0, tx, ty);
+    return;
+  }
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t i = i0 + tx, j = j0 + yy;
+    if (i < N && j < N) dst[i + j * ldd] = (i <= j + 1) ? sign * src[i + j * lds] : T(0);
   }
 }
 
@@ -317,9 +343,13 @@ struct TransDesc {
   int64_t lds;
   double* dst;  // N x N, leading dimension N
   int64_t N;
+  int32_t trans;  // anti-transpose (op = ^T) or plain copy
+  int32_t pad;
+  double sign;    // -1 for the B operand of isgn = -1
 };
 
-// dst_e = J src_e^T J (quasi-triangular part) for every equation e = blockIdx.z.
+// dst_e = sign_e * op(src_e) (quasi-triangular part; op = J .^T J or the identity) for every
+// equation e = blockIdx.z.
 __global__ void k_anti_transpose_batched(const TransDesc* __restrict__ d) {
   __shared__ double tile[32][33];
   const TransDesc D = d[blockIdx.z];
@@ -327,14 +357,13 @@ __global__ void k_anti_transpose_batched(const TransDesc* __restrict__ d) {
   const int64_t i0 = static_cast<int64_t>(blockIdx.x) * 32, j0 = static_cast<int64_t>(blockIdx.y) * 32;
   if (i0 >= N || j0 >= N) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int yy = ty; yy < 32; yy += 8) {
-    const int64_t i = i0 + yy, j = j0 + tx;
-    tile[yy][tx] = (i < N && j < N) ? D.src[(N - 1 - j) + (N - 1 - i) * D.lds] : 0.0;
+  if (D.trans) {
+    k_anti_transpose_body(D.src, D.lds, D.dst, N, N, D.sign, tile, i0, j0, tx, ty);
+    return;
   }
-  __syncthreads();
   for (int yy = ty; yy < 32; yy += 8) {
-    const int64_t j = j0 + yy, i = i0 + tx;
-    if (i < N && j < N) D.dst[i + j * N] = (i <= j + 1) ? tile[tx][yy] : 0.0;
+    const int64_t i = i0 + tx, j = j0 + yy;
+    if (i < N && j < N) D.dst[i + j * N] = (i <= j + 1) ? D.sign * D.src[i + j * D.lds] : 0.0;
   }
 }
 

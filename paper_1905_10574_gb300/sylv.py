@@ -44,7 +44,7 @@ class sylv_opts(ctypes.Structure):
                 ("tile", ctypes.c_int32), ("omega", ctypes.c_double), ("tol", ctypes.c_double),
                 ("maxit", ctypes.c_int32), ("sync", ctypes.c_int32), ("timeout_ms", ctypes.c_int64),
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("isgn", ctypes.c_int32), ("max_sms", ctypes.c_int32)]
 
 
 class sylv_result(ctypes.Structure):
@@ -302,8 +302,10 @@ class Result:
 
 
 def make_opts(*, transa=False, transb=False, precision="fp64", tile=0, omega=0.0, tol=0.0, maxit=0,
-              timeout_ms=0, stream=None, sync=True) -> sylv_opts:
+              timeout_ms=0, stream=None, sync=True, isgn=1, max_sms=0) -> sylv_opts:
     o = sylv_default_opts()
+    o.isgn = -1 if isgn < 0 else 1
+    o.max_sms = int(max_sms)
     o.transa = int(bool(transa))
     o.transb = int(bool(transb))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -318,9 +320,10 @@ def make_opts(*, transa=False, transb=False, precision="fp64", tile=0, omega=0.0
 
 
 def solve(A, B, C, *, transa=False, transb=False, precision="fp64", tile=0, omega=0.0, tol=0.0, maxit=0,
-          timeout_ms=0, inplace=False, check=True):
-    """Solve op(A) Y + Y op(B) = alpha C for CUDA float64 tensors; returns (Y, Result).
-    Y is column-major; with inplace=True and a column-major C, C itself is overwritten."""
+          timeout_ms=0, inplace=False, check=True, isgn=1, max_sms=0):
+    """Solve op(A) Y + isgn Y op(B) = alpha C (isgn = +1 or -1) for CUDA float64 tensors;
+    returns (Y, Result).  Y is column-major; with inplace=True and a column-major C, C
+    itself is overwritten.  max_sms caps the SMs the tile kernel occupies (0 = all)."""
     torch = _torch()
     A = fortran(A)
     B = fortran(B)
@@ -329,7 +332,7 @@ def solve(A, B, C, *, transa=False, transb=False, precision="fp64", tile=0, omeg
     m, n = Y.shape
     stream = torch.cuda.current_stream(Y.device).cuda_stream
     o = make_opts(transa=transa, transb=transb, precision=precision, tile=tile, omega=omega, tol=tol,
-                  maxit=maxit, timeout_ms=timeout_ms, stream=stream, sync=True)
+                  maxit=maxit, timeout_ms=timeout_ms, stream=stream, sync=True, isgn=isgn, max_sms=max_sms)
     ws_bytes = sylv_workspace_size(m, n, o)
     ws = torch.empty(max(ws_bytes, 1) + 256, dtype=torch.uint8, device=Y.device)
     base = (ws.data_ptr() + 255) // 256 * 256
@@ -357,7 +360,7 @@ def residual(A, B, X, C, *, stream=None):
     return R
 
 
-def batch_solve(As, Bs, Cs, *, transa=False, transb=False, tile=0, precision="fp64", timeout_ms=0):
+def batch_solve(As, Bs, Cs, *, transa=False, transb=False, tile=0, precision="fp64", timeout_ms=0, isgn=1):
     """Solve a list of equations op(A_i) Y_i + Y_i op(B_i) = alpha_i C_i in one batched
     launch; Cs are overwritten when they are column-major float64 CUDA tensors, else
     copies are solved.  Returns (Ys, [Result])."""
@@ -366,7 +369,7 @@ def batch_solve(As, Bs, Cs, *, transa=False, transb=False, tile=0, precision="fp
     Bs = [fortran(b) for b in Bs]
     Ys = [fortran(c) for c in Cs]
     o = make_opts(transa=transa, transb=transb, tile=tile, precision=precision, timeout_ms=timeout_ms,
-                  stream=torch.cuda.current_stream().cuda_stream)
+                  stream=torch.cuda.current_stream().cuda_stream, isgn=isgn)
     plan = sylv_batch_create([y.shape[0] for y in Ys], [y.shape[1] for y in Ys], [a.data_ptr() for a in As],
                              [_ld(a) for a in As], [b.data_ptr() for b in Bs], [_ld(b) for b in Bs],
                              [y.data_ptr() for y in Ys], [_ld(y) for y in Ys], o)

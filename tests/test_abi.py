@@ -37,7 +37,7 @@ def test_binding_covers_header():
 def test_struct_layouts():
     from paper_1905_10574_gb300 import sylv
     # offsets implied by the C declarations (natural alignment)
-    assert ctypes.sizeof(sylv.sylv_opts) == 72
+    assert ctypes.sizeof(sylv.sylv_opts) == 80
     assert sylv.sylv_opts.omega.offset == 16 and sylv.sylv_opts.timeout_ms.offset == 40
     assert sylv.sylv_opts.workspace_bytes.offset == 64
     assert ctypes.sizeof(sylv.sylv_result) == 40

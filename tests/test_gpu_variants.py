@@ -1,0 +1,142 @@
+"""GPU tests of the solver's variants beyond the paper's equation: the sign variant
+op(A) Y - Y op(B) = alpha C (LAPACK's ISGN = -1) and the SM cap of the persistent
+tile kernel (for SM-scaling measurements).
+
+The sign variant is checked against the oracle's Kronecker solve of the signed
+equation, and bitwise against the +1 solve with -B (negation is exact, so both run
+the same arithmetic).  Test matrices take B with eigenvalues of negative real part,
+so that A Y - Y B is as well conditioned as the paper's A Y + Y B.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1905_10574_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sy():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_10574_gb300 import build, sylv
+    build.build()
+    sylv.load()
+    return sylv
+
+
+def dev(a):
+    return torch.from_numpy(np.asfortranarray(a)).cuda()
+
+
+def solve(sy, A, B, C, **kw):
+    Y, res = sy.solve(dev(A), dev(B), dev(C), **kw)
+    torch.cuda.synchronize()
+    return Y.cpu().numpy(), res
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def signed_problem(m, n, seed):
+    A, Bg, C = inputs.problem(m, n, seed, kind="wellcond")
+    return A, -Bg, C, Bg  # A Y - Y (-Bg) = C is A Y + Y Bg = C
+
+
+@pytest.mark.parametrize("m,n,tile", [(70, 45, 32), (130, 97, 24), (64, 200, 0)])
+def test_sign_variant(orc, sy, m, n, tile):
+    A, B, C, Bg = signed_problem(m, n, seed=m + n)
+    Y, res = solve(sy, A, B, C, isgn=-1, tile=tile)
+    Yp, resp = solve(sy, A, Bg, C, tile=tile)
+    assert res.info == 0 and res.log2scale == resp.log2scale
+    assert np.array_equal(Y, Yp)  # the same arithmetic on -(-Bg) = Bg
+    if m * n <= 4000:
+        ref = orc.kron_solve(A, B, C, isgn=-1)
+        assert rel(Y, ref) <= 1e-12
+    ref = orc.trsyl(A, Bg, C)
+    assert rel(np.ldexp(Y, int(ref["log2scale"]) - int(res.log2scale)), ref["Y"]) <= 1e-12
+
+
+def test_sign_variant_transposed(orc, sy):
+    A, B, C, _ = signed_problem(40, 33, seed=5)
+    Y, res = solve(sy, A, B, C, isgn=-1, transa=True, transb=True)
+    assert res.info == 0
+    ref = orc.kron_solve(A, B, C, transa=True, transb=True, isgn=-1)
+    assert rel(Y, ref) <= 1e-12
+
+
+def test_sign_variant_mixed_precision(orc, sy):
+    A, B, C, Bg = signed_problem(300, 260, seed=8)
+    Y, res = solve(sy, A, B, C, isgn=-1, precision="fp32_refine")
+    Y64, _ = solve(sy, A, B, C, isgn=-1)
+    assert res.info == 0 and res.iters >= 1
+    assert rel(Y, Y64) <= 1e-12
+
+
+def test_sign_variant_batched(sy):
+    probs = [signed_problem(m, n, seed=i) for i, (m, n) in enumerate([(20, 30), (64, 17), (100, 100), (33, 95)])]
+    As = [dev(p[0]) for p in probs]
+    Bs = [dev(p[1]) for p in probs]
+    Cs = [dev(p[2]) for p in probs]
+    Ys, res = sy.batch_solve(As, Bs, Cs, isgn=-1)
+    torch.cuda.synchronize()
+    for (A, B, C, _), Yb, r in zip(probs, Ys, res):
+        Y, r1 = solve(sy, A, B, C, isgn=-1)
+        assert r.info == 0 and r.log2scale == r1.log2scale
+        assert np.array_equal(Yb.cpu().numpy(), Y)
+
+
+def test_sign_variant_adjoint(orc, sy):
+    """dA, dB, dC of L = sum(W Y) for A Y - Y B = C against the oracle's Kronecker
+    gradient of the signed equation."""
+    rng = np.random.default_rng(3)
+    m, n = 9, 7
+    A, B, C, _ = signed_problem(m, n, seed=21)
+    W = rng.uniform(-1, 1, (m, n))
+    Ad, Bd = dev(A), dev(B)
+    Y = dev(C).clone()
+    o = sy.make_opts(isgn=-1)
+    res = sy.sylv_result()
+    rc = sy.sylv_tri_solve_ex(m, n, Ad.data_ptr(), m, Bd.data_ptr(), n, Y.data_ptr(), m, o, res)
+    assert rc == 0 and res.log2scale == 0
+    G = dev(W).clone()
+    dA = torch.zeros((m, m), dtype=torch.float64, device="cuda").t()
+    dB = torch.zeros((n, n), dtype=torch.float64, device="cuda").t()
+    r2 = sy.sylv_result()
+    rc = sy.sylv_tri_solve_backward(m, n, Ad.data_ptr(), m, Bd.data_ptr(), n, Y.data_ptr(), m, res.log2scale,
+                                    G.data_ptr(), m, dA.data_ptr(), m, dB.data_ptr(), n, o, r2)
+    torch.cuda.synchronize()
+    assert rc == 0
+    rA, rB, rC, X = orc.kron_grad(A, B, C, W, isgn=-1)
+    assert rel(Y.cpu().numpy(), X) <= 1e-12
+    assert rel(G.cpu().numpy(), rC) <= 1e-12
+    assert rel(dA.cpu().numpy(), rA) <= 1e-11
+    assert rel(dB.cpu().numpy(), rB) <= 1e-11
+
+
+@pytest.mark.parametrize("sms", [1, 3, 17])
+def test_sm_cap_is_bitwise_identical(sy, sms):
+    """Capping the persistent grid changes which CTA owns which tile, never the order
+    of a tile's updates: the solution is bitwise the uncapped one."""
+    A, B, C = inputs.problem(300, 260, seed=31, kind="growth", upper=4.0)
+    Y, res = solve(sy, A, B, C)
+    Yc, resc = solve(sy, A, B, C, max_sms=sms)
+    assert res.info == resc.info and res.log2scale == resc.log2scale
+    assert np.array_equal(Y, Yc)
+
+
+def test_option_validation(sy):
+    o = sy.make_opts()
+    o.isgn = 2
+    d = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
+    res = sy.sylv_result()
+    p = d.data_ptr()
+    assert sy.sylv_tri_solve_ex(4, 4, p, 4, p, 4, p, 4, o, res) == sy.SYLV_ERR_UNSUPPORTED
+    o.isgn = 1
+    o.max_sms = -1
+    assert sy.sylv_tri_solve_ex(4, 4, p, 4, p, 4, p, 4, o, res) == sy.SYLV_ERR_UNSUPPORTED

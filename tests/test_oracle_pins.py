@@ -328,3 +328,38 @@ def test_residual_matrix_diagonal_closed_form(orc):
     ref = C - (a[:, None] + b[None, :]) * X  # three roundings in binary64
     bound = 4 * 2.0 ** -53 * (np.abs(a[:, None] + b[None, :]) * np.abs(X) + np.abs(C))
     assert np.all(np.abs(R - ref) <= bound)
+
+
+def test_kron_sign_variant_against_definition(orc):
+    """isgn = -1: the Kronecker solve satisfies A X - X B = C entry by entry, and equals
+    the isgn = +1 solve with -B (the two forms of the same equation)."""
+    rng = np.random.default_rng(12)
+    m, n = 7, 5
+    A = orc.quasi_tri(np.triu(rng.uniform(-1, 1, (m, m)), 0) + np.diag(rng.uniform(1, 3, m)))
+    B = orc.quasi_tri(np.triu(rng.uniform(-1, 1, (n, n)), 0) - np.diag(rng.uniform(1, 3, n)))
+    B[2, 1] = 0.5
+    C = rng.uniform(-1, 1, (m, n))
+    X = orc.kron_solve(A, B, C, isgn=-1)
+    assert np.allclose(A @ X - X @ np.triu(B, -1), C, rtol=0, atol=1e-13)
+    assert np.allclose(X, orc.kron_solve(A, -B, C), rtol=0, atol=1e-14)
+
+
+def test_kron_grad_sign_variant_fd(orc):
+    """Gradients of L = sum(W X) for A X - X B = C against central differences."""
+    rng = np.random.default_rng(13)
+    m, n = 4, 3
+    A = np.triu(rng.uniform(-1, 1, (m, m)), 1) + np.diag(rng.uniform(1, 2, m))
+    B = np.triu(rng.uniform(-1, 1, (n, n)), 1) - np.diag(rng.uniform(1, 2, n))
+    C, W = rng.uniform(-1, 1, (m, n)), rng.uniform(-1, 1, (m, n))
+    dA, dB, dC, _ = orc.kron_grad(A, B, C, W, isgn=-1)
+    L = lambda A_, B_, C_: float(np.sum(W * orc.kron_solve(A_, B_, C_, isgn=-1)))  # noqa: E731
+    h = 1e-6
+    for (M, D) in ((A, dA), (B, dB), (C, dC)):
+        for (i, j) in [(0, 0), (0, M.shape[1] - 1), (M.shape[0] - 1, M.shape[1] - 1)]:
+            Mp, Mm = M.copy(), M.copy()
+            Mp[i, j] += h
+            Mm[i, j] -= h
+            args_p = [Mp if M is X else X for X in (A, B, C)]
+            args_m = [Mm if M is X else X for X in (A, B, C)]
+            fd = (L(*args_p) - L(*args_m)) / (2 * h)
+            assert abs(fd - D[i, j]) <= 1e-7 * max(1.0, abs(fd))

@@ -244,6 +244,50 @@ int sylv_tri_solve_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, c
                            sylv_result* result);
 
 /*
+ * sylv_tri_solve_triangular -- the robust triangular solve op(A) X = alpha C with
+ * alpha in (0,1] a power of two chosen so that no intermediate exceeds Omega: the
+ * solver with the B term removed (the robust triangular solver the paper builds on,
+ * Sec. 2.1, and Algorithm 4 restricted to column updates).  Tiles of X depend only
+ * on the tiles below them in the same column, so every column block proceeds in
+ * parallel and the tile DAG has p levels instead of p + q - 1.
+ *   m, n      order of A and number of right-hand sides (m, n >= 0)
+ *   A, lda    device, m x m upper quasi-triangular (upper triangle + the first
+ *             subdiagonal of its 2x2 blocks), read only; op(A) = A^T when
+ *             opts->transa = 1
+ *   C, ldc    device, m x n; on exit X
+ *   opts      as for sylv_tri_solve_ex; precision SYLV_FP64 or SYLV_FP64_NONROBUST
+ *             (SYLV_FP32_REFINE and transb are rejected with SYLV_ERR_UNSUPPORTED),
+ *             isgn is ignored
+ *   result    as for sylv_tri_solve_ex (host record in sync mode, device address
+ *             otherwise)
+ * Returns as sylv_tri_solve_ex; -1..-6 name the bad argument.
+ */
+int sylv_tri_solve_triangular(int64_t m, int64_t n, const double* A, int64_t lda, double* C, int64_t ldc,
+                              const sylv_opts* opts, sylv_result* result);
+
+/*
+ * sylv_solve_schur -- the Bartels-Stewart wrapper around the robust solve (Sec. 1,
+ * eqs. (3)-(5)): given real Schur forms A = U TA U^T and B = V TB V^T (U, V
+ * orthogonal, TA, TB upper quasi-triangular, from an external eigensolver), solve
+ *     A X + isgn X B = alpha C
+ * as C~ = U^T C V, TA Y + isgn Y TB = alpha C~ (sylv_tri_solve_ex), X = U Y V^T.  The
+ * four products are plain dense GEMMs (cuBLAS); the solve is the library's.
+ *   U, ldu    device, m x m orthogonal, read only
+ *   TA, ldta  device, m x m upper quasi-triangular, read only
+ *   V, ldv    device, n x n orthogonal, read only
+ *   TB, ldtb  device, n x n upper quasi-triangular, read only
+ *   C, ldc    device, m x n; on exit X
+ *   opts      as for sylv_tri_solve_ex (transa/transb must be 0; the workspace, if
+ *             given, must also hold an m x n double matrix: sylv_workspace_size +
+ *             8 m n bytes rounded up to 256)
+ *   result    as for sylv_tri_solve_ex
+ * Returns as sylv_tri_solve_ex; -3/-4 U, -7/-8 V, -5/-6 TA, -9/-10 TB, -11/-12 C.
+ */
+int sylv_solve_schur(int64_t m, int64_t n, const double* U, int64_t ldu, const double* TA, int64_t ldta,
+                     const double* V, int64_t ldv, const double* TB, int64_t ldtb, double* C, int64_t ldc,
+                     const sylv_opts* opts, sylv_result* result);
+
+/*
  * sylv_residual -- R = C - (A X + X B) to binary64 accuracy, the residual of
  * eq. (7) with alpha = 1 that the refinement of SYLV_FP32_REFINE evaluates for its
  * first correction (Sec. 2 defines the equation; the residual is the numerator of

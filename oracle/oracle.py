@@ -16,6 +16,8 @@ Contents, each written from the paper (Schwarz & Kjelgaard Mikkelsen 2019):
                       power-of-two shift so that tiny alpha or huge Y cannot
                       under/overflow it.
   * ``smin_of``    -- the pivot floor for near-singular small systems.
+  * ``schur_solve``-- the Bartels-Stewart reduction of Sec. 1 (eqs. (3)-(5)) around
+                      ``trsyl``: U^T C V, the triangular solve, U Y V^T (numpy GEMMs).
   * ``residual_matrix`` -- R = C - (A X + X B) from its definition (eq. (7) with
                       alpha = 1) in extended precision, and ``residual_matrix_exact``
                       in exact rational arithmetic for tiny cases.
@@ -297,3 +299,12 @@ def residual_matrix_exact(A, B, X, C) -> np.ndarray:
                 acc -= F(X[i, k]) * F(B[k, j])
             R[i, j] = float(acc)
     return R
+
+
+def schur_solve(U, TA, V, TB, C, isgn: int = 1):
+    """X and log2(alpha) with A X + isgn X B = alpha C for A = U TA U^T, B = V TB V^T
+    (Sec. 1, eqs. (3)-(5)): C~ = U^T C V, TA Y + isgn Y TB = alpha C~, X = U Y V^T."""
+    U, TA, V, TB, C = (np.asarray(t, dtype=np.float64) for t in (U, TA, V, TB, C))
+    Ct = U.T @ C @ V
+    out = trsyl(TA, TB if isgn >= 0 else -TB, Ct)
+    return U @ out["Y"] @ V.T, out["log2scale"]

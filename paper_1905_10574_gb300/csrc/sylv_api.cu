@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include <cublas_v2.h>
+
 #include "sylv_gemm.cuh"
 #include "sylv_internal.cuh"
 #include "sylv_launch.h"
@@ -334,6 +336,7 @@ struct Opts {
   int transa, transb, precision, tile, maxit, sync;
   int isgn;     // +1 or -1: sign of the B term
   int max_sms;  // 0: all SMs
+  int nob;      // 1: no B term (the robust triangular solve op(A) X = alpha C)
   double omega, tol;
   int64_t timeout_ns;
   cudaStream_t stream;
@@ -448,6 +451,7 @@ int enqueue_fp64(const SolvePlan& P, char* ws, const double* A, int64_t lda, con
   Work w = make_work(ws, L, 1, o.timeout_ns);
   if (cudaMemsetAsync(ws + L.zero_lo, 0, L.zero_hi - L.zero_lo, s) != cudaSuccess) return SYLV_ERR_CUDA;
   std::vector<Inst> I = make_insts({P.shape}, L, {A}, {lda}, {B}, {ldb}, {C}, {ldc}, robust ? 1 : 0, o.omega);
+  I[0].nob = o.nob;
   k_set_inst<<<1, 1, 0, s>>>(w.inst, I[0]);
   cudaError_t e = run_prep<double>(w, L, 1, std::max(P.shape.m, P.shape.n), std::max(P.shape.pmax, P.shape.qmax), s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
@@ -752,6 +756,103 @@ int sylv_tri_solve_ex(int64_t m, int64_t n, const double* A, int64_t lda, const 
   if (oc) return oc;
   if (o.sync) return solve_impl(m, n, A, lda, B, ldb, C, ldc, o, result, nullptr);
   return solve_impl(m, n, A, lda, B, ldb, C, ldc, o, nullptr, result);
+}
+
+int sylv_tri_solve_triangular(int64_t m, int64_t n, const double* A, int64_t lda, double* C, int64_t ldc,
+                              const sylv_opts* opts, sylv_result* result) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (m > 0 && !A) return -3;
+  if (lda < (m > 1 ? m : 1)) return -4;
+  if (m > 0 && n > 0 && !C) return -5;
+  if (ldc < (m > 1 ? m : 1)) return -6;
+  if (m > kMaxScanN || n > kMaxScanN) return SYLV_ERR_UNSUPPORTED;
+  Opts o{};
+  const int oc = read_opts(opts, &o);
+  if (oc) return oc;
+  if (o.precision == SYLV_FP32_REFINE || o.transb) return SYLV_ERR_UNSUPPORTED;
+  o.isgn = 1;
+  o.nob = 1;
+  if (o.sync) return solve_impl(m, n, A, lda, nullptr, 1, C, ldc, o, result, nullptr);
+  return solve_impl(m, n, A, lda, nullptr, 1, C, ldc, o, nullptr, result);
+}
+
+// cuBLAS handle per device (the back-transform's plain GEMMs), created on first use.
+static cublasHandle_t blas_handle(int dev) {
+  static std::mutex mu;
+  static cublasHandle_t h[64] = {};
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!h[dev] && cublasCreate(&h[dev]) != CUBLAS_STATUS_SUCCESS) h[dev] = nullptr;
+  return h[dev];
+}
+
+int sylv_solve_schur(int64_t m, int64_t n, const double* U, int64_t ldu, const double* TA, int64_t ldta,
+                     const double* V, int64_t ldv, const double* TB, int64_t ldtb, double* C, int64_t ldc,
+                     const sylv_opts* opts, sylv_result* result) {
+  const int ac = check_args(m, n, TA, ldta, TB, ldtb, C, ldc);
+  if (ac) return ac == -3 ? -5 : ac == -4 ? -6 : ac == -5 ? -9 : ac == -6 ? -10 : ac == -7 ? -11 : ac == -8 ? -12 : ac;
+  if (m > 0 && !U) return -3;
+  if (ldu < (m > 1 ? m : 1)) return -4;
+  if (n > 0 && !V) return -7;
+  if (ldv < (n > 1 ? n : 1)) return -8;
+  Opts o{};
+  const int oc = read_opts(opts, &o);
+  if (oc) return oc;
+  if (o.transa || o.transb) return SYLV_ERR_UNSUPPORTED;
+  if (m == 0 || n == 0) return solve_impl(m, n, TA, ldta, TB, ldtb, C, ldc, o, o.sync ? result : nullptr,
+                                          o.sync ? nullptr : result);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SYLV_ERR_CUDA;
+  cublasHandle_t h = blas_handle(dev);
+  if (!h || cublasSetStream(h, o.stream) != CUBLAS_STATUS_SUCCESS) return SYLV_ERR_CUDA;
+  // Workspace: W (m x n) for the GEMM intermediates, then the solver's own scratch.
+  Opts os = o;
+  const SolvePlan P = plan_solve(m, n, os);
+  const size_t wbytes = align_up(sizeof(double) * m * n);
+  char* ws = nullptr;
+  if (o.ws) {
+    if (o.ws_bytes < wbytes + P.total || (reinterpret_cast<uintptr_t>(o.ws) & (kAlign - 1))) return SYLV_ERR_WORKSPACE;
+    ws = static_cast<char*>(o.ws);
+  } else {
+    void* p = nullptr;
+    const int rc = get_workspace(wbytes + P.total, &p);
+    if (rc) return rc;
+    ws = static_cast<char*>(p);
+  }
+  double* W = reinterpret_cast<double*>(ws);
+  os.ws = ws + wbytes;
+  os.ws_bytes = P.total;
+  const double one = 1.0, zero = 0.0;
+  const int M = static_cast<int>(m), N = static_cast<int>(n);
+  // C~ = U^T C V (Bartels-Stewart, eqs. (3) and (5)): W = U^T C, C = W V.
+  if (cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, M, N, M, &one, U, static_cast<int>(ldu), C, static_cast<int>(ldc), &zero,
+                  W, M) != CUBLAS_STATUS_SUCCESS ||
+      cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, M, N, N, &one, W, M, V, static_cast<int>(ldv), &zero, C,
+                  static_cast<int>(ldc)) != CUBLAS_STATUS_SUCCESS)
+    return SYLV_ERR_CUDA;
+  // The robust triangular solve in the Schur basis; its result record waits on the device.
+  const bool sync = o.sync != 0;
+  os.sync = 0;
+  sylv_result* res_dev = reinterpret_cast<sylv_result*>(static_cast<char*>(os.ws) + P.L.res);
+  int rc = solve_impl(m, n, TA, ldta, TB, ldtb, C, ldc, os, nullptr, nullptr);
+  if (rc) return rc;
+  // X = U Y V^T: W = U Y, C = W V^T.
+  if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, M, N, M, &one, U, static_cast<int>(ldu), C, static_cast<int>(ldc), &zero,
+                  W, M) != CUBLAS_STATUS_SUCCESS ||
+      cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, M, N, N, &one, W, M, V, static_cast<int>(ldv), &zero, C,
+                  static_cast<int>(ldc)) != CUBLAS_STATUS_SUCCESS)
+    return SYLV_ERR_CUDA;
+  if (!sync) {
+    if (result && cudaMemcpyAsync(result, res_dev, sizeof(sylv_result), cudaMemcpyDeviceToDevice, o.stream) != cudaSuccess)
+      return SYLV_ERR_CUDA;
+    return cuda_status(cudaGetLastError());
+  }
+  sylv_result r{};
+  if (cudaMemcpyAsync(&r, res_dev, sizeof(r), cudaMemcpyDeviceToHost, o.stream) != cudaSuccess) return SYLV_ERR_CUDA;
+  if (cudaStreamSynchronize(o.stream) != cudaSuccess) return SYLV_ERR_CUDA;
+  if (result) *result = r;
+  return r.info;
 }
 
 int sylv_tri_solve(int64_t m, int64_t n, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,

@@ -485,7 +485,8 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
   for (int idx = tid; idx < TT * TT; idx += kThreads) {
     const int r = idx % TT, c = idx / TT;
     Ak[r + c * LDY] = (r < mt && c < mt && r <= c + 1) ? __ldg(&A[(r0 + r) + static_cast<int64_t>(r0 + c) * lda]) : T(0);
-    Bk[r + c * LDY] = (r < nt && c < nt && r <= c + 1) ? __ldg(&B[(c0 + r) + static_cast<int64_t>(c0 + c) * ldb]) : T(0);
+    Bk[r + c * LDY] = (B && r < nt && c < nt && r <= c + 1) ? __ldg(&B[(c0 + r) + static_cast<int64_t>(c0 + c) * ldb])
+                                                             : T(0);
   }
   for (int i = tid; i < TT; i += kThreads) {
     sh.acolmax[i] = 0ull;
@@ -562,13 +563,15 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
     factp[kb * TT + lb] = pack;
   }
   // Wavefront order of the tile's elements: step s holds the blocks (kb, lb) with
-  // (pb-1-kb) + lb = s, the 2x2-by-2x2 blocks first, then the 2-element ones, then
-  // the 1x1 ones, so that a warp's lanes mostly share one dot-product length.
-  const int nsteps = pb + qb - 1;
+  // (pb-1-kb) + lb = s (without a B term, B null: (pb-1-kb) = s, every column at
+  // once), the 2x2-by-2x2 blocks first, then the 2-element ones, then the 1x1 ones,
+  // so that a warp's lanes mostly share one dot-product length.
+  const int lw = B ? 1 : 0;
+  const int nsteps = pb + lw * (qb - 1);
   for (int s = tid; s < nsteps; s += kThreads) {
     int cnt = 0;
-    for (int lb = max(0, s - (pb - 1)); lb <= min(s, qb - 1); ++lb) {
-      const int kb = pb - 1 - (s - lb);
+    for (int lb = lw ? max(0, s - (pb - 1)) : 0; lb <= (lw ? min(s, qb - 1) : qb - 1); ++lb) {
+      const int kb = pb - 1 - (s - lw * lb);
       cnt += (sh.astart[kb + 1] - sh.astart[kb]) * (sh.bstart[lb + 1] - sh.bstart[lb]);
     }
     sh.sstart[s + 1] = static_cast<short>(cnt);
@@ -582,8 +585,8 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
   for (int s = tid; s < nsteps; s += kThreads) {
     int pos = sh.sstart[s];
     for (int want = 4; want >= 1; want >>= 1)
-      for (int lb = max(0, s - (pb - 1)); lb <= min(s, qb - 1); ++lb) {
-        const int kb = pb - 1 - (s - lb);
+      for (int lb = lw ? max(0, s - (pb - 1)) : 0; lb <= (lw ? min(s, qb - 1) : qb - 1); ++lb) {
+        const int kb = pb - 1 - (s - lw * lb);
         const int ra = sh.astart[kb], ma = sh.astart[kb + 1] - ra;
         const int cb0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - cb0;
         if (ma * nb != want) continue;
@@ -616,7 +619,7 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
 // ProtectUpdate.
 template <int TT, typename T, bool ROBUST>
 __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, double smin, const double* gfact,
-                           const int* gfactp) {
+                           const int* gfactp, bool nob) {
   constexpr int LDY = DagSmem<TT, T>::LDY;
   constexpr int CSTEP = kThreads / TT;
   constexpr int NC = TT / CSTEP;  // columns owned per thread
@@ -630,6 +633,9 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
   const int pb = sh.pb, qb = sh.qb;
   const double omh = 0.5 * omega;
   const int eo = floor_log2(omh);
+  // Without a B term (nob) the columns are independent: step s solves block row
+  // pb-1-s in every column block, and no element takes a B-side contribution.
+  const int lw = nob ? 0 : 1;
 
   // Element ownership: row tid % TT, columns tid / TT + j * CSTEP (j < NC).
   const int my_r = tid % TT;
@@ -686,7 +692,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
   }
   bool near = false;
   int local_scale_events = 0;
-  const int nsteps = pb + qb - 1;
+  const int nsteps = pb + lw * (qb - 1);
   for (int s = 0; s < nsteps; ++s) {
     // Phase C's coefficients do not depend on this step's solutions: the binary32
     // tile-32 kernel (latency bound, with registers to spare) fetches them now, while
@@ -696,7 +702,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
     constexpr bool kPre = sizeof(T) == 4 && TT <= 32;
     constexpr int NP = kPre ? NC : 1;
     const int lbs = s - dr;
-    const bool bs_ok = row_ok && lbs >= 0 && lbs < qb;
+    const bool bs_ok = lw && row_ok && lbs >= 0 && lbs < qb;
     int cs0 = 0, nbs = 0;
     if (bs_ok) {
       cs0 = sh.bstart[lbs];
@@ -710,10 +716,10 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
       for (int j = 0; j < NC; ++j) {
         const int c = my_c0 + j * CSTEP;
         const int lbc = lbcj[j];
-        const int ia = s - lbc;
+        const int ia = s - lw * lbc;
         ca0[j] = ca1[j] = cb0[j] = cb1[j] = T(0);
         rsj[j] = 0;
-        if (okj[j] && dr + lbc > s) {
+        if (okj[j] && dr + lw * lbc > s) {
           if (ia >= 0 && ia < dr) {
             const int kbs = pb - 1 - ia;
             const int rs0 = sh.astart[kbs];
@@ -813,8 +819,8 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
       sh.pma[lb] = static_cast<short>(ma);
     }
     __syncthreads();
-    const int lb_lo = max(0, s - (pb - 1));
-    const int lb_hi = min(s, qb - 1);
+    const int lb_lo = lw ? max(0, s - (pb - 1)) : 0;
+    const int lb_hi = lw ? min(s, qb - 1) : qb - 1;
     int g = 0;
     if (ROBUST && sh.slow) {
       // Phase B (rare): exact tile-wide factor of this step.
@@ -824,7 +830,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
         emin = warp_min(emin);
         double zs = 0.0, as = 0.0, bs = 0.0;
         for (int lb = lb_lo + lane; lb <= lb_hi; lb += 32) {
-          const int kb = pb - 1 - (s - lb);
+          const int kb = pb - 1 - (s - lw * lb);
           const int r0 = sh.astart[kb], ma = sh.astart[kb + 1] - r0;
           const int c0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - c0;
           double zm = 0.0;
@@ -856,7 +862,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
         for (int lb = lb_lo + lane; lb <= lb_hi; lb += 32) {
           const int sc = gg - sh.pe[lb];
           if (sc != 0) {
-            const int kb = pb - 1 - (s - lb);
+            const int kb = pb - 1 - (s - lw * lb);
             const int r0 = sh.astart[kb], ma = sh.astart[kb + 1] - r0;
             const int c0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - c0;
             for (int jj = 0; jj < nb; ++jj)
@@ -883,7 +889,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
     for (int j = 0; j < NC; ++j) {
       const int c = my_c0 + j * CSTEP;
       const int lbc = lbcj[j];
-      const int dd = dr + lbc;
+      const int dd = dr + lw * lbc;
       if (!okj[j]) continue;
       if (dd < s) {
         if (g != 0) {  // solved earlier: rescale in place (rare)
@@ -903,7 +909,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
             if (nbs == 2) y = fma(-zb1, cb1[j], y);
           }
         } else {
-          const int ia = s - lbc;
+          const int ia = s - lw * lbc;
           if (ia >= 0 && ia < dr) {  // block of column block lbc solved now, below this row
             const int rs0 = sh.pr0[lbc];
             y = fma(-Ak[my_r + rs0 * LDY], Ys[rs0 + c * LDY], y);
@@ -1055,7 +1061,7 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
 
     double* fact = w.fact + static_cast<int64_t>(blockIdx.x) * w.fact_stride;
     int* factp = w.factp + static_cast<int64_t>(blockIdx.x) * TT * TT;
-    diag_prepare<TT, T, ROBUST>(sh, A, I.lda, B, I.ldb, r0, c0, mt, nt, st->smin, fact, factp);
+    diag_prepare<TT, T, ROBUST>(sh, A, I.lda, I.nob ? nullptr : B, I.ldb, r0, c0, mt, nt, st->smin, fact, factp);
 
     // ---- accumulator <- C_kl, exact infinity norm.  In binary32 the accumulator
     // is compensated: every group's product is summed into a fresh partial and the
@@ -1117,8 +1123,10 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
     // arithmetic to one at a time) as long as no scaling is needed -- when a group
     // member's exponent differs from the accumulator's or the bounds come near
     // omega, the group shrinks to one producer with the exact ProtectUpdate.
-    const int d = (p - 1 - k) + l;
-    const int a0 = l, b0 = p - 1 - k;
+    // Without a B term (nob) only the tiles below contribute: d = p-1-k, all on the A side.
+    const int lq = I.nob ? 0 : l;
+    const int d = (p - 1 - k) + lq;
+    const int a0 = lq, b0 = p - 1 - k;
     const int lo = min(a0, b0), hi = max(a0, b0);
     const int eo = floor_log2(omega);
     auto producer = [&](int q, int& side, int& prod, int& kdim) {
@@ -1134,7 +1142,7 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
       }
       side = sd;
       if (sd == 0) {
-        const int i = p - 1 + l - sq;  // A side: Y_kl -= A_ki Y_il
+        const int i = p - 1 + lq - sq;  // A side: Y_kl -= A_ki Y_il
         prod = i * I.qmax + l;
         kdim = rb[i + 1] - rb[i];
       } else {
@@ -1398,11 +1406,12 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
     for (int idx = tid; idx < TT * TT; idx += kThreads) {
       const int r = idx % TT, c = idx / TT;
       sh.L[r + c * LDY] = (r < mt && c < mt && r <= c + 1) ? __ldg(&A[(r0 + r) + (int64_t)(r0 + c) * I.lda]) : T(0);
-      sh.R[r + c * LDY] = (r < nt && c < nt && r <= c + 1) ? __ldg(&B[(c0 + r) + (int64_t)(c0 + c) * I.ldb]) : T(0);
+      sh.R[r + c * LDY] =
+          (!I.nob && r < nt && c < nt && r <= c + 1) ? __ldg(&B[(c0 + r) + (int64_t)(c0 + c) * I.ldb]) : T(0);
     }
     if (w.prio && tid == 0) atomicAdd(w.smbusy + sm_id(), 1);
     __syncthreads();
-    diag_solve<TT, T, ROBUST>(sh, mt, nt, omega, st->smin, fact, factp);
+    diag_solve<TT, T, ROBUST>(sh, mt, nt, omega, st->smin, fact, factp, I.nob != 0);
     if (w.prio && tid == 0) atomicSub(w.smbusy + sm_id(), 1);
 
     // ---- exact norm of the final tile, write back, publish

@@ -30,6 +30,7 @@ struct Inst {
   int32_t t;           // nominal tile size
   int32_t pmax, qmax;  // capacity of the tile arrays (>= actual tile counts)
   int32_t robust;      // 1: Algorithm 4 with scaling; 0: no scaling (Algorithm 1 per tile)
+  int32_t nob;         // 1: no B term, the robust triangular solve op(A) X = alpha C (B unused)
   int64_t rb, cb;      // offsets (ints) of the row/column tile boundaries in Work::ibuf
   int64_t tile;        // offset (elements) of this equation's per-tile arrays
   int64_t an, bn;      // offsets (doubles) of the tile-norm tables in Work::dbuf

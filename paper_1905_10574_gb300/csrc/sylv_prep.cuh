@@ -23,11 +23,13 @@ __global__ void k_scan(Work w) {
   const int64_t N = isA ? I.m : I.n;
   const int64_t ld = isA ? I.lda : I.ldb;
   const T* M = static_cast<const T*>(isA ? I.A : I.B);
+  const bool scan = isA || !I.nob;  // without a B term the columns of C are partitioned freely
   const int64_t nwords = (N + 31) / 32;
   for (int64_t i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = 0u;
   __syncthreads();
-  for (int64_t i = threadIdx.x; i + 1 < N; i += blockDim.x)
-    if (M[(i + 1) + i * ld] != T(0)) atomicOr(&bits[i >> 5], 1u << (i & 31));
+  if (scan)
+    for (int64_t i = threadIdx.x; i + 1 < N; i += blockDim.x)
+      if (M[(i + 1) + i * ld] != T(0)) atomicOr(&bits[i >> 5], 1u << (i & 31));
   __syncthreads();
   for (int64_t wd = threadIdx.x; wd < nwords; wd += blockDim.x) {
     const unsigned x = bits[wd];
@@ -67,6 +69,7 @@ __global__ void k_norms(Work w) {
   const Inst I = w.inst[blockIdx.x];
   InstState* st = &w.st[blockIdx.x];
   const bool isA = blockIdx.z == 0;
+  if (!isA && I.nob) return;
   const int ntile = isA ? st->p : st->q;
   const int rt = blockIdx.y;
   if (rt >= ntile || st->err) return;
@@ -114,6 +117,7 @@ __global__ void k_norms(Work w) {
 // levels, so ticket order is a topological order).  Also sets the pivot floor
 // smin = max(2^-52 max(|A|,|B|), 2^-1022).
 __global__ void k_level_count(Work w) {
+  const int lw = w.inst[blockIdx.x].nob ? 0 : 1;  // without a B term a tile waits only on the tiles below it
   InstState* st = &w.st[blockIdx.x];
   if (threadIdx.x == 0) {
     const double amax = __longlong_as_double(static_cast<long long>(st->amax));
@@ -124,7 +128,7 @@ __global__ void k_level_count(Work w) {
   const int p = st->p, q = st->q;
   for (int t = threadIdx.x; t < p * q; t += blockDim.x) {
     const int k = t / q, l = t % q;
-    atomicAdd(&w.lvl_cnt[(p - 1 - k) + l], 1);
+    atomicAdd(&w.lvl_cnt[(p - 1 - k) + lw * l], 1);
   }
 }
 
@@ -148,7 +152,7 @@ __global__ void k_level_scatter(Work w) {
   const int p = st->p, q = st->q;
   for (int t = threadIdx.x; t < p * q; t += blockDim.x) {
     const int k = t / q, l = t % q;
-    const int d = (p - 1 - k) + l;
+    const int d = (p - 1 - k) + (I.nob ? 0 : l);
     const int pos = atomicAdd(&w.lvl_cur[d], 1);
     w.tasks[w.lvl_off[d] + pos] = Task{static_cast<int32_t>(blockIdx.x), k * I.qmax + l};
   }
@@ -184,6 +188,7 @@ __global__ void __launch_bounds__(256) k_pack(Work w, int tt) {
         dst[idx] = (r < mt && kk < kd) ? A[(r0 + r) + static_cast<int64_t>(k0 + kk) * I.lda] : T(0);
       }
     } else {
+      if (I.nob) break;  // no B term
       const int64_t s2 = sidx - na;
       const int j = static_cast<int>(s2 / q), l = static_cast<int>(s2 % q);
       if (l <= j) continue;

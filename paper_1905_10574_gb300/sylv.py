@@ -83,6 +83,10 @@ SIGNATURES = {
     "sylv_version": (ctypes.c_char_p, []),
     "sylv_diag_wait_timeout": (ctypes.c_int, [_i64, _vp]),
     "sylv_residual": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _vp]),
+    "sylv_tri_solve_triangular": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, ctypes.POINTER(sylv_opts),
+                                                 _vp]),
+    "sylv_solve_schur": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _pd, _i64,
+                                        ctypes.POINTER(sylv_opts), _vp]),
     "sylv_tri_solve_noalloc": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _i64, _vp,
                                               ctypes.POINTER(sylv_result)]),
     "sylv_tri_solve_backward_batched": (ctypes.c_int, [_i32, _P64, _P64, _PP, _P64, _PP, _P64, _PP, _P64, _P64, _PP,
@@ -164,6 +168,62 @@ def sylv_tri_solve_noalloc(m, n, A, lda, B, ldb, C, ldc, tile=0, stream=None):
     res = sylv_result()
     rc = load().sylv_tri_solve_noalloc(m, n, A, lda, B, ldb, C, ldc, tile, stream, ctypes.byref(res))
     return rc, res
+
+
+def sylv_tri_solve_triangular(m, n, A, lda, C, ldc, opts: sylv_opts | None = None, result=None) -> int:
+    """Device pointers (ints).  Robust op(A) X = alpha C; ``result``: a sylv_result (host,
+    sync mode) or a device address (async mode).  Returns the status code."""
+    o = opts if opts is not None else sylv_default_opts()
+    if isinstance(result, sylv_result):
+        res = ctypes.cast(ctypes.pointer(result), ctypes.c_void_p)
+    else:
+        res = result
+    return load().sylv_tri_solve_triangular(m, n, A, lda, C, ldc, ctypes.byref(o), res)
+
+
+def sylv_solve_schur(m, n, U, ldu, TA, ldta, V, ldv, TB, ldtb, C, ldc, opts: sylv_opts | None = None,
+                     result=None) -> int:
+    """Device pointers (ints).  A X + isgn X B = alpha C from real Schur forms
+    A = U TA U^T, B = V TB V^T; ``result`` as for sylv_tri_solve_ex."""
+    o = opts if opts is not None else sylv_default_opts()
+    if isinstance(result, sylv_result):
+        res = ctypes.cast(ctypes.pointer(result), ctypes.c_void_p)
+    else:
+        res = result
+    return load().sylv_solve_schur(m, n, U, ldu, TA, ldta, V, ldv, TB, ldtb, C, ldc, ctypes.byref(o), res)
+
+
+def schur_solve(U, TA, V, TB, C, *, precision="fp64", tile=0, isgn=1, check=True):
+    """A X + isgn X B = alpha C for CUDA float64 tensors given A = U TA U^T and
+    B = V TB V^T (real Schur forms); returns (X, Result) with X column-major."""
+    torch = _torch()
+    U, TA, V, TB = (fortran(t) for t in (U, TA, V, TB))
+    X = fortran(C).clone()
+    m, n = X.shape
+    o = make_opts(precision=precision, tile=tile, isgn=isgn,
+                  stream=torch.cuda.current_stream(X.device).cuda_stream, sync=True)
+    res = sylv_result()
+    rc = sylv_solve_schur(m, n, U.data_ptr(), _ld(U), TA.data_ptr(), _ld(TA), V.data_ptr(), _ld(V), TB.data_ptr(),
+                          _ld(TB), X.data_ptr(), _ld(X), o, res)
+    if check and (rc >= 100 or rc < 0):
+        raise SylvError(rc, "sylv_solve_schur")
+    return X, Result(**res.as_dict())
+
+
+def triangular_solve(A, C, *, transa=False, precision="fp64", tile=0, omega=0.0, check=True):
+    """Robust op(A) X = alpha C for CUDA float64 tensors (A upper quasi-triangular);
+    returns (X, Result) with X column-major."""
+    torch = _torch()
+    A = fortran(A)
+    X = fortran(C).clone()
+    m, n = X.shape
+    o = make_opts(transa=transa, precision=precision, tile=tile, omega=omega,
+                  stream=torch.cuda.current_stream(X.device).cuda_stream, sync=True)
+    res = sylv_result()
+    rc = sylv_tri_solve_triangular(m, n, A.data_ptr(), _ld(A), X.data_ptr(), _ld(X), o, res)
+    if check and (rc >= 100 or rc < 0):
+        raise SylvError(rc, "sylv_tri_solve_triangular")
+    return X, Result(**res.as_dict())
 
 
 def sylv_residual(m, n, A, lda, B, ldb, X, ldx, C, ldc, R, ldr, stream=None) -> int:

@@ -140,3 +140,54 @@ def test_option_validation(sy):
     o.isgn = 1
     o.max_sms = -1
     assert sy.sylv_tri_solve_ex(4, 4, p, 4, p, 4, p, 4, o, res) == sy.SYLV_ERR_UNSUPPORTED
+
+
+def tri_solve(sy, A, C, **kw):
+    X, res = sy.triangular_solve(dev(A), dev(C), **kw)
+    torch.cuda.synchronize()
+    return X.cpu().numpy(), res
+
+
+@pytest.mark.parametrize("m,n,tile", [(70, 5, 32), (257, 1, 32), (130, 200, 24), (33, 64, 0), (400, 37, 64)])
+def test_triangular_solve(orc, sy, m, n, tile):
+    A, _, C = inputs.problem(m, n, seed=m + 7 * n, kind="wellcond")
+    X, res = tri_solve(sy, A, C, tile=tile)
+    assert res.info == 0 and res.log2scale == 0
+    ref = orc.trsyl(A, np.zeros((n, n)), C)
+    assert rel(X, ref["Y"]) <= 1e-12
+    assert rel(X, np.linalg.solve(np.triu(A, -1), C)) <= 1e-11
+
+
+def test_triangular_solve_transposed(orc, sy):
+    A, _, C = inputs.problem(150, 20, seed=4, kind="wellcond")
+    X, res = tri_solve(sy, A, C, transa=True)
+    assert res.info == 0
+    assert rel(X, orc.trsyl(A, np.zeros((20, 20)), C, transa=True)["Y"]) <= 1e-12
+
+
+def test_triangular_solve_scaling(orc, sy):
+    """Growth past the binary64 range: the robust solve scales (alpha < 1, finite X,
+    Y/alpha equal to the oracle's after a common power-of-two shift), the plain one
+    overflows."""
+    A, _, C = inputs.problem(500, 12, seed=2, kind="growth", upper=200.0)  # oracle: alpha = 2^-613
+    X, res = tri_solve(sy, A, C)
+    ref = orc.trsyl(A, np.zeros((12, 12)), C)
+    assert res.info in (0, 2) and res.log2scale < 0 and ref["log2scale"] < 0
+    assert np.all(np.isfinite(X)) and np.max(np.abs(X)) <= 2.0 ** 1020
+    Xs = np.ldexp(X, int(ref["log2scale"]) - int(res.log2scale))
+    s = np.max(np.abs(ref["Y"]))  # entries near 2^1016: normalise before the norm
+    assert rel(Xs / s, ref["Y"] / s) <= 1e-12
+    _, res_nr = tri_solve(sy, A, C, precision="fp64_nonrobust", check=False)
+    assert res_nr.info == sy.SYLV_OVERFLOWED
+
+
+def test_triangular_solve_arguments(sy):
+    d = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
+    p = d.data_ptr()
+    res = sy.sylv_result()
+    assert sy.sylv_tri_solve_triangular(-1, 4, p, 4, p, 4, None, res) == -1
+    assert sy.sylv_tri_solve_triangular(4, 4, 0, 4, p, 4, None, res) == -3
+    assert sy.sylv_tri_solve_triangular(4, 4, p, 4, p, 2, None, res) == -6
+    o = sy.make_opts(precision="fp32_refine")
+    assert sy.sylv_tri_solve_triangular(4, 4, p, 4, p, 4, o, res) == sy.SYLV_ERR_UNSUPPORTED
+    assert sy.sylv_tri_solve_triangular(0, 4, p, 1, p, 1, None, res) == 0

@@ -363,3 +363,36 @@ def test_kron_grad_sign_variant_fd(orc):
             args_m = [Mm if M is X else X for X in (A, B, C)]
             fd = (L(*args_p) - L(*args_m)) / (2 * h)
             assert abs(fd - D[i, j]) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_triangular_solve_is_sylvester_with_zero_b(orc):
+    """The robust triangular solve op(A) X = alpha C is Algorithm 2 with B = 0: the
+    oracle's solve with a zero B agrees with dense LU on a quasi-triangular A."""
+    rng = np.random.default_rng(14)
+    m, n = 11, 4
+    A = np.triu(rng.uniform(-1, 1, (m, m)), 1) + np.diag(rng.uniform(1, 3, m))
+    A[4, 3], A[3, 4], A[4, 4] = -0.9, 1.1, A[3, 3]  # a 2x2 block at rows 3-4
+    C = rng.uniform(-1, 1, (m, n))
+    out = orc.trsyl(A, np.zeros((n, n)), C)
+    assert out["info"] == 0 and out["log2scale"] == 0
+    assert np.allclose(out["Y"], np.linalg.solve(orc.quasi_tri(A), C), rtol=0, atol=1e-13)
+    outT = orc.trsyl(A, np.zeros((n, n)), C, transa=True)
+    assert np.allclose(outT["Y"], np.linalg.solve(orc.quasi_tri(A).T, C), rtol=0, atol=1e-13)
+
+
+def test_schur_solve_against_dense_sylvester(orc):
+    """The Bartels-Stewart form around the oracle's triangular solve matches scipy's
+    dense Sylvester solver on A = U TA U^T, B = V TB V^T (real Schur forms from scipy)."""
+    sla = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(15)
+    m, n = 9, 6
+    A = rng.standard_normal((m, m)) + 4 * np.eye(m)
+    B = rng.standard_normal((n, n)) + 4 * np.eye(n)
+    C = rng.standard_normal((m, n))
+    TA, U = sla.schur(A, output="real")
+    TB, V = sla.schur(B, output="real")
+    X, e = orc.schur_solve(U, TA, V, TB, C)
+    assert e == 0
+    assert np.allclose(X, sla.solve_sylvester(A, B, C), rtol=0, atol=1e-12)
+    Xm, _ = orc.schur_solve(U, TA, V, -TB, C, isgn=-1)
+    assert np.allclose(Xm, X, rtol=0, atol=1e-14)

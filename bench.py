@@ -50,10 +50,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--workload", default=None, help="named synthetic workload (each mode has its default)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--tile", type=int, default=0, help="override the workload's tile size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sms", default="", help="smscale mode: comma-separated SM counts")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (mixed precision, batched, adjoint)")
     ap.add_argument("--mode", default="solve", choices=["solve", "mixed", "batched", "adjoint", "smscale"],
@@ -341,7 +342,7 @@ def run_mixed(args):
     import torch
     from paper_1905_10574_gb300 import build, inputs, sylv
     build.build()
-    name = args.workload if args.workload != WORKLOAD else "wellcond_8000"
+    name = args.workload or "wellcond_8000"
     A, B, C, w = inputs.workload(name)
     m, n = w["m"], w["n"]
     dev = torch.device("cuda", 0)
@@ -377,12 +378,14 @@ def run_mixed(args):
 
 def run_smscale(args):
     """SM scaling of the robust FP64 solve (the GPU analogue of the paper's core-scaling
-    study, Sec. 4): the persistent tile kernel capped at N SMs (2 CTAs each), the
-    rest of the solve unchanged.  Efficiency = T(1 SM) / (N * T(N SMs))."""
+    study, Sec. 4): the persistent tile kernel restricted to the SMs with id < N (2 CTAs
+    each), the rest of the solve unchanged.  Efficiency = N0 T(N0 SMs) / (N T(N SMs)),
+    N0 the smallest count measured (1 by default; --sms picks the counts).  The
+    uncapped solve is timed last, as a check that the cap at N = #SMs loses no SM."""
     import torch
     from paper_1905_10574_gb300 import build, inputs, sylv
     build.build()
-    name = args.workload if args.workload != WORKLOAD else "benign_1000"
+    name = args.workload or "benign_1000"
     A, B, C, w = inputs.workload(name)
     m, n = w["m"], w["n"]
     dev = torch.device("cuda", 0)
@@ -390,13 +393,15 @@ def run_smscale(args):
     stream = torch.cuda.current_stream(dev)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     rows = []
-    for sms in [1, 2, 4, 8, 19, 38, 76, nsm]:
+    sm_list = [int(x) for x in args.sms.split(",")] if args.sms else [1, 2, 4, 8, 19, 38, 76, nsm]
+    uncapped = None
+    for sms in sm_list + [0]:
         opts = sylv.make_opts(tile=args.tile or w["tile"], stream=stream.cuda_stream, sync=True, max_sms=sms)
         wsb = sylv.sylv_workspace_size(m, n, opts)
         wsbuf = torch.empty(wsb + 256, dtype=torch.uint8, device=dev)
         opts.workspace = (wsbuf.data_ptr() + 255) // 256 * 256
         opts.workspace_bytes = wsb
-        steps = 2 if sms < 8 else args.steps
+        steps = 2 if 0 < sms < 8 else args.steps
         Cs = [C0.clone() for _ in range(1 + steps)]
         res = sylv.sylv_result()
 
@@ -407,15 +412,21 @@ def run_smscale(args):
                 raise sylv.SylvError(rc, "smscale")
 
         ms, _ = _timed(fn, steps, 1, stream)
-        rows.append({"sms": sms, "ms_per_solve": ms, "gflops_2mnmn": flops_2(m, n) / ms / 1e6})
         del Cs, wsbuf
-    t1 = rows[0]["ms_per_solve"]
+        if sms == 0:
+            uncapped = ms
+            break
+        rows.append({"sms": sms, "ms_per_solve": ms, "gflops_2mnmn": flops_2(m, n) / ms / 1e6,
+                     "log2scale": int(res.log2scale)})
+    t1, s1 = rows[0]["ms_per_solve"], rows[0]["sms"]
     for r in rows:
         r["speedup"] = t1 / r["ms_per_solve"]
-        r["efficiency"] = r["speedup"] / r["sms"]
+        r["efficiency"] = r["speedup"] * s1 / r["sms"]
     return {"metric": "SM-scaling efficiency of the robust FP64 solve", "value": rows[-1]["efficiency"],
             "unit": "fraction", "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "m": m, "n": n, "tile": args.tile or w["tile"]}, "rows": rows}
+            "config": {"workload": name, "m": m, "n": n, "tile": args.tile or w["tile"], "base_sms": s1,
+                       "uncapped_ms_per_solve": uncapped, "sms_on_device": nsm},
+            "rows": rows}
 
 
 def run_batched(args):
@@ -536,7 +547,7 @@ def secondary(args):
     import torch
     out = {}
     sub = _ap.Namespace(**vars(args))
-    sub.workload, sub.tile = WORKLOAD, 0
+    sub.workload, sub.tile = None, 0
     sub.steps, sub.warmup = 2, 1
     for name, fn in (("mixed_precision_8000", run_mixed), ("batched_4096", run_batched),
                      ("adjoint_256x512", run_adjoint)):
@@ -552,6 +563,8 @@ def secondary(args):
 
 def main():
     args = parse()
+    if args.mode == "solve" or args.impl == "reference":
+        args.workload = args.workload or WORKLOAD
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "mixed":

@@ -84,9 +84,10 @@ typedef struct sylv_opts {
   int32_t isgn;            /* sign of the B term: +1 (or 0) solves op(A) Y + Y op(B) = alpha C,
                               -1 solves op(A) Y - Y op(B) = alpha C (LAPACK's ISGN; not in
                               the paper, which treats +1: the solver runs on -B) */
-  int32_t max_sms;         /* cap on the SMs the persistent tile kernel occupies (its grid
-                              is at most 2 * max_sms CTAs); 0 = all.  For SM-scaling
-                              studies (the GPU analogue of Sec. 4's core scaling) */
+  int32_t max_sms;         /* cap on the SMs the persistent tile kernel occupies: its CTAs
+                              on SMs with id >= max_sms leave at once (CTA 0 always runs);
+                              0 = all.  For SM-scaling studies (the GPU analogue of
+                              Sec. 4's core scaling); the solution is bitwise the same */
 } sylv_opts;
 
 typedef struct sylv_result {

@@ -433,8 +433,17 @@ int check_args(int64_t m, int64_t n, const void* A, int64_t lda, const void* B, 
   return SYLV_OK;
 }
 
-// Grid cap of the persistent tile kernel for an SM budget (0: none): two CTAs per SM.
-int cap_ctas(int ctas, int max_sms) { return max_sms > 0 ? std::min(ctas, 2 * max_sms) : ctas; }
+// CTAs of the FP64 tile kernel for one equation.  Two CTAs per SM hide each other's
+// barriers and staging, but they also share the SM's FP64 pipe, which slows the
+// diagonal solves on the critical path.  Measured on GB300 (m = n, tile 32): one CTA
+// per SM is faster up to ~4000 tiles (m = 1000: 7.1 vs 8.7 ms; 1500: 12.3 vs 14.3;
+// 2000: 22.4 vs 22.8), two are faster from ~9000 (3000: 58.4 vs 63.0; 4000: 128 vs
+// 145).  The FP32 correction solves and batches keep two per SM.
+constexpr int kOneCtaPerSmTiles = 6000;
+int fp64_grid(int tiles, int ncta) {
+  const int g = std::min(tiles, ncta);
+  return tiles < kOneCtaPerSmTiles ? std::min(g, sm_count()) : g;
+}
 
 int grid_for(int64_t elems) {
   int64_t g = (elems + 255) / 256;
@@ -455,7 +464,7 @@ int enqueue_fp64(const SolvePlan& P, char* ws, const double* A, int64_t lda, con
   k_set_inst<<<1, 1, 0, s>>>(w.inst, I[0]);
   cudaError_t e = run_prep<double>(w, L, 1, std::max(P.shape.m, P.shape.n), std::max(P.shape.pmax, P.shape.qmax), s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
-  e = launch_dag_f64(P.shape.t, robust, w, cap_ctas(std::min(L.max_tiles, L.ncta), o.max_sms), s);
+  e = launch_dag_f64(P.shape.t, robust, w, fp64_grid(L.max_tiles, L.ncta), s, o.max_sms);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
   k_consistency<double><<<grid_for(static_cast<int64_t>(L.max_tiles) * 256), 256, 0, s>>>(w);
   k_results<<<1, 32, 0, s>>>(w);
@@ -552,9 +561,9 @@ int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, c
     k_to_float<<<grid_for(m * n), 256, 0, s>>>(R, m, Rf, m, m, n, rmax, nullptr, 0, &rs->conv);
     if (it > 0) {
       if (cudaMemsetAsync(w.tflag, 0, sizeof(int32_t) * L.sum_tiles, s) != cudaSuccess) return SYLV_ERR_CUDA;
-      if (cudaMemsetAsync(&w.ctrl->ticket, 0, sizeof(int32_t), s) != cudaSuccess) return SYLV_ERR_CUDA;
+      if (cudaMemsetAsync(&w.ctrl->ticket, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return SYLV_ERR_CUDA;
     }
-    e = launch_dag_f32(P.shape.t, w, cap_ctas(std::min(L.max_tiles, L.ncta), o.max_sms), s);
+    e = launch_dag_f32(P.shape.t, w, std::min(L.max_tiles, L.ncta), s, o.max_sms);
     if (e != cudaSuccess) return SYLV_ERR_CUDA;
     k_accumulate<<<grid_for(static_cast<int64_t>(L.max_tiles) * 256), 256, 0, s>>>(w, X, m, Dlast, rmax, amax, bmax,
                                                                                    dmax, xmax, &rs->conv);
@@ -1017,7 +1026,7 @@ int sylv_batch_execute(sylv_batch_plan* P, void* stream) {
   cudaError_t e = run_prep<double>(P->w, L, P->count, P->maxN, P->pmax_all, s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
   e = launch_dag_f64(P->tt, P->precision == SYLV_FP64, P->w,
-                     cap_ctas(static_cast<int>(std::min<int64_t>(L.sum_tiles, L.ncta)), P->max_sms), s);
+                     static_cast<int>(std::min<int64_t>(L.sum_tiles, L.ncta)), s, P->max_sms);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
   k_consistency<double><<<grid_for(L.sum_tiles * 256), 256, 0, s>>>(P->w);
   k_results<<<(P->count + 255) / 256, 256, 0, s>>>(P->w);

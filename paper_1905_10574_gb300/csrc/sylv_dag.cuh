@@ -48,7 +48,10 @@ struct DagSmem {
   // Small-system inverses in shared memory for tile capacity 32; the tile-64 kernels
   // keep them in the CTA's global slot.
   static constexpr bool kFactSmem = (TT <= 32);
-  double fact[kFactSmem ? 5 * TT * TT : 1];      // inverse store (see pair_offset), if kFactSmem
+  // The stored inverses are kept in the tile's precision: the binary32 kernel solves
+  // its small systems in binary32 (its corrections are refined in binary64 anyway).
+  using FactT = typename std::conditional<kFactSmem, T, double>::type;
+  FactT fact[kFactSmem ? 5 * TT * TT : 1];       // inverse store (see pair_offset), if kFactSmem
   int factp[kFactSmem ? TT * TT : 1];            // per pair: bit 16 = a pivot was raised, if kFactSmem
   unsigned short eord[TT * TT];       // tile elements in wavefront order: row | col << 6 | vec index << 12
   short sstart[2 * TT];               // first entry of each wavefront step in eord
@@ -61,6 +64,7 @@ struct DagSmem {
   int qb2[TT + 1];                    // prefix sums of squared B block sizes
   short rowblk[TT], colblk[TT];       // block index of every row / column of the tile
   short astart[TT + 1], bstart[TT + 1];
+  unsigned apsd, bpsd;                // diagonal solve: blocks that are two merged 1x1 blocks (bit per block)
   unsigned long long umax;
   unsigned long long stage_bar;        // mbarrier of the bulk-copy staging (packed tiles)
   double nb_acc;
@@ -71,6 +75,8 @@ struct DagSmem {
 __device__ __forceinline__ int ub_log2(double v) {
   return static_cast<int>((__double_as_longlong(v) >> 52) & 0x7ff) - 1022;
 }
+// The same for binary32 (2^-126 for zero/subnormals; 129 for infinities and NaNs).
+__device__ __forceinline__ int ub_log2(float v) { return static_cast<int>((__float_as_uint(v) >> 23) & 0xff) - 126; }
 __device__ __forceinline__ unsigned long long abs_bits(double v) {
   return static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7FFFFFFFFFFFFFFFull;
 }
@@ -462,6 +468,132 @@ __device__ inline int scan_blocks(const T* M, int N, short* blk, short* start, i
   return count;
 }
 
+// Pseudo blocks for the diagonal-tile solve (tile capacity <= 32): consecutive 1x1
+// blocks are merged in pairs, so that the wavefront over the tile's blocks takes about
+// half as many steps (each a chain of dependent FP64 operations and block barriers).
+// A merged pair is solved as one small system whose inverse is composed from the
+// inverses of its 1x1 parts (pair_merged_prepare), so a near-singular part raises
+// exactly the pivot it raises on its own.  One warp, nblk <= 32; rewrites blk and
+// start in place, returns the new count and sets *pseudo (bit per new block).
+__device__ inline int merge_blocks(short* blk, short* start, int n, int nblk, unsigned* pseudo, int lane) {
+  const int b = lane;
+  const bool valid = b < nblk;
+  const int sz = valid ? start[b + 1] - start[b] : 0;
+  const short my_start = valid ? start[b] : short(0);
+  const unsigned O = __ballot_sync(0xffffffffu, valid && sz == 1);
+  const unsigned zeros_below = ~O & ((1u << b) - 1u);
+  const int run0 = zeros_below ? 32 - __clz(zeros_below) : 0;  // first block of this run of 1x1 blocks
+  const bool one = (O >> b) & 1u;
+  const bool odd = ((b - run0) & 1) != 0;
+  const bool head = one && !odd && b < 31 && ((O >> (b + 1)) & 1u);  // merges with block b+1
+  const bool tail = one && odd;                                        // merged into block b-1
+  const unsigned S = __ballot_sync(0xffffffffu, valid && !tail);       // blocks that start a new block
+  const int nidx = __popc(S & (b == 31 ? 0xffffffffu : ((2u << b) - 1u))) - 1;
+  const unsigned pm = __reduce_or_sync(0xffffffffu, head ? (1u << nidx) : 0u);
+  __syncwarp();
+  if (valid && !tail) start[nidx] = my_start;
+  for (int i = lane; i < n; i += 32) {
+    const int ob = blk[i];
+    blk[i] = static_cast<short>(__popc(S & (ob == 31 ? 0xffffffffu : ((2u << ob) - 1u))) - 1);
+  }
+  const int count = __popc(S);
+  if (lane == 0) {
+    start[count] = static_cast<short>(n);
+    *pseudo = pm;
+  }
+  __syncwarp();
+  return count;
+}
+
+// Solve of a merged pair from its parts' solvers, in dependency order: rows split in
+// two 1-row parts when pa (bottom part first), columns in two 1-column parts when pb
+// (left part first).  part(rp, cp, x) solves the part's system in place on x (its
+// elements in the part's vec order); the coupling terms a12 = A[r0, r0+1] and
+// b12 = B[c0, c0+1] are subtracted from the right-hand side before each part.
+template <typename Part>
+__device__ __forceinline__ void merged_apply(int ma, int nb, bool pa, bool pb, double a12, double b12, double (&r)[4],
+                                             Part part) {
+  const int nrp = pa ? 2 : 1, ncp = pb ? 2 : 1;
+  const int mas = pa ? 1 : ma, nbs = pb ? 1 : nb;
+  for (int rp = nrp - 1; rp >= 0; --rp)
+    for (int cp = 0; cp < ncp; ++cp) {
+      double x[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int js = 0; js < nbs; ++js)
+        for (int is = 0; is < mas; ++is) {
+          const int i = pa ? rp : is, j = pb ? cp : js;
+          double v = r[i + ma * j];
+          if (pa && rp == 0) v = fma(-a12, r[1 + ma * j], v);  // row below, solved
+          if (pb && cp == 1) v = fma(-r[i], b12, v);          // column to the left, solved
+          x[is + mas * js] = v;
+        }
+      part(rp, cp, mas, nbs, x);
+      for (int js = 0; js < nbs; ++js)
+        for (int is = 0; is < mas; ++is) r[(pa ? rp : is) + ma * (pb ? cp : js)] = x[is + mas * js];
+    }
+}
+
+// Sub-system of part (rp, cp) of a merged pair: the diagonal entries of the split
+// dimension, the whole block of the other.
+__device__ __forceinline__ void merged_part(const double (&a)[4], const double (&b)[4], bool pa, bool pb, int rp,
+                                            int cp, double (&as)[4], double (&bs)[4]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    as[u] = pa ? (u == 0 ? a[rp * 3] : 0.0) : a[u];
+    bs[u] = pb ? (u == 0 ? b[cp * 3] : 0.0) : b[u];
+  }
+}
+
+// Stored inverse of a merged pair (the layout of pair_prepare: Minv row-major, then
+// ||Minv||_inf, non-finite as infinity): column k is the merged solve of e_k with the
+// parts' own inverses.  Returns bit 16 if a part raised a pivot.
+static __device__ __noinline__ int pair_merged_prepare(int ma, int nb, bool pa, bool pb, const double (&a)[4],
+                                          const double (&b)[4], double smin, double* out) {
+  const int s = ma * nb;
+  double inv[4][5];  // per part: inverse (<= 2 x 2) and norm
+  int flags = 0;
+  const int nrp = pa ? 2 : 1, ncp = pb ? 2 : 1;
+  for (int rp = 0; rp < nrp; ++rp)
+    for (int cp = 0; cp < ncp; ++cp) {
+      double as[4], bs[4];
+      merged_part(a, b, pa, pb, rp, cp, as, bs);
+      const int mas = pa ? 1 : ma, nbs = pb ? 1 : nb;
+      double* o = inv[rp * 2 + cp];
+      if (mas == 1 && nbs == 1)
+        flags |= pair_prepare<1, 1>(as, bs, smin, o);
+      else if (mas == 2)
+        flags |= pair_prepare<2, 1>(as, bs, smin, o);
+      else
+        flags |= pair_prepare<1, 2>(as, bs, smin, o);
+    }
+  double nrm = 0.0;
+  bool finite = true;
+  double M[4][4];
+  for (int k = 0; k < s; ++k) {
+    double r[4] = {0.0, 0.0, 0.0, 0.0};
+    r[k] = 1.0;
+    merged_apply(ma, nb, pa, pb, a[2], b[2], r, [&](int rp, int cp, int mas, int nbs, double (&x)[4]) {
+      const double* f = inv[rp * 2 + cp];
+      const int ss = mas * nbs;
+      double y[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int e = 0; e < ss; ++e)
+        for (int u = 0; u < ss; ++u) y[e] = fma(f[e * ss + u], x[u], y[e]);
+      for (int e = 0; e < 4; ++e) x[e] = y[e];
+    });
+    for (int e = 0; e < s; ++e) M[e][k] = r[e];
+  }
+  for (int e = 0; e < s; ++e) {
+    double rs = 0.0;
+    for (int u = 0; u < s; ++u) {
+      out[e * s + u] = M[e][u];
+      rs += fabs(M[e][u]);
+    }
+    finite = finite && (rs <= 1.7976931348623157e308);
+    nrm = rs > nrm ? rs : nrm;
+  }
+  out[s * s] = finite ? nrm : __longlong_as_double(0x7ff0000000000000ll);
+  return flags & (1 << 16);
+}
+
 // Offset of pair (kb, lb) in the factor store: pairs are stored block row by block
 // row, each taking s^2 + s doubles (s = ma nb).
 template <int TT, typename T>
@@ -478,8 +610,16 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
                              int mt, int nt, double smin, double* gfact, int* gfactp) {
   constexpr int LDY = DagSmem<TT, T>::LDY;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double* fact = DagSmem<TT, T>::kFactSmem ? sh.fact : gfact;
-  int* factp = DagSmem<TT, T>::kFactSmem ? sh.factp : gfactp;
+  using FactT = typename DagSmem<TT, T>::FactT;
+  FactT* fact;
+  int* factp;
+  if constexpr (DagSmem<TT, T>::kFactSmem) {
+    fact = sh.fact;
+    factp = sh.factp;
+  } else {
+    fact = gfact;
+    factp = gfactp;
+  }
   T* Ak = sh.L;
   T* Bk = sh.R;
   for (int idx = tid; idx < TT * TT; idx += kThreads) {
@@ -493,11 +633,26 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
     sh.bcolmax[i] = 0ull;
   }
   __syncthreads();
+  // Blocks of A_kk and B_ll; for tile capacity 32 consecutive 1x1 blocks are merged in
+  // pairs (merge_blocks).  Without a B term the columns are independent and stay 1x1.
+  constexpr bool kMerge = TT <= 32;
   if (warp == 0) {
-    const int pb = scan_blocks<T, LDY>(Ak, mt, sh.rowblk, sh.astart, lane);
+    int pb = scan_blocks<T, LDY>(Ak, mt, sh.rowblk, sh.astart, lane);
+    if (kMerge) {
+      __syncwarp();
+      pb = merge_blocks(sh.rowblk, sh.astart, mt, pb, &sh.apsd, lane);
+    } else if (lane == 0) {
+      sh.apsd = 0;
+    }
     if (lane == 0) sh.pb = pb;
   } else if (warp == 1) {
-    const int qb = scan_blocks<T, LDY>(Bk, nt, sh.colblk, sh.bstart, lane);
+    int qb = scan_blocks<T, LDY>(Bk, nt, sh.colblk, sh.bstart, lane);
+    if (kMerge && B) {
+      __syncwarp();
+      qb = merge_blocks(sh.colblk, sh.bstart, nt, qb, &sh.bpsd, lane);
+    } else if (lane == 0) {
+      sh.bpsd = 0;
+    }
     if (lane == 0) sh.qb = qb;
   }
   __syncthreads();
@@ -550,9 +705,12 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
         a[i + 2 * j] = (i < ma && j < ma) ? static_cast<double>(Ak[(ra + i) + (ra + j) * LDY]) : 0.0;
         b[i + 2 * j] = (i < nb && j < nb) ? static_cast<double>(Bk[(cb0 + i) + (cb0 + j) * LDY]) : 0.0;
       }
-    double* o = fact + pair_offset(sh, kb, lb, ma);
+    double o[17];  // the pair's inverse and its norm, stored below in FactT
+    const bool psa = kMerge && ((sh.apsd >> kb) & 1u), psb = kMerge && ((sh.bpsd >> lb) & 1u);
     int pack;
-    if (ma == 1 && nb == 1)
+    if (psa || psb)
+      pack = pair_merged_prepare(ma, nb, psa, psb, a, b, smin, o);
+    else if (ma == 1 && nb == 1)
       pack = pair_prepare<1, 1>(a, b, smin, o);
     else if (ma == 2 && nb == 1)
       pack = pair_prepare<2, 1>(a, b, smin, o);
@@ -560,6 +718,9 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
       pack = pair_prepare<1, 2>(a, b, smin, o);
     else
       pack = pair_prepare<2, 2>(a, b, smin, o);
+    FactT* fo = fact + pair_offset(sh, kb, lb, ma);
+    const int sz = ma * nb;
+    for (int i = 0; i <= sz * sz; ++i) fo[i] = static_cast<FactT>(o[i]);  // overflow -> inf: guarded path
     factp[kb * TT + lb] = pack;
   }
   // Wavefront order of the tile's elements: step s holds the blocks (kb, lb) with
@@ -625,8 +786,16 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
   constexpr int NC = TT / CSTEP;  // columns owned per thread
   constexpr int NW = kThreads / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double* fact = DagSmem<TT, T>::kFactSmem ? sh.fact : gfact;
-  const int* factp = DagSmem<TT, T>::kFactSmem ? sh.factp : gfactp;
+  using FactT = typename DagSmem<TT, T>::FactT;
+  const FactT* fact;
+  const int* factp;
+  if constexpr (DagSmem<TT, T>::kFactSmem) {
+    fact = sh.fact;
+    factp = sh.factp;
+  } else {
+    fact = gfact;
+    factp = gfactp;
+  }
   const T* Ak = sh.L;
   const T* Bk = sh.R;
   T* Ys = sh.Y;
@@ -711,7 +880,12 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
     T ca0[NP], ca1[NP], cb0[NP], cb1[NP];
     int rsj[NP];
     unsigned amask = 0, a2mask = 0, bmask = 0;  // per slot: A side present / 2 rows; B side present
-    if constexpr (kPre) {
+    // The warps holding this step's Phase A threads fetch after the barrier instead:
+    // their Phase A is the step's critical path.
+    const int e0 = sh.sstart[s];
+    const int nact = sh.sstart[s + 1] - e0;
+    const bool pre_early = warp >= ((nact + 31) >> 5);
+    auto prefetch = [&]() {
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int c = my_c0 + j * CSTEP;
@@ -738,14 +912,15 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
           }
         }
       }
-    }
+    };
+    if constexpr (kPre)
+      if (pre_early) prefetch();
     // Phase A: the step's elements, one thread each.  All reads of the step's
     // right-hand sides come before any write of a solution (__syncwarp).
-    const int e0 = sh.sstart[s];
-    const bool act = tid < sh.sstart[s + 1] - e0;
+    const bool act = tid < nact;
     int r = 0, c = 0, e = 0, r0 = 0, c0 = 0, ma = 1, sz = 0, lb = 0, eb = 0, mode = 0;
     double rv[4] = {0.0, 0.0, 0.0, 0.0};
-    double z = 0.0;
+    FactT z = FactT(0);
     if (act) {
       const unsigned code = sh.eord[e0 + tid];
       r = code & 63;
@@ -758,20 +933,20 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
       c0 = sh.bstart[lb];
       const int nb = sh.bstart[lb + 1] - c0;
       sz = ma * nb;
-      const double* f = fact + pair_offset(sh, kb, lb, ma);
+      const FactT* f = fact + pair_offset(sh, kb, lb, ma);
       if (factp[kb * TT + lb] & (1 << 16)) near = true;
-      unsigned long long rmb = 0;
+      T rt[4];
+      int rexp = -1022;  // upper bound on log2 max |r| (exponent fields only)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        rv[u] = (u < sz) ? to_f64(Ys[(r0 + (ma == 2 ? (u & 1) : 0)) + (c0 + (ma == 2 ? (u >> 1) : u)) * LDY]) : 0.0;
-        const unsigned long long bv = abs_bits(rv[u]);
-        rmb = bv > rmb ? bv : rmb;
+        rt[u] = (u < sz) ? Ys[(r0 + (ma == 2 ? (u & 1) : 0)) + (c0 + (ma == 2 ? (u >> 1) : u)) * LDY] : T(0);
+        rexp = max(rexp, ub_log2(rt[u]));
       }
-      const bool ok = !ROBUST || ub_log2(f[sz * sz]) + ub_log2(bits_to_double(rmb)) + 1 <= eo;
+      const bool ok = !ROBUST || ub_log2(f[sz * sz]) + rexp + 1 <= eo;
       if (ok) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (u < sz) z = fma(f[e * sz + u], rv[u], z);
+          if (u < sz) z = fma(f[e * sz + u], static_cast<FactT>(rt[u]), z);
         mode = 1;
         if (ROBUST) {
           unsigned u0 = 0;
@@ -784,7 +959,10 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
           if (!fast) sh.slow = 1;
         }
       } else if (e == 0) {
-        // Guarded small solve of the whole block by its first thread (rare).
+        // Guarded small solve of the whole block by its first thread (rare).  A pseudo
+        // block takes the same guarded elimination of its (block-triangular) system.
+#pragma unroll
+        for (int u = 0; u < 4; ++u) rv[u] = to_f64(rt[u]);
         double a[4], b[4];
         for (int i = 0; i < 2; ++i)
           for (int jj = 0; jj < 2; ++jj) {
@@ -819,6 +997,8 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
       sh.pma[lb] = static_cast<short>(ma);
     }
     __syncthreads();
+    if constexpr (kPre)
+      if (!pre_early) prefetch();
     const int lb_lo = lw ? max(0, s - (pb - 1)) : 0;
     const int lb_hi = lw ? min(s, qb - 1) : qb - 1;
     int g = 0;
@@ -1020,6 +1200,28 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
   const int rbase = tx * MR, cbase = ty * NR;
   Ctrl* ctrl = w.ctrl;
   if (w.skip && ld_volatile(w.skip)) return;
+  // SM cap: the CTAs placed on SMs outside the budget leave before their first ticket
+  // (tickets are dynamic, so the others take all the tasks).  CTAs inside the budget
+  // register; CTA 0, if outside, leaves once one has registered and works itself if
+  // none has within 2 ms, so the kernel is never left without a worker.  The whole
+  // CTA shares one SM id, so every exit is CTA-uniform.
+  if (w.sm_limit > 0) {
+    const bool inside = static_cast<int>(sm_id()) < w.sm_limit;
+    if (inside) {
+      if (tid == 0) atomicAdd(&ctrl->workers, 1);
+    } else if (blockIdx.x != 0) {
+      return;
+    } else {
+      if (tid == 0) {
+        const unsigned long long t0 = global_ns();
+        int seen = 0;
+        while (!(seen = ld_volatile(&ctrl->workers)) && global_ns() - t0 < 2000000ull) __nanosleep(1000);
+        sh.abort = seen;
+      }
+      __syncthreads();
+      if (sh.abort) return;
+    }
+  }
   const bool packed = w.pack != nullptr;
   uint32_t stage_phase = 0;
   if (packed) {

@@ -6,7 +6,9 @@
 
 namespace sylv {
 
-cudaError_t launch_dag_f32(int tt, const Work& w, int max_tasks, cudaStream_t stream) {
+cudaError_t launch_dag_f32(int tt, const Work& w0, int max_tasks, cudaStream_t stream, int sm_limit) {
+  Work w = w0;
+  w.sm_limit = sm_limit;
   if (tt <= 32) return launch_dag_impl<32, float, true>(w, max_tasks, stream);
   return launch_dag_impl<64, float, true>(w, max_tasks, stream);
 }

@@ -18,9 +18,10 @@ static int diag_priority() {
   return v;
 }
 
-cudaError_t launch_dag_f64(int tt, bool robust, const Work& w0, int max_tasks, cudaStream_t stream) {
+cudaError_t launch_dag_f64(int tt, bool robust, const Work& w0, int max_tasks, cudaStream_t stream, int sm_limit) {
   Work w = w0;
   w.prio = diag_priority();
+  w.sm_limit = sm_limit;
   if (tt <= 32) return robust ? launch_dag_impl<32, double, true>(w, max_tasks, stream)
                               : launch_dag_impl<32, double, false>(w, max_tasks, stream);
   return robust ? launch_dag_impl<64, double, true>(w, max_tasks, stream)

@@ -56,6 +56,7 @@ struct Task {
 
 struct Ctrl {
   int32_t ticket;   // next task of the persistent kernel
+  int32_t workers;  // SM cap: CTAs of this launch inside the SM budget (reset with ticket)
   int32_t ntasks;   // tasks in Work::tasks
   int32_t err;      // first launch-wide error (timeout)
   int32_t nlevels;  // anti-diagonal levels in use
@@ -85,7 +86,7 @@ struct Work {
   int32_t prio;     // 1: update GEMMs yield the SM while a diagonal solve runs on it
   int64_t timeout_ns;
   int32_t max_tiles;  // max over equations of pmax * qmax
-  int32_t pad;
+  int32_t sm_limit;   // > 0: CTAs (except CTA 0) on SMs with id >= sm_limit leave at once
   // Packed operand tiles (null: the kernel stages tiles from A, B, C directly).  One
   // slot holds a tile in the shared-memory operand layout of the update GEMM (TT rows
   // of k, row stride TT + 2, zero-padded), so one bulk copy stages it.  Per equation,

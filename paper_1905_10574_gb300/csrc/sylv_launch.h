@@ -17,8 +17,9 @@ constexpr int max_ctas_per_sm() {
 
 // Launch the persistent DAG kernel for tile capacity tt (32 or 64) on `stream`.
 // max_tasks bounds the grid (no more CTAs than tiles).  Returns the launch error.
-cudaError_t launch_dag_f64(int tt, bool robust, const Work& w, int max_tasks, cudaStream_t stream);
-cudaError_t launch_dag_f32(int tt, const Work& w, int max_tasks, cudaStream_t stream);
+// sm_limit > 0 runs the tile kernel on the SMs with id < sm_limit only (SM scaling).
+cudaError_t launch_dag_f64(int tt, bool robust, const Work& w, int max_tasks, cudaStream_t stream, int sm_limit = 0);
+cudaError_t launch_dag_f32(int tt, const Work& w, int max_tasks, cudaStream_t stream, int sm_limit = 0);
 
 // Event bracketing of DAG launches for sylv_profile (no-ops unless enabled).
 void profile_begin(cudaStream_t stream);

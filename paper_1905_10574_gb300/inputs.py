@@ -128,6 +128,8 @@ WORKLOADS = {
     "benign_1000": dict(m=1000, n=1000, seed=0, kind="benign", upper=1.0, tile=32),
     "benign_4000": dict(m=4000, n=4000, seed=0, kind="benign", upper=1.0, tile=32),
     "benign_8000": dict(m=8000, n=8000, seed=0, kind="benign", upper=1.0, tile=32),
+    "benign_10000": dict(m=10000, n=10000, seed=0, kind="benign", upper=1.0, tile=32),
+    "benign_20000": dict(m=20000, n=20000, seed=0, kind="benign", upper=1.0, tile=32),
     "wellcond_8000": dict(m=8000, n=8000, seed=0, kind="wellcond", upper=1.0, tile=32),
     "wellcond_4000": dict(m=4000, n=4000, seed=0, kind="wellcond", upper=1.0, tile=32),
 }

@@ -1115,6 +1115,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
   if (local_scale_events) atomicAdd(&sh.nscale, local_scale_events);
 }
 
+
 // ----------------------------------------------------------------------------
 // GEMM operand staging: L (rows x kdim) from column-major P (coalesced along rows),
 // R (kdim x cols) from column-major P (coalesced along k); both stored k-major at

@@ -1,6 +1,6 @@
 // sylv_dag_f32.cu -- FP32 instantiations of the tile-DAG kernel, used for the
-// correction solves of the FP32 + refinement mode (robust, with FP64 small
-// solves and FP64 bound arithmetic).
+// correction solves of the FP32 + refinement mode (robust; binary32 small solves
+// with FP64 bound arithmetic and an FP64 guarded fallback).
 #include "sylv_dag_common.cuh"
 #include "sylv_launch.h"
 

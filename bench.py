@@ -57,9 +57,10 @@ def parse():
     ap.add_argument("--sms", default="", help="smscale mode: comma-separated SM counts")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (mixed precision, batched, adjoint)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "mixed", "batched", "adjoint", "smscale"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "mixed", "batched", "adjoint", "smscale", "variants"],
                     help="solve: the headline robust FP64 solve; mixed: FP32 + refinement vs FP64 at "
-                         "m=n=8000; batched: 4096 uneven equations; adjoint: 256 Lyapunov forward+backward")
+                         "m=n=8000; batched: 4096 uneven equations; adjoint: 256 Lyapunov forward+backward; "
+                         "smscale: SM scaling; variants: sign variant, triangular solve, Bartels-Stewart at 4000")
     return ap.parse_args()
 
 
@@ -541,6 +542,66 @@ def run_adjoint(args):
     return line
 
 
+def run_variants(args):
+    """The variants beside the paper's equation, each at m = n = 4000 on its own entry
+    point: the sign variant A Y - Y B = C (isgn = -1), the robust triangular solve
+    A X = alpha C (n = 4000 right-hand sides, growth generator, so it scales), and the
+    Bartels-Stewart wrapper (U^T C V, the solve, U Y V^T) on random orthogonal U, V."""
+    import numpy as np
+    import torch
+    from paper_1905_10574_gb300 import build, inputs, sylv
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    m = n = 4000
+    F = lambda x: torch.from_numpy(np.asfortranarray(x)).to(dev)  # noqa: E731
+    A, B, C = inputs.problem(m, n, 0, kind="benign")
+    Ad, Bd, C0 = F(A), F(-B), F(C)
+    rows = {}
+    steps, warm = max(1, args.steps), max(1, args.warmup)
+    res = sylv.sylv_result()
+    Cs = [C0.clone() for _ in range(steps + warm)]
+
+    def sign(i):
+        o = sylv.make_opts(isgn=-1, stream=stream.cuda_stream)
+        rc = sylv.sylv_tri_solve_ex(m, n, Ad.data_ptr(), m, Bd.data_ptr(), n, Cs[i].data_ptr(), m, o, res)
+        if rc not in (0, 1):
+            raise sylv.SylvError(rc, "sign variant")
+    ms, _ = _timed(sign, steps, warm, stream)
+    rows["sign_variant"] = {"ms": ms, "gflops_2mnmn": flops_2(m, n) / ms / 1e6, "log2scale": int(res.log2scale)}
+
+    Ag, _, Cg = inputs.problem(m, n, 0, kind="growth", upper=4.1)
+    Agd = F(Ag)
+    Cs = [F(Cg) for _ in range(steps + warm)]
+
+    def tri(i):
+        o = sylv.make_opts(stream=stream.cuda_stream)
+        rc = sylv.sylv_tri_solve_triangular(m, n, Agd.data_ptr(), m, Cs[i].data_ptr(), m, o, res)
+        if rc not in (0, 1):
+            raise sylv.SylvError(rc, "triangular")
+    ms, _ = _timed(tri, steps, warm, stream)
+    rows["triangular"] = {"ms": ms, "gflops_m2n": 1.0 * m * m * n / ms / 1e6, "log2scale": int(res.log2scale)}
+
+    rng = np.random.default_rng(7)
+    U = np.linalg.qr(rng.standard_normal((m, m)))[0]
+    V = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    Ud, Vd, TAd, TBd = F(U), F(V), F(A), F(B)
+    Cs = [C0.clone() for _ in range(steps + warm)]
+
+    def schur(i):
+        o = sylv.make_opts(stream=stream.cuda_stream)
+        rc = sylv.sylv_solve_schur(m, n, Ud.data_ptr(), m, TAd.data_ptr(), m, Vd.data_ptr(), n, TBd.data_ptr(), n,
+                                   Cs[i].data_ptr(), m, o, res)
+        if rc not in (0, 1):
+            raise sylv.SylvError(rc, "schur")
+    ms, _ = _timed(schur, steps, warm, stream)
+    rows["bartels_stewart"] = {"ms": ms, "gflops_6mnmn": 3 * flops_2(m, n) / ms / 1e6,
+                               "note": "4 cuBLAS DGEMMs (4mn(m+n) flops) + the robust solve"}
+    return {"metric": "variant solves, m = n = 4000", "value": rows["bartels_stewart"]["ms"], "unit": "ms",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"m": m, "n": n, "tile": 32}, "rows": rows}
+
+
 def secondary(args):
     """The other configurations, measured briefly beside the headline solve."""
     import argparse as _ap
@@ -575,6 +636,8 @@ def main():
         print(json.dumps(run_adjoint(args)), flush=True)
     elif args.mode == "smscale":
         print(json.dumps(run_smscale(args)), flush=True)
+    elif args.mode == "variants":
+        print(json.dumps(run_variants(args)), flush=True)
     else:
         run_ours(args)
 

@@ -33,6 +33,12 @@
 
 namespace sylv {
 
+// Merging of consecutive 1x1 blocks into pseudo 2x2 blocks in the diagonal solves
+// (merge_blocks); a build may turn it off for comparison.
+#ifndef SYLV_MERGE_DIAG
+#define SYLV_MERGE_DIAG 1
+#endif
+
 template <int TT, typename T>
 struct DagSmem {
   static constexpr int LDG = TT + 2;  // row stride of the GEMM operands (16-byte aligned rows)
@@ -472,8 +478,8 @@ __device__ inline int scan_blocks(const T* M, int N, short* blk, short* start, i
 // blocks are merged in pairs, so that the wavefront over the tile's blocks takes about
 // half as many steps (each a chain of dependent FP64 operations and block barriers).
 // A merged pair is solved as one small system whose inverse is composed from the
-// inverses of its 1x1 parts (pair_merged_prepare), so a near-singular part raises
-// exactly the pivot it raises on its own.  One warp, nblk <= 32; rewrites blk and
+// inverses of its parts (pair_quad_prepare, pair_half_prepare), so a near-singular
+// part raises exactly the pivot it raises on its own.  One warp, nblk <= 32; rewrites blk and
 // start in place, returns the new count and sets *pseudo (bit per new block).
 __device__ inline int merge_blocks(short* blk, short* start, int n, int nblk, unsigned* pseudo, int lane) {
   const int b = lane;
@@ -505,92 +511,129 @@ __device__ inline int merge_blocks(short* blk, short* start, int n, int nblk, un
   return count;
 }
 
-// Solve of a merged pair from its parts' solvers, in dependency order: rows split in
-// two 1-row parts when pa (bottom part first), columns in two 1-column parts when pb
-// (left part first).  part(rp, cp, x) solves the part's system in place on x (its
-// elements in the part's vec order); the coupling terms a12 = A[r0, r0+1] and
-// b12 = B[c0, c0+1] are subtracted from the right-hand side before each part.
-template <typename Part>
-__device__ __forceinline__ void merged_apply(int ma, int nb, bool pa, bool pb, double a12, double b12, double (&r)[4],
-                                             Part part) {
-  const int nrp = pa ? 2 : 1, ncp = pb ? 2 : 1;
-  const int mas = pa ? 1 : ma, nbs = pb ? 1 : nb;
-  for (int rp = nrp - 1; rp >= 0; --rp)
-    for (int cp = 0; cp < ncp; ++cp) {
-      double x[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int js = 0; js < nbs; ++js)
-        for (int is = 0; is < mas; ++is) {
-          const int i = pa ? rp : is, j = pb ? cp : js;
-          double v = r[i + ma * j];
-          if (pa && rp == 0) v = fma(-a12, r[1 + ma * j], v);  // row below, solved
-          if (pb && cp == 1) v = fma(-r[i], b12, v);          // column to the left, solved
-          x[is + mas * js] = v;
-        }
-      part(rp, cp, mas, nbs, x);
-      for (int js = 0; js < nbs; ++js)
-        for (int is = 0; is < mas; ++is) r[(pa ? rp : is) + ma * (pb ? cp : js)] = x[is + mas * js];
+// A merged pair of two pseudo blocks (four 1x1 parts): the composed inverse in closed
+// form.  With the parts' reciprocals i_ij = 1/d_ij, d_ij = a_ii + b_jj raised to smin
+// like a 1x1 pair's pivot, and the couplings a12 = A[r0, r0+1], b12 = B[c0, c0+1],
+// the solve order z10, z00, z11, z01 gives (vec order u = i + 2j)
+//   z00 = i00 (r00 - a12 z10),  z10 = i10 r10,  z11 = i11 (r11 - b12 z10),
+//   z01 = i01 (r01 - a12 z11 - b12 z00).
+// Writes Minv row-major and ||Minv||_inf (infinity if not finite) in OutT; returns
+// bit 16 if a part raised its pivot.
+template <typename OutT>
+__device__ __forceinline__ int pair_quad_prepare(const double (&a)[4], const double (&b)[4], double smin, OutT* out) {
+  int flag = 0;
+  auto inv = [&](double d) {
+    if (fabs(d) < smin) {
+      d = smin;
+      flag = 1 << 16;
     }
-}
-
-// Sub-system of part (rp, cp) of a merged pair: the diagonal entries of the split
-// dimension, the whole block of the other.
-__device__ __forceinline__ void merged_part(const double (&a)[4], const double (&b)[4], bool pa, bool pb, int rp,
-                                            int cp, double (&as)[4], double (&bs)[4]) {
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    as[u] = pa ? (u == 0 ? a[rp * 3] : 0.0) : a[u];
-    bs[u] = pb ? (u == 0 ? b[cp * 3] : 0.0) : b[u];
-  }
-}
-
-// Stored inverse of a merged pair (the layout of pair_prepare: Minv row-major, then
-// ||Minv||_inf, non-finite as infinity): column k is the merged solve of e_k with the
-// parts' own inverses.  Returns bit 16 if a part raised a pivot.
-static __device__ __noinline__ int pair_merged_prepare(int ma, int nb, bool pa, bool pb, const double (&a)[4],
-                                          const double (&b)[4], double smin, double* out) {
-  const int s = ma * nb;
-  double inv[4][5];  // per part: inverse (<= 2 x 2) and norm
-  int flags = 0;
-  const int nrp = pa ? 2 : 1, ncp = pb ? 2 : 1;
-  for (int rp = 0; rp < nrp; ++rp)
-    for (int cp = 0; cp < ncp; ++cp) {
-      double as[4], bs[4];
-      merged_part(a, b, pa, pb, rp, cp, as, bs);
-      const int mas = pa ? 1 : ma, nbs = pb ? 1 : nb;
-      double* o = inv[rp * 2 + cp];
-      if (mas == 1 && nbs == 1)
-        flags |= pair_prepare<1, 1>(as, bs, smin, o);
-      else if (mas == 2)
-        flags |= pair_prepare<2, 1>(as, bs, smin, o);
-      else
-        flags |= pair_prepare<1, 2>(as, bs, smin, o);
-    }
+    return 1.0 / d;
+  };
+  const double i00 = inv(a[0] + b[0]), i10 = inv(a[3] + b[0]), i01 = inv(a[0] + b[3]), i11 = inv(a[3] + b[3]);
+  const double a12 = a[2], b12 = b[2];
+  const double m[16] = {i00,
+                        -a12 * i00 * i10,
+                        0.0,
+                        0.0,
+                        0.0,
+                        i10,
+                        0.0,
+                        0.0,
+                        -b12 * i01 * i00,
+                        a12 * b12 * i01 * i10 * (i00 + i11),
+                        i01,
+                        -a12 * i01 * i11,
+                        0.0,
+                        -b12 * i11 * i10,
+                        0.0,
+                        i11};
   double nrm = 0.0;
   bool finite = true;
-  double M[4][4];
-  for (int k = 0; k < s; ++k) {
-    double r[4] = {0.0, 0.0, 0.0, 0.0};
-    r[k] = 1.0;
-    merged_apply(ma, nb, pa, pb, a[2], b[2], r, [&](int rp, int cp, int mas, int nbs, double (&x)[4]) {
-      const double* f = inv[rp * 2 + cp];
-      const int ss = mas * nbs;
-      double y[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int e = 0; e < ss; ++e)
-        for (int u = 0; u < ss; ++u) y[e] = fma(f[e * ss + u], x[u], y[e]);
-      for (int e = 0; e < 4; ++e) x[e] = y[e];
-    });
-    for (int e = 0; e < s; ++e) M[e][k] = r[e];
-  }
-  for (int e = 0; e < s; ++e) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
     double rs = 0.0;
-    for (int u = 0; u < s; ++u) {
-      out[e * s + u] = M[e][u];
-      rs += fabs(M[e][u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      out[e * 4 + u] = static_cast<OutT>(m[e * 4 + u]);
+      rs += fabs(m[e * 4 + u]);
     }
     finite = finite && (rs <= 1.7976931348623157e308);
     nrm = rs > nrm ? rs : nrm;
   }
-  out[s * s] = finite ? nrm : __longlong_as_double(0x7ff0000000000000ll);
+  out[16] = static_cast<OutT>(finite ? nrm : __longlong_as_double(0x7ff0000000000000ll));
+  return flag;
+}
+
+// A merged pair with one pseudo side, composed inline from its two parts' inverses
+// (pair_prepare of each part, so a part raises exactly the pivots it raises alone).
+// Pseudo A (rows split, bottom part solved first): Minv = [[It, -a12 It Ib], [0, Ib]]
+// over (top, bottom) rows; pseudo B (columns split, left first):
+// Minv = [[Il, 0], [-b12 Ir Il, Ir]] over (left, right) columns.  Each part has the
+// other side's whole block (1x1 or 2x2).  Same output layout as pair_prepare.
+template <typename OutT>
+__device__ __forceinline__ int pair_half_prepare(int ma, int nb, bool pa, const double (&a)[4], const double (&b)[4],
+                                                 double smin, OutT* out) {
+  const int s = ma * nb;
+  const int h = pa ? nb : ma;  // size of each part's system (the other side's block)
+  double P0[5], P1[5];          // part inverses (<= 2 x 2, row-major) and norms
+  double a0[4] = {0.0, 0.0, 0.0, 0.0}, a1[4] = {0.0, 0.0, 0.0, 0.0};
+  double b0[4] = {0.0, 0.0, 0.0, 0.0}, b1[4] = {0.0, 0.0, 0.0, 0.0};
+  int flags;
+  if (pa) {  // part 0: top row (a00), part 1: bottom row (a11); both with B
+    a0[0] = a[0];
+    a1[0] = a[3];
+    flags = (h == 1) ? (pair_prepare<1, 1>(a0, b, smin, P0) | pair_prepare<1, 1>(a1, b, smin, P1))
+                     : (pair_prepare<1, 2>(a0, b, smin, P0) | pair_prepare<1, 2>(a1, b, smin, P1));
+  } else {  // part 0: left column (b00), part 1: right column (b11); both with A
+    b0[0] = b[0];
+    b1[0] = b[3];
+    flags = (h == 1) ? (pair_prepare<1, 1>(a, b0, smin, P0) | pair_prepare<1, 1>(a, b1, smin, P1))
+                     : (pair_prepare<2, 1>(a, b0, smin, P0) | pair_prepare<2, 1>(a, b1, smin, P1));
+  }
+  // Coupled block: pseudo A: top += -a12 It Ib (rows of the top part, columns of the
+  // bottom part); pseudo B: right += -b12 Ir Il.
+  const double cpl = pa ? a[2] : b[2];
+  double m[4][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) m[e][u] = 0.0;
+  // vec index of part p, local index t: pseudo A: element (i = p, j = t) -> p + 2t;
+  // pseudo B: element (i = t, j = p) -> t + ma p.
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      if (t >= h || v >= h) continue;
+      const int e0 = pa ? 0 + 2 * t : t, u0 = pa ? 0 + 2 * v : v;            // part 0
+      const int e1 = pa ? 1 + 2 * t : t + ma, u1 = pa ? 1 + 2 * v : v + ma;  // part 1
+      m[e0][u0] = P0[t * h + v];
+      m[e1][u1] = P1[t * h + v];
+      double c = 0.0;  // (P_first_solved_after * P_solved_first)[t][v]
+#pragma unroll
+      for (int w = 0; w < 2; ++w)
+        if (w < h) c = fma(pa ? P0[t * h + w] : P1[t * h + w], pa ? P1[w * h + v] : P0[w * h + v], c);
+      if (pa)
+        m[e0][u1] = -cpl * c;  // top row element from the bottom right-hand side
+      else
+        m[e1][u0] = -cpl * c;  // right column element from the left right-hand side
+    }
+  double nrm = 0.0;
+  bool finite = true;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (e >= s) continue;
+    double rs = 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (u >= s) continue;
+      out[e * s + u] = static_cast<OutT>(m[e][u]);
+      rs += fabs(m[e][u]);
+    }
+    finite = finite && (rs <= 1.7976931348623157e308);
+    nrm = rs > nrm ? rs : nrm;
+  }
+  out[s * s] = static_cast<OutT>(finite ? nrm : __longlong_as_double(0x7ff0000000000000ll));
   return flags & (1 << 16);
 }
 
@@ -635,7 +678,7 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
   __syncthreads();
   // Blocks of A_kk and B_ll; for tile capacity 32 consecutive 1x1 blocks are merged in
   // pairs (merge_blocks).  Without a B term the columns are independent and stay 1x1.
-  constexpr bool kMerge = TT <= 32;
+  constexpr bool kMerge = SYLV_MERGE_DIAG && TT <= 32;
   if (warp == 0) {
     int pb = scan_blocks<T, LDY>(Ak, mt, sh.rowblk, sh.astart, lane);
     if (kMerge) {
@@ -705,22 +748,28 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
         a[i + 2 * j] = (i < ma && j < ma) ? static_cast<double>(Ak[(ra + i) + (ra + j) * LDY]) : 0.0;
         b[i + 2 * j] = (i < nb && j < nb) ? static_cast<double>(Bk[(cb0 + i) + (cb0 + j) * LDY]) : 0.0;
       }
-    double o[17];  // the pair's inverse and its norm, stored below in FactT
     const bool psa = kMerge && ((sh.apsd >> kb) & 1u), psb = kMerge && ((sh.bpsd >> lb) & 1u);
-    int pack;
-    if (psa || psb)
-      pack = pair_merged_prepare(ma, nb, psa, psb, a, b, smin, o);
-    else if (ma == 1 && nb == 1)
-      pack = pair_prepare<1, 1>(a, b, smin, o);
-    else if (ma == 2 && nb == 1)
-      pack = pair_prepare<2, 1>(a, b, smin, o);
-    else if (ma == 1)
-      pack = pair_prepare<1, 2>(a, b, smin, o);
-    else
-      pack = pair_prepare<2, 2>(a, b, smin, o);
     FactT* fo = fact + pair_offset(sh, kb, lb, ma);
-    const int sz = ma * nb;
-    for (int i = 0; i <= sz * sz; ++i) fo[i] = static_cast<FactT>(o[i]);  // overflow -> inf: guarded path
+    auto prep = [&](double* o) -> int {
+      if (psa || psb) return pair_half_prepare(ma, nb, psa, a, b, smin, o);
+      if (ma == 1 && nb == 1) return pair_prepare<1, 1>(a, b, smin, o);
+      if (ma == 2 && nb == 1) return pair_prepare<2, 1>(a, b, smin, o);
+      if (ma == 1) return pair_prepare<1, 2>(a, b, smin, o);
+      return pair_prepare<2, 2>(a, b, smin, o);
+    };
+    int pack;
+    if (psa && psb) {
+      pack = pair_quad_prepare(a, b, smin, fo);
+    } else {
+      if constexpr (std::is_same<FactT, double>::value) {
+        pack = prep(fo);
+      } else {
+        double o[17];  // binary32 store: the inverse and its norm are rounded (overflow -> inf: guarded path)
+        pack = prep(o);
+        const int sz = ma * nb;
+        for (int i = 0; i <= sz * sz; ++i) fo[i] = static_cast<FactT>(o[i]);
+      }
+    }
     factp[kb * TT + lb] = pack;
   }
   // Wavefront order of the tile's elements: step s holds the blocks (kb, lb) with
@@ -1114,7 +1163,6 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
   if (near) atomicOr(&sh.flags, kFlagNearSingular);
   if (local_scale_events) atomicAdd(&sh.nscale, local_scale_events);
 }
-
 
 // ----------------------------------------------------------------------------
 // GEMM operand staging: L (rows x kdim) from column-major P (coalesced along rows),

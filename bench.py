@@ -544,7 +544,8 @@ def run_adjoint(args):
 
 def run_variants(args):
     """The variants beside the paper's equation, each at m = n = 4000 on its own entry
-    point: the sign variant A Y - Y B = C (isgn = -1), the robust triangular solve
+    point: the sign variant A Y - Y B = C (isgn = -1), the robust solve against the
+    non-robust one (Algorithm 1) on the same input, the robust triangular solve
     A X = alpha C (n = 4000 right-hand sides, growth generator, so it scales), and the
     Bartels-Stewart wrapper (U^T C V, the solve, U Y V^T) on random orthogonal U, V."""
     import numpy as np
@@ -569,6 +570,22 @@ def run_variants(args):
             raise sylv.SylvError(rc, "sign variant")
     ms, _ = _timed(sign, steps, warm, stream)
     rows["sign_variant"] = {"ms": ms, "gflops_2mnmn": flops_2(m, n) / ms / 1e6, "log2scale": int(res.log2scale)}
+
+    # Robust against non-robust (Algorithm 4 against Algorithm 1) on the same input:
+    # the cost of the overflow protection.
+    Bp = F(B)
+    for prec in ("fp64", "fp64_nonrobust"):
+        Cs = [C0.clone() for _ in range(steps + warm)]
+
+        def plain(i, prec=prec):
+            o = sylv.make_opts(precision=prec, stream=stream.cuda_stream)
+            rc = sylv.sylv_tri_solve_ex(m, n, Ad.data_ptr(), m, Bp.data_ptr(), n, Cs[i].data_ptr(), m, o, res)
+            if rc not in (0, 1):
+                raise sylv.SylvError(rc, prec)
+        ms, _ = _timed(plain, steps, warm, stream)
+        rows[prec] = {"ms": ms, "gflops_2mnmn": flops_2(m, n) / ms / 1e6}
+    rows["robustness_overhead"] = rows["fp64"]["ms"] / rows["fp64_nonrobust"]["ms"] - 1.0
+    Cs = [C0.clone() for _ in range(steps + warm)]
 
     Ag, _, Cg = inputs.problem(m, n, 0, kind="growth", upper=4.1)
     Agd = F(Ag)

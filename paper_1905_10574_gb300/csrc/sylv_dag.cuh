@@ -288,6 +288,22 @@ __device__ __noinline__ int pair_solve_guarded(const double* f, int pack, double
   return lb;
 }
 
+// Magnitude bits (for pivot search) and limits of the small-system compute type.
+__device__ __forceinline__ unsigned long long mag_bits(double v) { return abs_bits(v); }
+__device__ __forceinline__ unsigned mag_bits(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+template <typename CT>
+struct Lim;
+template <>
+struct Lim<double> {
+  static __device__ __forceinline__ double big() { return 1.7976931348623157e308; }
+  static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+};
+template <>
+struct Lim<float> {
+  static __device__ __forceinline__ float big() { return 3.4028234663852886e38f; }
+  static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+};
+
 // The factorization of pair_factor for a compile-time block shape (MA x MA with
 // NB x NB), in registers, followed by the inverse: column k of Minv solves
 // M x = e_k with the same interchanges, multipliers and reciprocals.  Writes Minv
@@ -295,10 +311,11 @@ __device__ __noinline__ int pair_solve_guarded(const double* f, int pack, double
 // entry (a raised pivot of a near-singular pair can overflow) stores an infinite
 // norm, which sends every solve of the pair to the guarded path.  Returns the
 // packed interchanges.
-template <int MA, int NB>
-__device__ __forceinline__ int pair_prepare(const double (&a)[4], const double (&b)[4], double smin, double* out) {
+template <int MA, int NB, typename CT = double>
+__device__ __forceinline__ int pair_prepare(const double (&a)[4], const double (&b)[4], double smin, CT* out) {
   constexpr int S = MA * NB;
-  double M[S][S];
+  const CT sm = static_cast<CT>(smin);
+  CT M[S][S];
 #pragma unroll
   for (int u = 0; u < S; ++u)
 #pragma unroll
@@ -306,24 +323,24 @@ __device__ __forceinline__ int pair_prepare(const double (&a)[4], const double (
       double e = 0.0;
       if (u / MA == v / MA) e += a[(u % MA) + 2 * (v % MA)];
       if (u % MA == v % MA) e += b[(v / MA) + 2 * (u / MA)];
-      M[u][v] = e;
+      M[u][v] = static_cast<CT>(e);
     }
   int cperm[S];
 #pragma unroll
   for (int u = 0; u < S; ++u) cperm[u] = u;
-  double rcp[S];
+  CT rcp[S];
   int pack = 0;
 #pragma unroll
   for (int st = 0; st < S; ++st) {
     int pr = st, pc = st;
-    unsigned long long best = abs_bits(M[st][st]);
+    auto best = mag_bits(M[st][st]);
 #pragma unroll
     for (int u = st; u < S; ++u)
 #pragma unroll
       for (int v = st; v < S; ++v) {
-        const unsigned long long mag = abs_bits(M[u][v]);
-        if (mag > best) {
-          best = mag;
+        const auto mg = mag_bits(M[u][v]);
+        if (mg > best) {
+          best = mg;
           pr = u;
           pc = v;
         }
@@ -333,7 +350,7 @@ __device__ __forceinline__ int pair_prepare(const double (&a)[4], const double (
       if (pr == k)
 #pragma unroll
         for (int v = 0; v < S; ++v) {
-          const double t = M[st][v];
+          const CT t = M[st][v];
           M[st][v] = M[k][v];
           M[k][v] = t;
         }
@@ -342,7 +359,7 @@ __device__ __forceinline__ int pair_prepare(const double (&a)[4], const double (
       if (pc == k) {
 #pragma unroll
         for (int u = 0; u < S; ++u) {
-          const double t = M[u][st];
+          const CT t = M[u][st];
           M[u][st] = M[u][k];
           M[u][k] = t;
         }
@@ -351,14 +368,14 @@ __device__ __forceinline__ int pair_prepare(const double (&a)[4], const double (
         cperm[k] = ct;
       }
     pack |= (pr & 3) << (2 * st);
-    if (fabs(M[st][st]) < smin) {
-      M[st][st] = smin;
+    if (fabs(M[st][st]) < sm) {
+      M[st][st] = sm;
       pack |= 1 << 16;
     }
-    rcp[st] = 1.0 / M[st][st];
+    rcp[st] = CT(1) / M[st][st];
 #pragma unroll
     for (int u = st + 1; u < S; ++u) {
-      const double l = M[u][st] * rcp[st];
+      const CT l = M[u][st] * rcp[st];
       M[u][st] = l;
 #pragma unroll
       for (int v = st + 1; v < S; ++v) M[u][v] = fma(-l, M[st][v], M[u][v]);
@@ -366,19 +383,19 @@ __device__ __forceinline__ int pair_prepare(const double (&a)[4], const double (
   }
 #pragma unroll
   for (int u = 0; u < S; ++u) pack |= (cperm[u] & 3) << (8 + 2 * u);
-  double inv[S][S];
+  CT inv[S][S];
 #pragma unroll
   for (int k = 0; k < S; ++k) {
-    double r[S];
+    CT r[S];
 #pragma unroll
-    for (int u = 0; u < S; ++u) r[u] = (u == k) ? 1.0 : 0.0;
+    for (int u = 0; u < S; ++u) r[u] = (u == k) ? CT(1) : CT(0);
 #pragma unroll
     for (int st = 0; st < S; ++st) {
       const int pr = (pack >> (2 * st)) & 3;
 #pragma unroll
       for (int kk = st + 1; kk < S; ++kk)
         if (pr == kk) {
-          const double t = r[st];
+          const CT t = r[st];
           r[st] = r[kk];
           r[kk] = t;
         }
@@ -399,20 +416,20 @@ __device__ __forceinline__ int pair_prepare(const double (&a)[4], const double (
       for (int t = 0; t < S; ++t)
         if (cperm[u] == t) inv[t][k] = r[u];
   }
-  double nrm = 0.0;
+  CT nrm = CT(0);
   bool finite = true;
 #pragma unroll
   for (int e = 0; e < S; ++e) {
-    double rs = 0.0;
+    CT rs = CT(0);
 #pragma unroll
     for (int u = 0; u < S; ++u) {
       out[e * S + u] = inv[e][u];
       rs += fabs(inv[e][u]);
     }
-    finite = finite && (rs <= 1.7976931348623157e308);
+    finite = finite && (rs <= Lim<CT>::big());
     nrm = rs > nrm ? rs : nrm;
   }
-  out[S * S] = finite ? nrm : __longlong_as_double(0x7ff0000000000000ll);
+  out[S * S] = finite ? nrm : Lim<CT>::inf();
   return pack;
 }
 
@@ -519,48 +536,50 @@ __device__ inline int merge_blocks(short* blk, short* start, int n, int nblk, un
 //   z01 = i01 (r01 - a12 z11 - b12 z00).
 // Writes Minv row-major and ||Minv||_inf (infinity if not finite) in OutT; returns
 // bit 16 if a part raised its pivot.
-template <typename OutT>
-__device__ __forceinline__ int pair_quad_prepare(const double (&a)[4], const double (&b)[4], double smin, OutT* out) {
+template <typename CT>
+__device__ __forceinline__ int pair_quad_prepare(const double (&a)[4], const double (&b)[4], double smin, CT* out) {
   int flag = 0;
-  auto inv = [&](double d) {
-    if (fabs(d) < smin) {
-      d = smin;
+  const CT sm = static_cast<CT>(smin);
+  auto inv = [&](double dd) {
+    CT d = static_cast<CT>(dd);
+    if (fabs(d) < sm) {
+      d = sm;
       flag = 1 << 16;
     }
-    return 1.0 / d;
+    return CT(1) / d;
   };
-  const double i00 = inv(a[0] + b[0]), i10 = inv(a[3] + b[0]), i01 = inv(a[0] + b[3]), i11 = inv(a[3] + b[3]);
-  const double a12 = a[2], b12 = b[2];
-  const double m[16] = {i00,
+  const CT i00 = inv(a[0] + b[0]), i10 = inv(a[3] + b[0]), i01 = inv(a[0] + b[3]), i11 = inv(a[3] + b[3]);
+  const CT a12 = static_cast<CT>(a[2]), b12 = static_cast<CT>(b[2]);
+  const CT m[16] = {i00,
                         -a12 * i00 * i10,
-                        0.0,
-                        0.0,
-                        0.0,
+                        CT(0),
+                        CT(0),
+                        CT(0),
                         i10,
-                        0.0,
-                        0.0,
+                        CT(0),
+                        CT(0),
                         -b12 * i01 * i00,
                         a12 * b12 * i01 * i10 * (i00 + i11),
                         i01,
                         -a12 * i01 * i11,
-                        0.0,
+                        CT(0),
                         -b12 * i11 * i10,
-                        0.0,
+                        CT(0),
                         i11};
-  double nrm = 0.0;
+  CT nrm = CT(0);
   bool finite = true;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    double rs = 0.0;
+    CT rs = CT(0);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      out[e * 4 + u] = static_cast<OutT>(m[e * 4 + u]);
+      out[e * 4 + u] = m[e * 4 + u];
       rs += fabs(m[e * 4 + u]);
     }
-    finite = finite && (rs <= 1.7976931348623157e308);
+    finite = finite && (rs <= Lim<CT>::big());
     nrm = rs > nrm ? rs : nrm;
   }
-  out[16] = static_cast<OutT>(finite ? nrm : __longlong_as_double(0x7ff0000000000000ll));
+  out[16] = finite ? nrm : Lim<CT>::inf();
   return flag;
 }
 
@@ -570,34 +589,34 @@ __device__ __forceinline__ int pair_quad_prepare(const double (&a)[4], const dou
 // over (top, bottom) rows; pseudo B (columns split, left first):
 // Minv = [[Il, 0], [-b12 Ir Il, Ir]] over (left, right) columns.  Each part has the
 // other side's whole block (1x1 or 2x2).  Same output layout as pair_prepare.
-template <typename OutT>
-__device__ __forceinline__ int pair_half_prepare(int ma, int nb, bool pa, const double (&a)[4], const double (&b)[4],
-                                                 double smin, OutT* out) {
+template <typename CT>
+__device__ __noinline__ int pair_half_prepare(int ma, int nb, bool pa, const double (&a)[4], const double (&b)[4],
+                                                 double smin, CT* out) {
   const int s = ma * nb;
   const int h = pa ? nb : ma;  // size of each part's system (the other side's block)
-  double P0[5], P1[5];          // part inverses (<= 2 x 2, row-major) and norms
+  CT P0[5], P1[5];              // part inverses (<= 2 x 2, row-major) and norms
   double a0[4] = {0.0, 0.0, 0.0, 0.0}, a1[4] = {0.0, 0.0, 0.0, 0.0};
   double b0[4] = {0.0, 0.0, 0.0, 0.0}, b1[4] = {0.0, 0.0, 0.0, 0.0};
   int flags;
   if (pa) {  // part 0: top row (a00), part 1: bottom row (a11); both with B
     a0[0] = a[0];
     a1[0] = a[3];
-    flags = (h == 1) ? (pair_prepare<1, 1>(a0, b, smin, P0) | pair_prepare<1, 1>(a1, b, smin, P1))
-                     : (pair_prepare<1, 2>(a0, b, smin, P0) | pair_prepare<1, 2>(a1, b, smin, P1));
+    flags = (h == 1) ? (pair_prepare<1, 1, CT>(a0, b, smin, P0) | pair_prepare<1, 1, CT>(a1, b, smin, P1))
+                     : (pair_prepare<1, 2, CT>(a0, b, smin, P0) | pair_prepare<1, 2, CT>(a1, b, smin, P1));
   } else {  // part 0: left column (b00), part 1: right column (b11); both with A
     b0[0] = b[0];
     b1[0] = b[3];
-    flags = (h == 1) ? (pair_prepare<1, 1>(a, b0, smin, P0) | pair_prepare<1, 1>(a, b1, smin, P1))
-                     : (pair_prepare<2, 1>(a, b0, smin, P0) | pair_prepare<2, 1>(a, b1, smin, P1));
+    flags = (h == 1) ? (pair_prepare<1, 1, CT>(a, b0, smin, P0) | pair_prepare<1, 1, CT>(a, b1, smin, P1))
+                     : (pair_prepare<2, 1, CT>(a, b0, smin, P0) | pair_prepare<2, 1, CT>(a, b1, smin, P1));
   }
   // Coupled block: pseudo A: top += -a12 It Ib (rows of the top part, columns of the
   // bottom part); pseudo B: right += -b12 Ir Il.
-  const double cpl = pa ? a[2] : b[2];
-  double m[4][4];
+  const CT cpl = static_cast<CT>(pa ? a[2] : b[2]);
+  CT m[4][4];
 #pragma unroll
   for (int e = 0; e < 4; ++e)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) m[e][u] = 0.0;
+    for (int u = 0; u < 4; ++u) m[e][u] = CT(0);
   // vec index of part p, local index t: pseudo A: element (i = p, j = t) -> p + 2t;
   // pseudo B: element (i = t, j = p) -> t + ma p.
 #pragma unroll
@@ -609,7 +628,7 @@ __device__ __forceinline__ int pair_half_prepare(int ma, int nb, bool pa, const 
       const int e1 = pa ? 1 + 2 * t : t + ma, u1 = pa ? 1 + 2 * v : v + ma;  // part 1
       m[e0][u0] = P0[t * h + v];
       m[e1][u1] = P1[t * h + v];
-      double c = 0.0;  // (P_first_solved_after * P_solved_first)[t][v]
+      CT c = CT(0);  // (P_first_solved_after * P_solved_first)[t][v]
 #pragma unroll
       for (int w = 0; w < 2; ++w)
         if (w < h) c = fma(pa ? P0[t * h + w] : P1[t * h + w], pa ? P1[w * h + v] : P0[w * h + v], c);
@@ -618,22 +637,22 @@ __device__ __forceinline__ int pair_half_prepare(int ma, int nb, bool pa, const 
       else
         m[e1][u0] = -cpl * c;  // right column element from the left right-hand side
     }
-  double nrm = 0.0;
+  CT nrm = CT(0);
   bool finite = true;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     if (e >= s) continue;
-    double rs = 0.0;
+    CT rs = CT(0);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (u >= s) continue;
-      out[e * s + u] = static_cast<OutT>(m[e][u]);
+      out[e * s + u] = m[e][u];
       rs += fabs(m[e][u]);
     }
-    finite = finite && (rs <= 1.7976931348623157e308);
+    finite = finite && (rs <= Lim<CT>::big());
     nrm = rs > nrm ? rs : nrm;
   }
-  out[s * s] = static_cast<OutT>(finite ? nrm : __longlong_as_double(0x7ff0000000000000ll));
+  out[s * s] = finite ? nrm : Lim<CT>::inf();
   return flags & (1 << 16);
 }
 
@@ -750,26 +769,21 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
       }
     const bool psa = kMerge && ((sh.apsd >> kb) & 1u), psb = kMerge && ((sh.bpsd >> lb) & 1u);
     FactT* fo = fact + pair_offset(sh, kb, lb, ma);
-    auto prep = [&](double* o) -> int {
-      if (psa || psb) return pair_half_prepare(ma, nb, psa, a, b, smin, o);
-      if (ma == 1 && nb == 1) return pair_prepare<1, 1>(a, b, smin, o);
-      if (ma == 2 && nb == 1) return pair_prepare<2, 1>(a, b, smin, o);
-      if (ma == 1) return pair_prepare<1, 2>(a, b, smin, o);
-      return pair_prepare<2, 2>(a, b, smin, o);
-    };
+    // Computed in the store's precision (binary32 for the binary32 kernel: an inverse
+    // whose norm overflows it is infinite, which sends the pair to the guarded path).
     int pack;
-    if (psa && psb) {
-      pack = pair_quad_prepare(a, b, smin, fo);
-    } else {
-      if constexpr (std::is_same<FactT, double>::value) {
-        pack = prep(fo);
-      } else {
-        double o[17];  // binary32 store: the inverse and its norm are rounded (overflow -> inf: guarded path)
-        pack = prep(o);
-        const int sz = ma * nb;
-        for (int i = 0; i <= sz * sz; ++i) fo[i] = static_cast<FactT>(o[i]);
-      }
-    }
+    if (psa && psb)
+      pack = pair_quad_prepare<FactT>(a, b, smin, fo);
+    else if (psa || psb)
+      pack = pair_half_prepare<FactT>(ma, nb, psa, a, b, smin, fo);
+    else if (ma == 1 && nb == 1)
+      pack = pair_prepare<1, 1, FactT>(a, b, smin, fo);
+    else if (ma == 2 && nb == 1)
+      pack = pair_prepare<2, 1, FactT>(a, b, smin, fo);
+    else if (ma == 1)
+      pack = pair_prepare<1, 2, FactT>(a, b, smin, fo);
+    else
+      pack = pair_prepare<2, 2, FactT>(a, b, smin, fo);
     factp[kb * TT + lb] = pack;
   }
   // Wavefront order of the tile's elements: step s holds the blocks (kb, lb) with

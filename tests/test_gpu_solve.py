@@ -228,6 +228,24 @@ def test_near_singular_reported(sy):
     assert np.all(np.isfinite(Y))
 
 
+def test_near_singular_matches_oracle(orc, sy):
+    """The singular pair of test_near_singular_reported sits in merged pseudo blocks on
+    both sides (rows 2-3 of A, columns 6-7 of B are pairs of 1x1 blocks): the composed
+    inverse raises exactly the 1x1 pivot that the oracle raises, so Y / alpha agrees
+    with the oracle's (normwise, after a common power-of-two shift)."""
+    m, n = 20, 20
+    A = np.triu(np.full((m, m), 0.1), 1) + np.diag(np.linspace(1, 3, m))
+    B = np.triu(np.full((n, n), 0.1), 1) + np.diag(np.linspace(1, 3, n))
+    B[7, 7] = -A[3, 3]
+    C = inputs.rhs(m, n, 1)
+    Y, res = gpu_solve(sy, A, B, C, check=False)
+    ref = orc.trsyl(A, B, C)
+    assert res.info in (sy.SYLV_NEAR_SINGULAR, sy.SYLV_SCALE_UNDERFLOW)
+    Ys = np.ldexp(Y, int(ref["log2scale"]) - int(res.log2scale))
+    s = np.max(np.abs(ref["Y"]))
+    assert np.linalg.norm(Ys / s - ref["Y"] / s) <= 1e-9 * np.linalg.norm(ref["Y"] / s)
+
+
 def test_bounded_wait_times_out_without_hanging(sy):
     """A wait on a flag nothing sets ends with SYLV_ERR_TIMEOUT; the context stays
     usable for the next solve."""

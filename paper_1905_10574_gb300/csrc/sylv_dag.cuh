@@ -801,23 +801,39 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
     sh.sstart[s + 1] = static_cast<short>(cnt);
   }
   __syncthreads();
-  if (tid == 0) {
-    sh.sstart[0] = 0;
-    for (int s = 0; s < nsteps; ++s) sh.sstart[s + 1] = static_cast<short>(sh.sstart[s + 1] + sh.sstart[s]);
+  if (warp == 0) {  // exclusive prefix of the step counts (warp scan, 32 steps a pass)
+    int carry = 0;
+    if (lane == 0) sh.sstart[0] = 0;
+    for (int base = 0; base < nsteps; base += 32) {
+      const int st = base + lane;
+      int v = st < nsteps ? sh.sstart[st + 1] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (st < nsteps) sh.sstart[st + 1] = static_cast<short>(v + carry);
+      carry += __shfl_sync(0xffffffffu, v, 31);
+    }
   }
   __syncthreads();
-  for (int s = tid; s < nsteps; s += kThreads) {
+  // Every pair writes its own elements: its position within its step counts the
+  // step's pairs that come first (more elements, or as many and further left).
+  for (int pidx = tid; pidx < pb * qb; pidx += kThreads) {
+    const int kb = pidx / qb, lb = pidx % qb;
+    const int ra = sh.astart[kb], ma = sh.astart[kb + 1] - ra;
+    const int cb0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - cb0;
+    const int sz = ma * nb;
+    const int s = (pb - 1 - kb) + lw * lb;
     int pos = sh.sstart[s];
-    for (int want = 4; want >= 1; want >>= 1)
-      for (int lb = lw ? max(0, s - (pb - 1)) : 0; lb <= (lw ? min(s, qb - 1) : qb - 1); ++lb) {
-        const int kb = pb - 1 - (s - lw * lb);
-        const int ra = sh.astart[kb], ma = sh.astart[kb + 1] - ra;
-        const int cb0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - cb0;
-        if (ma * nb != want) continue;
-        for (int jc = 0; jc < nb; ++jc)
-          for (int ir = 0; ir < ma; ++ir)
-            sh.eord[pos++] = static_cast<unsigned short>((ra + ir) | ((cb0 + jc) << 6) | ((ir + ma * jc) << 12));
-      }
+    const int lo = lw ? max(0, s - (pb - 1)) : 0, hi = lw ? min(s, qb - 1) : qb - 1;
+    for (int l2 = lo; l2 <= hi; ++l2) {
+      const int k2 = pb - 1 - (s - lw * l2);
+      const int sz2 = (sh.astart[k2 + 1] - sh.astart[k2]) * (sh.bstart[l2 + 1] - sh.bstart[l2]);
+      if (sz2 > sz || (sz2 == sz && l2 < lb)) pos += sz2;
+    }
+    for (int jc = 0; jc < nb; ++jc)
+      for (int ir = 0; ir < ma; ++ir)
+        sh.eord[pos + ir + ma * jc] = static_cast<unsigned short>((ra + ir) | ((cb0 + jc) << 6) | ((ir + ma * jc) << 12));
   }
   __syncthreads();
 }

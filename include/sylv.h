@@ -73,7 +73,9 @@ typedef struct sylv_opts {
   int32_t tile;            /* nominal tile size t (Sec. 2.2); 0 = automatic.  Tiles
                               hold t or t-1 rows so that no 2x2 block is split */
   double omega;            /* overflow threshold Omega; 0 = 2^1020 (2^124 for binary32) */
-  double tol;              /* refinement: stop when max|dY| <= tol * max|Y|; 0 = 2^-46 */
+  double tol;              /* refinement: stop when max|dY| <= tol * max|Y|, or when the
+                              corrections contract and the next one is predicted that small;
+                              0 = 2^-43 */
   int32_t maxit;           /* refinement: at most this many correction solves; 0 = 6 */
   int32_t sync;            /* 1: wait, host result; 0: asynchronous, device result */
   int64_t timeout_ms;      /* bound on each device-side wait; 0 = 20000 */
@@ -95,7 +97,9 @@ typedef struct sylv_result {
   double scale;       /* alpha as a double (0 when alpha < 2^-1074) */
   int32_t info;       /* SYLV_OK, SYLV_NEAR_SINGULAR, SYLV_SCALE_UNDERFLOW, ... */
   int32_t iters;      /* refinement corrections applied (FP32_REFINE), else 0 */
-  double last_update; /* FP32_REFINE: max|dY| / max|Y| of the last correction */
+  double last_update; /* FP32_REFINE: estimated max|error| / max|Y| of the result: the last
+                         correction's relative size, or, when the corrections' contraction
+                         ended the loop, the predicted size of the next one */
   int32_t scale_events; /* number of scaling decisions taken (Sec. 4's "amount of scaling") */
   int32_t min_tile_exp; /* smallest local exponent before consistency scaling */
 } sylv_result;

@@ -361,7 +361,7 @@ int read_opts(const sylv_opts* o, Opts* out) {
   out->maxit = o->maxit > 0 ? o->maxit : 6;
   out->sync = o->sync;
   out->omega = o->omega > 0 ? o->omega : (o->precision == SYLV_FP32_REFINE ? 0x1p124 : 0x1p1020);
-  out->tol = o->tol > 0 ? o->tol : 0x1p-46;
+  out->tol = o->tol > 0 ? o->tol : 0x1p-43;  // ~1.1e-13: a 9x margin under a 1e-12 forward-error target
   out->timeout_ns = (o->timeout_ms > 0 ? o->timeout_ms : 20000) * 1000000LL;
   out->stream = static_cast<cudaStream_t>(o->stream);
   out->ws = o->workspace;

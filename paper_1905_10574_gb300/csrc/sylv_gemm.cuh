@@ -271,7 +271,10 @@ __global__ void k_refine_check(RefineState* rs, const unsigned long long* dmax, 
   if (!conv && dprev) {
     const double dp = __longlong_as_double(static_cast<long long>(*dprev));
     const double rho = dp > 0.0 ? d / dp : 1.0;
-    if (rho < 0.5 && rho * d <= tol * x) conv = true;
+    if (rho < 0.5 && rho * d <= tol * x) {
+      conv = true;
+      rs->last = rho * d / x;  // the predicted size of the next correction
+    }
   }
   if (e) {
     rs->err = e;

@@ -70,13 +70,21 @@ def test_overflow_4000_full_size(orc, sy):
     assert res_nr.info == sy.SYLV_OVERFLOWED
 
 
-def test_mixed_8000_full_size(orc, sy):
-    A, B, C, w = inputs.workload("wellcond_8000")
+@pytest.mark.parametrize("name", ["wellcond_4000", "wellcond_8000"])
+def test_mixed_full_size(orc, sy, name):
+    """FP32 + refinement at full size: the corner against the oracle, and every entry
+    against the robust FP64 solve (itself within ~1e-15 of the oracle, so the
+    comparison measures the refined solution's own error), both within 1e-12."""
+    A, B, C, w = inputs.workload(name)
     Y, res = _gpu(sy, A, B, C, tile=w["tile"], precision="fp32_refine")
     assert res.info == 0 and res.log2scale == 0
+    assert res.iters >= 2 and res.last_update <= 2.0 ** -43
     r0, cb, ref = _corner(orc, A, B, C, 300)
     assert ref["log2scale"] == 0
     assert _rel(Y[r0:, :cb], ref["Y"]) <= FWD_TOL
+    Y64, res64 = _gpu(sy, A, B, C, tile=w["tile"])
+    assert res64.info == 0 and res64.log2scale == 0
+    assert _rel(Y, Y64) <= FWD_TOL
 
 
 def test_batched_4096_sampled(orc, sy):

@@ -590,8 +590,10 @@ __device__ __forceinline__ int pair_quad_prepare(const double (&a)[4], const dou
 // Minv = [[Il, 0], [-b12 Ir Il, Ir]] over (left, right) columns.  Each part has the
 // other side's whole block (1x1 or 2x2).  Same output layout as pair_prepare.
 template <typename CT>
-__device__ __noinline__ int pair_half_prepare(int ma, int nb, bool pa, const double (&a)[4], const double (&b)[4],
-                                                 double smin, CT* out) {
+__device__ __noinline__ int pair_half_prepare(int ma, int nb, bool pa, double a0_, double a1_, double a2_, double a3_,
+                                              double b0_, double b1_, double b2_, double b3_, double smin, CT* out) {
+  // The blocks' entries arrive as scalars, so the caller's arrays stay in registers.
+  const double a[4] = {a0_, a1_, a2_, a3_}, b[4] = {b0_, b1_, b2_, b3_};
   const int s = ma * nb;
   const int h = pa ? nb : ma;  // size of each part's system (the other side's block)
   CT P0[5], P1[5];              // part inverses (<= 2 x 2, row-major) and norms
@@ -775,7 +777,7 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
     if (psa && psb)
       pack = pair_quad_prepare<FactT>(a, b, smin, fo);
     else if (psa || psb)
-      pack = pair_half_prepare<FactT>(ma, nb, psa, a, b, smin, fo);
+      pack = pair_half_prepare<FactT>(ma, nb, psa, a[0], a[1], a[2], a[3], b[0], b[1], b[2], b[3], smin, fo);
     else if (ma == 1 && nb == 1)
       pack = pair_prepare<1, 1, FactT>(a, b, smin, fo);
     else if (ma == 2 && nb == 1)
@@ -1067,8 +1069,9 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
     if (mode == 1) {
       Ys[r + c * LDY] = static_cast<T>(z);
     } else if (mode == 2) {
-      for (int u = 0; u < sz; ++u)
-        Ys[(r0 + (ma == 2 ? (u & 1) : 0)) + (c0 + (ma == 2 ? (u >> 1) : u)) * LDY] = static_cast<T>(rv[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)  // static indices keep rv in registers
+        if (u < sz) Ys[(r0 + (ma == 2 ? (u & 1) : 0)) + (c0 + (ma == 2 ? (u >> 1) : u)) * LDY] = static_cast<T>(rv[u]);
     }
     if (mode != 0 && e == 0) {
       sh.pe[lb] = eb;

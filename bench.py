@@ -57,10 +57,12 @@ def parse():
     ap.add_argument("--sms", default="", help="smscale mode: comma-separated SM counts")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (mixed precision, batched, adjoint)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "mixed", "batched", "adjoint", "smscale", "variants"],
+    ap.add_argument("--mode", default="solve",
+                    choices=["solve", "mixed", "batched", "adjoint", "smscale", "variants", "robustness"],
                     help="solve: the headline robust FP64 solve; mixed: FP32 + refinement vs FP64 at "
                          "m=n=8000; batched: 4096 uneven equations; adjoint: 256 Lyapunov forward+backward; "
-                         "smscale: SM scaling; variants: sign variant, triangular solve, Bartels-Stewart at 4000")
+                         "smscale: SM scaling; variants: sign variant, triangular solve, Bartels-Stewart at 4000; "
+                         "robustness: robust vs plain on the paper's matrices, m=n=10000")
     return ap.parse_args()
 
 
@@ -619,6 +621,50 @@ def run_variants(args):
             "config": {"m": m, "n": n, "tile": 32}, "rows": rows}
 
 
+def run_robustness(args):
+    """The cost-of-robustness sweep on the paper's own matrices (Sec. 3-4): strictly
+    upper ones, diagonal blocks mu*T (A) and nu*T (B) with T in {1, [1 1; -1 1]},
+    C = ones, m = n = 10000, nu = 1e-2 and mu from 1e2 down to 1e-7.  Small mu needs
+    scaling far below the double range (alpha = 2^log2scale); the plain solve
+    (Algorithm 1) overflows there.  Robust and plain times side by side."""
+    import numpy as np
+    import torch
+    from paper_1905_10574_gb300 import build, inputs, sylv
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    m = n = 10000
+    nu = 1e-2
+    F = lambda x: torch.from_numpy(np.asfortranarray(x)).to(dev)  # noqa: E731
+    B = F(inputs.paper_matrix(n, nu, seed=2))
+    C0 = torch.ones((n, m), dtype=torch.float64, device=dev).t()
+    rows = []
+    steps, warm = max(1, args.steps), max(1, args.warmup)
+    for mu in (1e2, 10.0, 1.0, 1e-3, 1e-7):
+        A = F(inputs.paper_matrix(m, mu, seed=1))
+        row = {"mu": mu}
+        for prec in ("fp64", "fp64_nonrobust"):
+            Cs = [C0.clone() for _ in range(steps + warm)]
+            res = sylv.sylv_result()
+
+            def fn(i, prec=prec, res=res):
+                o = sylv.make_opts(precision=prec, stream=stream.cuda_stream)
+                rc = sylv.sylv_tri_solve_ex(m, n, A.data_ptr(), m, B.data_ptr(), n, Cs[i].data_ptr(), m, o, res)
+                if rc >= 100 or rc < 0:
+                    raise sylv.SylvError(rc, prec)
+            ms, _ = _timed(fn, steps, warm, stream)
+            row[prec] = {"ms": ms, "gflops_2mnmn": flops_2(m, n) / ms / 1e6, "info": int(res.info),
+                         "log2scale": int(res.log2scale), "scale_events": int(res.scale_events),
+                         "finite": bool(torch.isfinite(Cs[-1]).all())}
+            del Cs
+        row["overhead"] = row["fp64"]["ms"] / row["fp64_nonrobust"]["ms"] - 1.0
+        rows.append(row)
+    return {"metric": "cost of robustness on the paper's matrices", "value": max(r["overhead"] for r in rows),
+            "unit": "fraction (robust / plain - 1, worst mu)", "n_gpus": 1, "higher_is_better": False,
+            "dtype": "f64", "data": "synthetic (the paper's generator)",
+            "config": {"m": m, "n": n, "nu": nu, "tile": 32}, "rows": rows}
+
+
 def secondary(args):
     """The other configurations, measured briefly beside the headline solve."""
     import argparse as _ap
@@ -655,6 +701,8 @@ def main():
         print(json.dumps(run_smscale(args)), flush=True)
     elif args.mode == "variants":
         print(json.dumps(run_variants(args)), flush=True)
+    elif args.mode == "robustness":
+        print(json.dumps(run_robustness(args)), flush=True)
     else:
         run_ours(args)
 

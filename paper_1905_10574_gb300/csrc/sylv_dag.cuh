@@ -49,6 +49,7 @@ struct DagSmem {
   T L[G * TT * LDG];                  // left GEMM operands, k-major; A_kk in the diagonal phases
   T R[G * TT * LDG];                  // right GEMM operands, k-major; B_ll in the diagonal phases
   int gside[G], gprod[G], gk[G], goff[G];  // the current group of producers
+  int gsop[G];                        // per producer: power of two its Y operand takes (scaled group)
   int gn, gktot, gfast;
   T Y[TT * LDY];                      // the tile being solved (column-major)
   // Small-system inverses in shared memory for tile capacity 32; the tile-64 kernels
@@ -1465,19 +1466,39 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
             pn = tnorm[prod];
             on = opnorm(side, prod);
           }
+          int gsacc = 0;
           if (ROBUST) {
+            // The group is applied in one pass at the smallest exponent eta of the
+            // accumulator and its producers: one-at-a-time Algorithm 3 reaches the same
+            // exponent when no guard fires, and no guard can fire while the summed
+            // bound of the g + 1 terms at eta stays ceil(log2(g + 1)) binades (at least
+            // two) under omega.  Equal exponents need no scaling; otherwise the
+            // accumulator and each producer's Y tile take exact powers of two.
             const bool same = __all_sync(0xffffffffu, lane >= g || ep == sh.e_acc);
-            int emx = lane < g ? ub_log2(on) + ub_log2(pn) : -4096;
+            int emn = lane < g ? ep : 0x7fffffff;
+            for (int o = 16; o > 0; o >>= 1) emn = min(emn, __shfl_xor_sync(0xffffffffu, emn, o));
+            const int eta = min(sh.e_acc, emn);
+            int emx = lane < g ? ub_log2(on) + ub_log2(pn) + (eta - ep) : -4096;
             for (int o = 16; o > 0; o >>= 1) emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
-            emx = max(emx, ub_log2(sh.nb_acc));
-            if (!(same && emx + 2 <= eo)) {
+            emx = max(emx, ub_log2(sh.nb_acc) + (eta - sh.e_acc));
+            const int margin = max(2, 32 - __clz(g));
+            if (!(emx + margin <= eo)) {
               fast = 0;
               g = 1;
             } else {
-              double inc = lane < g ? on * pn : 0.0;  // summed in producer order by lane 0
-              double nb = sh.nb_acc;
+              fast = same ? 1 : 2;
+              const double inc = lane < g ? on * mul2(pn, eta - ep) : 0.0;  // summed in producer order
+              double nb = mul2(sh.nb_acc, eta - sh.e_acc);
               for (int u = 0; u < g; ++u) nb += __shfl_sync(0xffffffffu, inc, u);
-              if (lane == 0) sh.nb_acc = nb;
+              if (lane < g) sh.gsop[lane] = eta - ep;
+              gsacc = eta - sh.e_acc;
+              const bool scaled = __any_sync(0xffffffffu, (lane < g && ep != eta)) || gsacc != 0;
+              __syncwarp();
+              if (lane == 0) {
+                sh.nb_acc = nb;
+                sh.e_acc = eta;
+                if (scaled) ++sh.nscale;
+              }
             }
           }
           int ko = lane < g ? kdim : 0;  // exclusive prefix of the K extents
@@ -1525,7 +1546,7 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
             sh.gn = g;
             sh.gktot = ktot;
             sh.gfast = fast;
-            sh.sacc = 0;
+            sh.sacc = gsacc;
             sh.sop = 0;
           }
         }
@@ -1645,6 +1666,17 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
           T* Yop = (sh.gside[0] == 0) ? sh.R : sh.L;
           const int nel = sh.gk[0] * DagSmem<TT, T>::LDG;
           for (int idx = tid; idx < nel; idx += kThreads) Yop[idx] = mul2(Yop[idx], sop);
+          __syncthreads();
+        }
+        if (sh.gfast == 2) {  // scaled group: each producer's Y operand to the common exponent
+          constexpr int LDG = DagSmem<TT, T>::LDG;
+          for (int u = 0; u < g; ++u) {
+            const int so = sh.gsop[u];
+            if (so == 0) continue;
+            T* Yop = ((sh.gside[u] == 0) ? sh.R : sh.L) + sh.goff[u] * LDG;
+            const int nel = sh.gk[u] * LDG;
+            for (int idx = tid; idx < nel; idx += kThreads) Yop[idx] = mul2(Yop[idx], so);
+          }
           __syncthreads();
         }
         if (sacc != 0) {

@@ -1468,35 +1468,56 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
           }
           int gsacc = 0;
           if (ROBUST) {
-            // The group is applied in one pass at the smallest exponent eta of the
-            // accumulator and its producers: one-at-a-time Algorithm 3 reaches the same
-            // exponent when no guard fires, and no guard can fire while the summed
+            // The group is applied in one pass (Algorithm 3 on the concatenated update
+            // C - [A_1 .. A_g][Y_1; ..; Y_g], bound sum_p ||A_p|| ||Y_p||) at the smallest
+            // exponent eta of the accumulator and its producers, times 2^z with z the
+            // ProtectUpdate factor of the summed bound.  z = 0 whenever the summed
             // bound of the g + 1 terms at eta stays ceil(log2(g + 1)) binades (at least
-            // two) under omega.  Equal exponents need no scaling; otherwise the
-            // accumulator and each producer's Y tile take exact powers of two.
+            // two) under omega; one-at-a-time Algorithm 3 then reaches the same exponent
+            // with no guard firing.  Equal exponents and z = 0 need no scaling;
+            // otherwise the accumulator and each producer's Y tile take exact powers of
+            // two.  A lone producer that needs a guard takes the exact single-producer
+            // ProtectUpdate below.
             const bool same = __all_sync(0xffffffffu, lane >= g || ep == sh.e_acc);
             int emn = lane < g ? ep : 0x7fffffff;
             for (int o = 16; o > 0; o >>= 1) emn = min(emn, __shfl_xor_sync(0xffffffffu, emn, o));
             const int eta = min(sh.e_acc, emn);
-            int emx = lane < g ? ub_log2(on) + ub_log2(pn) + (eta - ep) : -4096;
+            const int ea = ub_log2(on);
+            int emx = lane < g ? ea + ub_log2(pn) + (eta - ep) : -4096;
             for (int o = 16; o > 0; o >>= 1) emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
             emx = max(emx, ub_log2(sh.nb_acc) + (eta - sh.e_acc));
             const int margin = max(2, 32 - __clz(g));
-            if (!(emx + margin <= eo)) {
+            const bool fits = emx + margin <= eo;
+            if (!fits && g == 1) {
               fast = 0;
-              g = 1;
             } else {
-              fast = same ? 1 : 2;
-              const double inc = lane < g ? on * mul2(pn, eta - ep) : 0.0;  // summed in producer order
-              double nb = mul2(sh.nb_acc, eta - sh.e_acc);
-              for (int u = 0; u < g; ++u) nb += __shfl_sync(0xffffffffu, inc, u);
-              if (lane < g) sh.gsop[lane] = eta - ep;
-              gsacc = eta - sh.e_acc;
-              const bool scaled = __any_sync(0xffffffffu, (lane < g && ep != eta)) || gsacc != 0;
+              int z = 0;
+              double nb;
+              if (fits) {
+                const double inc = lane < g ? on * mul2(pn, eta - ep) : 0.0;  // summed in producer order
+                nb = mul2(sh.nb_acc, eta - sh.e_acc);
+                for (int u = 0; u < g; ++u) nb += __shfl_sync(0xffffffffu, inc, u);
+              } else {
+                // Terms normalised by 2^-emx (each <= 1, no overflow), summed in
+                // producer order with a 2^-50 rounding margin; z is the largest power
+                // of two with 2^z * sum * 2^emx <= omega.
+                const double tn = lane < g ? mul2(on, -ea) * mul2(pn, (eta - ep) - (emx - ea)) : 0.0;
+                double sn = mul2(sh.nb_acc, (eta - sh.e_acc) - emx);
+                for (int u = 0; u < g; ++u) sn += __shfl_sync(0xffffffffu, tn, u);
+                sn *= 1.0 + 0x1p-50;
+                // omega = 2^eo f, f in [1, 2): z = (eo - emx) + floor(log2(f / sn))
+                z = sn > 0.0 ? min(0, (eo - emx) + floor_log2(mul2(omega, -eo) / sn)) : 0;
+                nb = mul2(sn, emx + z);
+              }
+              fast = (same && z == 0) ? 1 : 2;
+              const int delta = eta + z;
+              if (lane < g) sh.gsop[lane] = delta - ep;
+              gsacc = delta - sh.e_acc;
+              const bool scaled = __any_sync(0xffffffffu, (lane < g && ep != delta)) || gsacc != 0;
               __syncwarp();
               if (lane == 0) {
                 sh.nb_acc = nb;
-                sh.e_acc = eta;
+                sh.e_acc = delta;
                 if (scaled) ++sh.nscale;
               }
             }

@@ -186,7 +186,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_1905_10574_gb300 import build, inputs, sylv
+    from paper_1905_10574_gb300 import build, inputs, replicas, sylv
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -239,11 +239,7 @@ def run_ours(args):
     clocks = sampler.stop()
     if ws > 1:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    tmax = torch.tensor([ms], device=device, dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_max = float(tmax.item())
+    ms_max = replicas.max_over_ranks(e0.elapsed_time(e1))
     # per-step results (the last timed solve)
     res = sylv.sylv_result.from_buffer_copy(res_dev[64 * (nsteps - 1): 64 * (nsteps - 1) + 40].cpu().numpy().tobytes())
     ok = res.info in (sylv.SYLV_OK, sylv.SYLV_NEAR_SINGULAR)
@@ -278,15 +274,11 @@ def run_ours(args):
         e2e_step()
     f1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1) / esteps
-    e2e_max = torch.tensor([e2e_ms], device=device, dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(e2e_max, op=dist.ReduceOp.MAX)
-    e2e_ms = float(e2e_max.item())
+    e2e_ms = replicas.max_over_ranks(f0.elapsed_time(f1) / esteps)
 
     if rank == 0:
         per_step = ms_max / args.steps
-        value = ws * flops_2(m, n) / (per_step / 1000) / 1e9
+        value = replicas.whole_job_rate(flops_2(m, n), ws, per_step / 1000) / 1e9
         dag_per_launch_ms = dag_ms / max(dag_launches, 1)
         achieved = flops_alg(m, n) / (dag_per_launch_ms / 1000) / 1e9
         traffic = traffic_for_dag()
@@ -305,7 +297,7 @@ def run_ours(args):
                          "flops_per_launch": flops_alg(m, n),
                          "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived); a DFMA loop measured "
                                       "1184 GFLOP/s at ~1.98 GHz"},
-            "e2e": {"value": ws * flops_2(m, n) / (e2e_ms / 1000) / 1e9, "unit": "GFLOP/s",
+            "e2e": {"value": replicas.whole_job_rate(flops_2(m, n), ws, e2e_ms / 1000) / 1e9, "unit": "GFLOP/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 10 * args.steps,  # per solve: set_inst, scan, norms, 3 level kernels, pack, DAG, consistency, results
             "clocks": clocks,
@@ -435,16 +427,27 @@ def run_smscale(args):
 def run_batched(args):
     """4096 independent equations, m, n log-uniform in [16, 512]: autotuned tile per
     size bucket, one batched persistent launch captured in a CUDA graph and replayed;
-    against the plain path solving the same equations one call at a time (sampled)."""
+    against the plain path solving the same equations one call at a time (sampled).
+    On N GPUs (torchrun) the equations are split by flops, longest first (no exchange
+    but the slowest rank's time); the value is all 4096 over that time."""
     import numpy as np
     import torch
-    from paper_1905_10574_gb300 import autotune, build, inputs, sylv
+    import torch.distributed as dist
+    from paper_1905_10574_gb300 import autotune, build, inputs, replicas, sylv
     build.build()
-    count = 4096
-    shapes = inputs.batch_shapes(count, 16, 512, seed=1234)
-    dev = torch.device("cuda", 0)
+    ws, rank, local = dist_env()
+    own_pg = ws > 1 and not dist.is_initialized()
+    if own_pg:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    total = 4096
+    all_shapes = inputs.batch_shapes(total, 16, 512, seed=1234)
+    mine = replicas.lpt_shards([m * n * (m + n) for m, n in all_shapes], ws)[rank] if ws > 1 else range(total)
+    shapes = [all_shapes[i] for i in mine]
+    count = len(shapes)
+    dev = torch.device("cuda", local)
     As, Bs, C0s = [], [], []
-    for i, (m, n) in enumerate(shapes):
+    for i, (m, n) in zip(mine, shapes):
         A, B, C = inputs.problem(m, n, 10000 + i, kind="wellcond")
         As.append(torch.from_numpy(A).to(dev))
         Bs.append(torch.from_numpy(B).to(dev))
@@ -482,7 +485,19 @@ def run_batched(args):
             ts.append(a.elapsed_time(b))
     rc, res = sylv.sylv_batch_results(plan, count)
     sylv.sylv_batch_destroy(plan)
-    ms = sum(ts) / len(ts)
+    ms = replicas.max_over_ranks(sum(ts) / len(ts))  # the slowest rank's time
+    if ws > 1:
+        worst = int(replicas.max_over_ranks(max(r.info for r in res)))
+        if own_pg:
+            dist.destroy_process_group()
+        if rank != 0:
+            return None
+        return {"metric": "batched solves/s", "value": total / (ms / 1000), "unit": "solves/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "strong", "dtype": "f64", "data": "synthetic",
+                "config": {"count": total, "m_n": "log-uniform [16,512]", "generator": "wellcond",
+                           "split": "longest processing time first, by 2mn(m+n)", "cuda_graph": True},
+                "worst_info": worst}
     # plain path, one call per equation, on a sample of 256 equations (scaled to 4096)
     sample = list(range(0, count, count // 256))
     cur = torch.cuda.current_stream(dev)
@@ -694,7 +709,9 @@ def main():
     elif args.mode == "mixed":
         print(json.dumps(run_mixed(args)), flush=True)
     elif args.mode == "batched":
-        print(json.dumps(run_batched(args)), flush=True)
+        line = run_batched(args)
+        if line is not None:
+            print(json.dumps(line), flush=True)
     elif args.mode == "adjoint":
         print(json.dumps(run_adjoint(args)), flush=True)
     elif args.mode == "smscale":

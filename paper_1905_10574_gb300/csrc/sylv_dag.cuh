@@ -1404,10 +1404,11 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
     // tile (0 <= q < d): while only one side has producers left to start, that side;
     // afterwards A side then B side per anti-diagonal.  Up to G producers whose
     // flags are already set are staged back to back and applied in one GEMM pass;
-    // each element still receives their products in producer order (identical
-    // arithmetic to one at a time) as long as no scaling is needed -- when a group
-    // member's exponent differs from the accumulator's or the bounds come near
-    // omega, the group shrinks to one producer with the exact ProtectUpdate.
+    // each element still receives their products in producer order.  With equal
+    // exponents and bounds far from omega that is the arithmetic of one at a time;
+    // otherwise the group takes one exponent and one ProtectUpdate factor (scaling
+    // its tiles by exact powers of two), and a lone producer near omega the exact
+    // single-producer ProtectUpdate.
     // Without a B term (nob) only the tiles below contribute: d = p-1-k, all on the A side.
     const int lq = I.nob ? 0 : l;
     const int d = (p - 1 - k) + lq;

@@ -1442,31 +1442,36 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
     };
     for (int q = 0; q < d && !sh.abort;) {
       if (tid < 32) {
-        // Warp 0 forms the group: lane u looks at producer q + u; lane 0 waits for
-        // its flag (bounded), the others only test theirs, and the group is the
-        // ready prefix.  Flags, exponents and norms are fetched by all lanes at once.
+        // Warp 0 forms the group: lane u looks at producer q + u.  Every candidate's
+        // flag (acquire) and operator norm (independent of readiness) are fetched in
+        // one round trip; lane 0 then waits for its flag (bounded) if it was not set,
+        // and the group is the ready prefix.  Exponents and bounds are read after the
+        // acquire that saw their flag set.
         constexpr int G = DagSmem<TT, T>::G;
         const int lane = tid;
         int side = 0, prod = 0, kdim = 0;
         const bool cand = lane < G && q + lane < d;
         if (cand) producer(q + lane, side, prod, kdim);
+        int fl = cand ? ld_acquire(&tflag[prod]) : 0;
+        double on = 0.0;
+        if (ROBUST && cand) on = opnorm(side, prod);
         int okw = 1;
-        if (lane == 0) okw = wait_flag(&tflag[prod], ctrl, w.timeout_ns) ? 1 : 0;
+        if (lane == 0 && !fl) okw = wait_flag(&tflag[prod], ctrl, w.timeout_ns) ? 1 : 0;
         okw = __shfl_sync(0xffffffffu, okw, 0);
         if (!okw) {
           if (lane == 0) sh.abort = 1;
         } else {
-          const bool ready = cand && (lane == 0 || ld_acquire(&tflag[prod]) != 0);
+          const bool ready = cand && (lane == 0 || fl != 0);
           const unsigned nr = ~__ballot_sync(0xffffffffu, ready);
           int g = nr ? __ffs(nr) - 1 : 32;  // the ready prefix (lane 0 is ready)
           int fast = 1;
           int ep = 0;
-          double pn = 0.0, on = 0.0;
+          double pn = 0.0;
           if (ROBUST && lane < g) {
             ep = texp[prod];
             pn = tnorm[prod];
-            on = opnorm(side, prod);
           }
+          if (lane >= g) on = 0.0;
           int gsacc = 0;
           if (ROBUST) {
             // The group is applied in one pass (Algorithm 3 on the concatenated update

@@ -233,6 +233,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&v)[16]) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // The two products of one launch: left operands (R = 128) and right operands (R = 64).
+// Row panels per group of the output-tile order (8 x 19 panels resident at once).
+constexpr int kGroupRows = 8;
+
 struct Gemm {
   Packed a[2];
   Packed b[2];
@@ -270,8 +273,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   Smem& sh = *reinterpret_cast<Smem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * BM, j0 = static_cast<int64_t>(blockIdx.y) * BN;
-  const int mb = blockIdx.x, nb = blockIdx.y;
+  // Output tiles in L2-friendly order: the launch runs through groups of kGroupRows
+  // row panels, column panels fastest within a group, so that the CTAs resident at
+  // once share a few row panels of A (and of X) and a set of column panels instead
+  // of streaming every row panel's slices through L2 again for each column wave.
+  int mb, nb;
+  {
+    const int MBt = gridDim.x, NBt = gridDim.y;
+    const int id = blockIdx.x + MBt * blockIdx.y;
+    const int gsize = kGroupRows * NBt;
+    const int grp = id / gsize, in = id - grp * gsize;
+    const int rows = min(kGroupRows, MBt - grp * kGroupRows);
+    mb = grp * kGroupRows + in % rows;
+    nb = in / rows;
+  }
+  const int64_t i0 = static_cast<int64_t>(mb) * BM, j0 = static_cast<int64_t>(nb) * BN;
   const int smax = min(kSlices, maxw - 1);  // slices in use
 
   if (tid == 0) {

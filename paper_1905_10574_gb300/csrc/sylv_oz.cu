@@ -84,12 +84,11 @@ cudaError_t oz_residual(const OzBuffers& b, const double* X, int64_t ldx, const 
   g.b[0] = packed(b, 1);
   g.a[1] = packed(b, 2);
   g.b[1] = packed(b, 3);
-  e = cudaFuncSetAttribute(oz::k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(sizeof(oz::Smem)));
+  auto kern = binary64 ? oz::k_oz_gemm<oz::kMaxW> : oz::k_oz_gemm<oz::kMaxW32>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sizeof(oz::Smem)));
   if (e != cudaSuccess) return e;
   const dim3 grid(static_cast<unsigned>(cdiv(m, oz::BM)), static_cast<unsigned>(cdiv(n, oz::BN)));
-  oz::k_oz_gemm<<<grid, oz::kThreads, sizeof(oz::Smem), s>>>(g, binary64 ? oz::kMaxW : oz::kMaxW32, C, ldc, R,
-                                                               ldr, m, n, rmax, err, timeout_ns, skip);
+  kern<<<grid, oz::kThreads, sizeof(oz::Smem), s>>>(g, C, ldc, R, ldr, m, n, rmax, err, timeout_ns, skip);
   return cudaGetLastError();
 }
 

@@ -7,26 +7,29 @@
 // binary32 accumulation).  Every row r of the left operand gets a power of two
 // 2^e_r above its largest magnitude, and every value v of the row is written as
 //     v = 2^e_r * sum_{s=1..S} a_s 2^(-8s) + (error below 2^(e_r - 8S)),
-// with integer slices a_1 in [-256, 256] and a_s in [-128, 128] for s > 1 (each an
-// exact bf16).  The right operand is split the same way per column.  A product of
-// two slices is an integer of magnitude <= 2^16, so a sum of 256 of them is an
-// exact integer below 2^24 and the tensor core's binary32 accumulation of it is
-// exact: the kernel accumulates chunks of 256 in TMEM, converts each chunk to
-// int32 (exact) and sums chunks in int32, pairs of equal weight 2^(-8(s+t))
-// together; every 64 chunks or at the end of a weight it adds the integer, scaled
-// by 2^(e_r + e_c - 8(s+t)), into a binary64 accumulator.  Pairs with s + t > S + 1
-// are dropped: with S = 7 they weigh below 2^-56 of (row maximum) x (column maximum)
-// per product term, as do the truncated slices; the binary64 sums of the ~14
-// flushes per element add rounding below 2^-49 of the products' magnitude.  The
+// with integer slices a_1 in [-256, 256] and a_s in [-128, 128] for s > 1, stored
+// pre-scaled as the exact bf16 values a_s 2^(-8(s-1)).  The right operand is split
+// the same way per column.  A product of two integer slices has magnitude <= 2^16,
+// so a sum of 256 of them is an exact integer below 2^24 and the tensor core's
+// binary32 accumulation of it is exact (a power-of-two scale changes nothing): the
+// kernel accumulates the pairs of each of the three leading weights s + t = 2, 3, 4
+// in chunks of 192 in TMEM, converts each chunk to integers (exact) and sums the
+// chunks in one int64 per element; each smaller weight has a binary32 accumulator
+// of its own; at the end of a product both go, scaled by 2^(e_r + e_c - 32), into R
+// in binary64.  Pairs with s + t > S + 1 are dropped: with S = 7 they weigh below
+// 2^-56 of (row maximum) x (column maximum) per product term, as does the rounding
+// of the elements to 56 bits; the binary32 sums of the smaller weights are rounded
+// at 2^-24 of terms that are themselves below 2^-24 of the leading ones, and the two
+// binary64 updates of each element (one per product) round at 2^-53.  The
 // guarantee is relative to the row and column maxima (normwise): with balanced rows
 // and columns it is about 2^-48 componentwise (|A||X| + |X||B|), like the
 // double-float kernel it replaces; rows dominated by one large entry (a heavy
 // diagonal) keep correspondingly fewer bits of their small entries.
 //
 // Layouts.  Operand slices are stored pre-tiled in the canonical no-swizzle K-major
-// layout of tcgen05: a tile is R rows x 64 K elements (R = 128 for the left
+// layout of tcgen05: a tile is R rows x 16 K elements (R = 128 for the left
 // operand, 64 for the right), made of 8 x 8 core matrices (8 rows of 16 bytes,
-// 128 contiguous bytes), core matrix (row/8, k/8) at index (row/8)*8 + k/8.  A tile
+// 128 contiguous bytes), core matrix (row/8, k/8) at index (row/8)*2 + k/8.  A tile
 // is contiguous, so one 1D bulk copy (cp.async.bulk) moves it into shared memory.
 // Products: A X uses A (rows of A, K = columns, quasi-upper mask) and X by columns
 // (N = columns of X, K = rows); X B uses X by rows (K = columns of X) and B by
@@ -37,12 +40,8 @@
 // in place (C = R): the correction D is small, and its product needs only to be
 // well below the next residual.
 //
-// The GEMM kernel: one CTA per 128 x 64 tile of R, 192 threads.  Warp 4 issues the
-// bulk copies into a 4-stage shared-memory ring (mbarriers with transaction
-// counts), one thread of warp 5 issues the MMAs (M = 128, N = 64, K = 16) into two
-// TMEM accumulators used alternately per chunk, and warps 0-3 (one TMEM lane
-// quarter each, one row of the tile per thread) take each finished chunk out of
-// TMEM.  Every wait is bounded; a timeout records SYLV_ERR_TIMEOUT.
+// The GEMM kernel: one CTA per 128 x 64 tile of R, 320 threads (details at the
+// kernel).  Every wait is bounded; a timeout records SYLV_ERR_TIMEOUT.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -55,13 +54,12 @@ namespace oz {
 constexpr int kSlices = 7;             // 8-bit slices per operand (56 bits below the maximum)
 constexpr int kMaxW = kSlices + 1;     // binary64 residual: pairs (s, t), 1-based, with s + t <= kMaxW
 constexpr int kMaxW32 = 6;             // products for the binary32 recurrence: s + t <= 6 (40 bits)
-constexpr int BM = 128, BN = 64, BK = 32;
+constexpr int BM = 128, BN = 64, BK = 16;
 constexpr int kLeadW = 4;              // weights 2..4 are accumulated exactly (chunked)
-constexpr int kLeadStages = 6;         // 6 K blocks of 32 per exact binary32 chunk (< 2^24, see below)
-constexpr int kFlushLead = 64;         // chunks per int32 sum: 64 * 2^24 = 2^30 < 2^31
-constexpr int NST = 2;                 // shared-memory stages (all slices of one K block each)
-constexpr int kTileA = BM * BK;        // bf16 elements of a left-operand tile (8 KB)
-constexpr int kTileB = BN * BK;        // of a right-operand tile (4 KB)
+constexpr int kLeadStages = 12;        // 12 K blocks of 16 per exact binary32 chunk (< 2^24, see below)
+constexpr int NST = 5;                 // shared-memory stages (all slices of one K block each)
+constexpr int kTileA = BM * BK;        // bf16 elements of a left-operand tile (4 KB)
+constexpr int kTileB = BN * BK;        // of a right-operand tile (2 KB)
 constexpr int kEpiWarps = 8;           // two per TMEM lane quarter, 32 columns each
 constexpr int kThreads = 32 * (kEpiWarps + 2);
 
@@ -121,9 +119,33 @@ __global__ void k_oz_rowexp(View v, int* e, int64_t rows_padded, const int* skip
   }
 }
 
+// round(x * 2^(56 - e)) as an integer, for |x| < 2^e: the element on the grid of
+// its row's 56 bits (|result| <= 2^56), from the bits of x alone.
+__device__ __forceinline__ long long fixed56(double x, int e) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int E = static_cast<int>((b >> 52) & 0x7ff);
+  unsigned long long M = b & ((1ull << 52) - 1);
+  if (E != 0) M |= 1ull << 52;
+  const int sh = (E != 0 ? E : 1) - 1019 - e;  // x = +-M 2^(E - 1075)
+  long long v;
+  if (sh >= 0)
+    v = static_cast<long long>(M << sh);  // M 2^sh < 2^56
+  else if (sh > -60)
+    v = static_cast<long long>((M + (1ull << (-sh - 1))) >> (-sh));
+  else
+    v = 0;
+  return (b >> 63) ? -v : v;
+}
+
 // Slices of every element, one block per packed tile: the tile is read along its
 // contiguous dimension into shared memory (rows when rs == 1, else K), then each
 // thread takes positions of the packed layout and writes all kSlices slices of each.
+// In integers: V = round(x 2^(56 - e_r)), then signed base-256 digits from the top,
+// q_1 = round(V / 2^48), V -= q_1 2^48, q_2 = round(V / 2^40), ..., q_7 = V, so that
+// |q_1| <= 256, |q_s| <= 128 and x = 2^(e_r - 8) sum_s q_s 2^(-8(s-1)) to within
+// 2^(e_r - 57).  Slice s is stored pre-scaled, q_s 2^(-8(s-1)) (exact in bf16), so
+// that a product of slices s and t carries its weight 2^(-8(s+t-2)) relative to
+// the leading pair.  Infinities and NaN give NaN slices.
 __global__ void __launch_bounds__(256) k_oz_split(View v, Packed P, const int* skip) {
   if (skip && ld_volatile(skip)) return;
   __shared__ double tile[BM * (BK + 1)];
@@ -143,13 +165,20 @@ __global__ void __launch_bounds__(256) k_oz_split(View v, Packed P, const int* s
       const int cm = o >> 6, w = o & 63;  // core matrix (rr/8) * (BK/8) + kk/8, then row-major 8 x 8
       const int rr = (cm / (BK / 8)) * 8 + (w >> 3), kk = (cm % (BK / 8)) * 8 + (w & 7);
       const double x = tile[rr * (BK + 1) + kk];
-      double u = (x == 0.0) ? 0.0 : mul2(x, 8 - P.e[r0 + rr]);  // |u| < 256
+      const bool finite = ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+      long long V = finite ? fixed56(x, P.e[r0 + rr]) : 0;
       const int64_t idx = t * tsz + o;
 #pragma unroll
       for (int s = 0; s < kSlices; ++s) {
-        const double q = rint(u);
-        P.p[idx + s * per] = __float2bfloat16_rn(static_cast<float>(q));  // exact: |q| <= 256, an integer
-        u = (u - q) * 256.0;                                              // exact
+        const int sh = 8 * (kSlices - 1 - s);
+        long long q = V;
+        if (sh > 0) {
+          q = (V + (1ll << (sh - 1))) >> sh;
+          V -= q << sh;
+        }
+        const float scale = __int_as_float((127 - 8 * s) << 23);  // 2^(-8s)
+        const float f = finite ? static_cast<float>(static_cast<int>(q)) * scale : __int_as_float(0x7fc00000);
+        P.p[idx + s * per] = __float2bfloat16_rn(f);  // exact: an integer of at most 9 bits times 2^(-8s)
       }
     }
   }
@@ -253,22 +282,55 @@ __device__ __forceinline__ void kb_range(int p, const Gemm& g, int64_t i0, int64
   }
 }
 
-// Exactness of the leading weights.  Per K block of 32, weight 2 (pair (1,1)) adds at
-// most 32 * 2^16 = 2^21 in magnitude, weight 3 (pairs (1,2), (2,1)) 2 * 32 * 2^15 =
-// 2^21, weight 4 ((1,3), (3,1), (2,2)) 32 * (2^15 + 2^15 + 2^14) < 2^21.33; six blocks
-// stay below 2^24, so those accumulators are taken out of TMEM exactly every six
-// blocks (integers, exact in binary32).  Weights >= 5 are accumulated over the whole
-// K range in binary32: their rounding is below 2^-24 of a sum that is itself below
-// 2^-24 of the leading term, so below 2^-48 of the result.
-//
+// Exactness of the leading weights.  Per K block of 16, weight 2 (pair (1,1)) adds at
+// most 16 * 2^16 = 2^20 in magnitude, weight 3 (pairs (1,2), (2,1)) 2 * 16 * 2^15 =
+// 2^20, weight 4 ((1,3), (3,1), (2,2)) 16 * (2^15 + 2^15 + 2^14) = 1310720, counted
+// as integers; twelve blocks stay below 2^24 (15728640).  With the pre-scaled slices
+// the accumulator of weight w holds its integer sum times 2^(-8(w-2)), a power of two
+// that keeps every partial sum exact in binary32, so those three accumulators are
+// taken out of TMEM exactly every twelve blocks.  Each weight >= 5 has its own
+// binary32 accumulator over the whole K range: its rounding is below 2^-24 of a sum
+// that is itself below 2^-24 of the leading term, so below 2^-48 of the result.
+// (One accumulator shared by all weights >= 5 loses more: the tensor core adds the
+// small weights' products to a running sum up to 2^24 times larger, and at K = 300
+// the error measured 2^-40 of the leading term.)
+
+// Descriptor steps (16-byte units): one slice tile within a stage, one stage.
+constexpr uint64_t kDescSliceA = kTileA * 2 / 16, kDescSliceB = kTileB * 2 / 16;
+constexpr uint64_t kDescStageA = kSlices * kDescSliceA, kDescStageB = kSlices * kDescSliceB;
+static_assert(BK == 16, "one MMA (K = 16) per slice pair and K block");
+
+// Every slice pair (sl, w - sl) of weights W0..W1 of one staged K block, into the
+// accumulator of its weight (TMEM columns 64 (w - 2)..), the first pair of each
+// weight overwriting it unless acc0 is set.  Fully unrolled: the descriptors are the
+// stage's base plus constants (a shared address below 256 KB never carries out of
+// the 14-bit address field), so one thread issues an MMA in a few instructions.
+template <int W0, int W1, int SMAX>
+__device__ __forceinline__ void issue_weights(uint32_t tbase, uint64_t da, uint64_t db, uint32_t acc0) {
+#pragma unroll
+  for (int w = W0; w <= W1; ++w) {
+    const int first = w - SMAX > 1 ? w - SMAX : 1;
+#pragma unroll
+    for (int sl = 1; sl <= SMAX; ++sl) {
+      const int t = w - sl;
+      if (t < 1 || t > SMAX) continue;
+      umma(tbase + static_cast<uint32_t>((w - 2) * BN), da + (sl - 1) * kDescSliceA, db + (t - 1) * kDescSliceB,
+           sl == first ? acc0 : 1u);
+    }
+  }
+}
+
 // The kernel.  One CTA per 128 x 64 tile of R; warp 8 loads, one thread of warp 9
 // issues the MMAs, warps 0-7 drain TMEM (warp w: TMEM lanes 32 (w & 3).., tile
 // columns 32 (w >> 2)..).  Per K block a stage holds all slices of both operands,
-// and every slice pair of weight <= maxw goes into the accumulator of its weight
-// (TMEM columns 64 (w - 2)..).  R starts as C and every flush subtracts its terms.
+// and every slice pair of weight <= MAXW goes into the accumulator of its weight
+// (TMEM columns 64 (w - 2)..).  R starts as C and the end of each product subtracts
+// its terms.
+template <int MAXW>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_oz_gemm(Gemm g, int maxw, const double* C, int64_t ldc, double* R, int64_t ldr, int64_t m, int64_t n,
+    k_oz_gemm(Gemm g, const double* C, int64_t ldc, double* R, int64_t ldr, int64_t m, int64_t n,
               unsigned long long* rmax, int* err, long long timeout_ns, const int* skip) {
+  constexpr int SMAX = MAXW - 1 < kSlices ? MAXW - 1 : kSlices;  // slices in use
   if (skip && ld_volatile(skip)) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   Smem& sh = *reinterpret_cast<Smem*>(smem_raw);
@@ -288,7 +350,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     nb = in / rows;
   }
   const int64_t i0 = static_cast<int64_t>(mb) * BM, j0 = static_cast<int64_t>(nb) * BN;
-  const int smax = min(kSlices, maxw - 1);  // slices in use
 
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -311,9 +372,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == kEpiWarps) {
     // ---- loads: all slices in use of one K block per stage
     if (lane == 0) {
-      int gs = 0;
+      int st = 0;
+      uint32_t ph = 0;
       bool ok = true;
-      const uint32_t bytes = static_cast<uint32_t>(smax) * (kTileA + kTileB) * 2;
+      constexpr uint32_t bytes = static_cast<uint32_t>(SMAX) * (kTileA + kTileB) * 2;
       for (int p = 0; p < 2 && ok; ++p) {
         int lo, hi;
         kb_range(p, g, i0, j0, lo, hi);
@@ -321,18 +383,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         const Packed& B = g.b[p];
         const __nv_bfloat16* ab = A.p + (static_cast<int64_t>(mb) * A.KB) * kTileA;
         const __nv_bfloat16* bb = B.p + (static_cast<int64_t>(nb) * B.KB) * kTileB;
-        for (int kb = lo; kb < hi; ++kb, ++gs) {
-          const int st = gs & 1;
-          if (!mbar_wait(&sh.empty[st], ((gs >> 1) & 1) ^ 1, err, timeout_ns)) {
+        for (int kb = lo; kb < hi; ++kb) {
+          if (!mbar_wait(&sh.empty[st], ph ^ 1, err, timeout_ns)) {
             ok = false;
             break;
           }
           mbar_expect_tx(&sh.full[st], bytes);
-          for (int sl = 0; sl < smax; ++sl) {
+#pragma unroll
+          for (int sl = 0; sl < SMAX; ++sl) {
             bulk_g2s(sh.a[st][sl], ab + sl * A.slice_elems() + static_cast<int64_t>(kb) * kTileA, kTileA * 2,
                      &sh.full[st]);
             bulk_g2s(sh.b[st][sl], bb + sl * B.slice_elems() + static_cast<int64_t>(kb) * kTileB, kTileB * 2,
                      &sh.full[st]);
+          }
+          if (++st == NST) {
+            st = 0;
+            ph ^= 1;
           }
         }
       }
@@ -341,16 +407,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == kEpiWarps + 1) {
     // ---- MMAs
     if (lane == 0) {
-      int gs = 0, ev = 0, pend = -1;  // pend: event whose drain must end before the accumulators it frees are reused
+      int st = 0, ev = 0, pend = -1;  // pend: event whose drain must end before the accumulators it frees are reused
+      uint32_t ph = 0;
       bool pend_all = false, ok = true;
+      const uint64_t da0 = sdesc(su32(sh.a[0][0]), 128, (BK / 8) * 128);
+      const uint64_t db0 = sdesc(su32(sh.b[0][0]), 128, (BK / 8) * 128);
       for (int p = 0; p < 2 && ok; ++p) {
         int lo, hi;
         kb_range(p, g, i0, j0, lo, hi);
-        unsigned written = 0;  // weights written since their last drain
-        int since = 0;
-        for (int kb = lo; kb < hi && ok; ++kb, ++gs) {
-          const int st = gs & 1;
-          if (!mbar_wait(&sh.full[st], (gs >> 1) & 1, err, timeout_ns)) {
+        int since = 0;  // K blocks of the current chunk of the leading weights
+        for (int kb = lo; kb < hi; ++kb) {
+          if (!mbar_wait(&sh.full[st], ph, err, timeout_ns)) {
             ok = false;
             break;
           }
@@ -363,38 +430,30 @@ __global__ void __launch_bounds__(kThreads, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             pend = -1;
           }
-          for (int pass = 0; pass < 2; ++pass) {  // weights >= 5 first, then the leading ones
-            if (pass == 1 && pend >= 0) {  // the leading accumulators are being drained
-              if (!mbar_wait(&sh.accempty, pend & 1, err, timeout_ns)) {
-                ok = false;
-                break;
-              }
-              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              pend = -1;
+          const uint64_t da = da0 + st * kDescStageA, db = db0 + st * kDescStageB;
+          // weights above kLeadW first (their accumulators live for the whole product),
+          // then the leading ones, once their previous chunk has been drained
+          issue_weights<kLeadW + 1, MAXW, SMAX>(tbase, da, db, kb != lo ? 1u : 0u);
+          if (pend >= 0) {
+            if (!mbar_wait(&sh.accempty, pend & 1, err, timeout_ns)) {
+              ok = false;
+              break;
             }
-            for (int w = pass ? 2 : kLeadW + 1; w <= (pass ? kLeadW : maxw); ++w)
-              for (int sl = max(1, w - smax); sl <= min(smax, w - 1); ++sl) {
-                const int t = w - sl;
-                const uint32_t aa = su32(sh.a[st][sl - 1]), ba = su32(sh.b[st][t - 1]);
-                const uint32_t dtm = tbase + static_cast<uint32_t>((w - 2) * BN);
-#pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) {
-                  const bool acc = ((written >> w) & 1u) != 0;
-                  umma(dtm, sdesc(aa + kk * 256, 128, (BK / 8) * 128), sdesc(ba + kk * 256, 128, (BK / 8) * 128),
-                       acc ? 1u : 0u);
-                  written |= 1u << w;
-                }
-              }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            pend = -1;
           }
-          if (!ok) break;
+          issue_weights<2, kLeadW, SMAX>(tbase, da, db, since != 0 ? 1u : 0u);
           umma_commit(&sh.empty[st]);
+          if (++st == NST) {
+            st = 0;
+            ph ^= 1;
+          }
           ++since;
           const bool last = kb == hi - 1;
           if (last || since == kLeadStages) {
             umma_commit(&sh.accfull);
             pend = ev++;
             pend_all = last;
-            written = last ? 0u : (written & ~((1u << (kLeadW + 1)) - 1u));
             since = 0;
           }
         }
@@ -412,11 +471,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t gj = j0 + cb0 + j;
         if (gj < n) R[gi + gj * ldr] = C[gi + gj * ldc];
       }
-    int iacc[kLeadW - 1][32];
+    // Leading weights of each column, over the chunks of a product:
+    //   L = 2^16 S_2 + 2^8 S_3 + S_4   (S_w the integer sum of weight w),
+    // so that their part of the product is 2^(e_row + e_col - 32) L.  A chunk adds
+    // less than 2^24 (2^16 + 2^8 + 1) < 2^40.01 in magnitude, so L is exact in int64
+    // for up to 2^22 chunks (K below 8 * 10^8) and exact in binary64 below 2^12
+    // chunks (K below 786432); beyond that its conversion rounds once, by 2^-53.
+    long long lacc[32];
 #pragma unroll
-    for (int a = 0; a < kLeadW - 1; ++a)
-#pragma unroll
-      for (int j = 0; j < 32; ++j) iacc[a][j] = 0;
+    for (int j = 0; j < 32; ++j) lacc[j] = 0;
     int ev = 0;
     bool ok = true;
     for (int p = 0; p < 2 && ok; ++p) {
@@ -425,71 +488,66 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int erow = g.a[p].e[gi];
       const int nst = hi - lo;
       const int nlead = (nst - 1) / kLeadStages;  // drains of the leading weights before the last
-      int nacc = 0;
       for (int d = 0; d <= nlead && ok; ++d, ++ev) {
-        const bool last = d == nlead;
+        const bool last = d == nlead;  // the same in every lane (TMEM loads are warp-collective)
         if (!mbar_wait(&sh.accfull, ev & 1, err, timeout_ns)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int a = 0; a < kLeadW - 1; ++a) {
-          uint32_t v0[16], v1[16];
-          tmem_ld16(tl + static_cast<uint32_t>(a * BN + cb0), v0);
-          tmem_ld16(tl + static_cast<uint32_t>(a * BN + cb0 + 16), v1);
+        for (int h = 0; h < 2; ++h) {
+          uint32_t v2[16], v3[16], v4[16];
+          tmem_ld16(tl + static_cast<uint32_t>(0 * BN + cb0 + 16 * h), v2);
+          tmem_ld16(tl + static_cast<uint32_t>(1 * BN + cb0 + 16 * h), v3);
+          tmem_ld16(tl + static_cast<uint32_t>(2 * BN + cb0 + 16 * h), v4);
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            iacc[a][j] += __float2int_rn(__uint_as_float(v0[j]));
-            iacc[a][16 + j] += __float2int_rn(__uint_as_float(v1[j]));
+          for (int j = 0; j < 16; ++j) {  // the integer sums S_2, S_3, S_4 (exact)
+            const long long c2 = __float2int_rn(__uint_as_float(v2[j]));
+            const long long c3 = __float2int_rn(__uint_as_float(v3[j]) * 0x1p8f);
+            const int c4 = __float2int_rn(__uint_as_float(v4[j]) * 0x1p16f);
+            lacc[16 * h + j] += c2 * 65536 + c3 * 256 + c4;
           }
         }
-        ++nacc;
-        const bool flush = last || nacc == kFlushLead;  // the same in every lane (TMEM loads are warp-collective)
-        if (flush) {
-          // R -= 2^(e_row + e_col) * (sum over weights w of 2^(-8w) * sum_w), smallest weights first
+        // The accumulators of the weights w >= 5 hold 2^(-8(w-2)) S_w; their sum T'
+        // is formed in binary32 from the smallest weight up (one more rounding of
+        // 2^-24 T', the size of the accumulation's own), and the product is
+        // 2^(e_row + e_col - 32) (L + 2^16 T').  Everything leaves TMEM before the
+        // accumulators are handed back, so the binary64 update below overlaps the
+        // next product's MMAs.
+        float tf[32];
+        if (last) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            double dsum[16];
+          for (int j = 0; j < 32; ++j) tf[j] = 0.0f;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) dsum[j] = 0.0;
-            if (last)
-              for (int w = maxw; w > kLeadW; --w) {
-                uint32_t v[16];
-                tmem_ld16(tl + static_cast<uint32_t>((w - 2) * BN + cb0 + 16 * h), v);
-                tmem_wait_ld();
+          for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                  const float f = __uint_as_float(v[j]);
-                  if (f != 0.0f)
-                    dsum[j] += mul2(static_cast<double>(f), erow + sh.ecol[p][cb0 + 16 * h + j] - 8 * w);
-                }
-              }
+            for (int w = MAXW; w > kLeadW; --w) {
+              uint32_t v[16];
+              tmem_ld16(tl + static_cast<uint32_t>((w - 2) * BN + cb0 + 16 * h), v);
+              tmem_wait_ld();
 #pragma unroll
-            for (int a = kLeadW - 2; a >= 0; --a)
-#pragma unroll
-              for (int j = 0; j < 16; ++j)
-                if (iacc[a][16 * h + j] != 0)
-                  dsum[j] += mul2(static_cast<double>(iacc[a][16 * h + j]),
-                                  erow + sh.ecol[p][cb0 + 16 * h + j] - 8 * (a + 2));
-            if (gi < m)
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const int64_t gj = j0 + cb0 + 16 * h + j;
-                if (gj < n) R[gi + gj * ldr] -= dsum[j];
-              }
-          }
-        }
-        if (flush) {
-#pragma unroll
-          for (int a = 0; a < kLeadW - 1; ++a)
-#pragma unroll
-            for (int j = 0; j < 32; ++j) iacc[a][j] = 0;
-          nacc = 0;
+              for (int j = 0; j < 16; ++j) tf[16 * h + j] += __uint_as_float(v[j]);
+            }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(&sh.accempty);
+        if (last) {
+          // R -= 2^(e_row + e_col - 32) (L + 2^16 T')
+          if (gi < m)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int64_t gj = j0 + cb0 + j;
+              const long long L = lacc[j];
+              if (gj < n && (L != 0 || tf[j] != 0.0f)) {
+                const double dv = fma(static_cast<double>(tf[j]), 0x1p16, static_cast<double>(L));
+                R[gi + gj * ldr] -= mul2(dv, erow + sh.ecol[p][cb0 + j] - 32);
+              }
+            }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) lacc[j] = 0;
+        }
       }
     }
     if (!ok) atomicCAS(err, 0, SYLV_ERR_TIMEOUT);

@@ -70,15 +70,18 @@ def test_overflow_4000_full_size(orc, sy):
     assert res_nr.info == sy.SYLV_OVERFLOWED
 
 
+@pytest.mark.parametrize("tol", [0.0, 2.0 ** -41])
 @pytest.mark.parametrize("name", ["wellcond_4000", "wellcond_8000"])
-def test_mixed_full_size(orc, sy, name):
+def test_mixed_full_size(orc, sy, name, tol):
     """FP32 + refinement at full size: the corner against the oracle, and every entry
     against the robust FP64 solve (itself within ~1e-15 of the oracle, so the
-    comparison measures the refined solution's own error), both within 1e-12."""
+    comparison measures the refined solution's own error), both within 1e-12.  The
+    library's default stop tolerance (2^-43) and the benchmark's (2^-41, chosen for
+    the 1e-12 forward-error target) are both checked."""
     A, B, C, w = inputs.workload(name)
-    Y, res = _gpu(sy, A, B, C, tile=w["tile"], precision="fp32_refine")
+    Y, res = _gpu(sy, A, B, C, tile=w["tile"], precision="fp32_refine", tol=tol)
     assert res.info == 0 and res.log2scale == 0
-    assert res.iters >= 2 and res.last_update <= 2.0 ** -43
+    assert res.iters >= 2 and res.last_update <= (tol or 2.0 ** -43)
     r0, cb, ref = _corner(orc, A, B, C, 300)
     assert ref["log2scale"] == 0
     assert _rel(Y[r0:, :cb], ref["Y"]) <= FWD_TOL

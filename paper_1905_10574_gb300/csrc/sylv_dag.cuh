@@ -1757,13 +1757,23 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
     diag_solve<TT, T, ROBUST>(sh, mt, nt, omega, st->smin, fact, factp, I.nob != 0);
     if (w.prio && tid == 0) atomicSub(w.smbusy + sm_id(), 1);
 
-    // ---- exact norm of the final tile, write back, publish
+    // ---- infinity norm of the final tile (binary64 row sums), write back, publish.
+    // A warp per row, lanes across the columns and a shuffle tree, so the sum is a
+    // short dependency chain on the FP64 pipe; the maximum is taken on the bit
+    // patterns of the non-negative sums, so a NaN row still reaches the check below.
     if (tid == 0) sh.umax = 0ull;
     __syncthreads();
-    for (int r = tid; r < mt; r += kThreads) {
-      double s = 0.0;
-      for (int c = 0; c < nt; ++c) s += fabs(static_cast<double>(sh.Y[r + c * LDY]));
-      atomic_max_nonneg(&sh.umax, s);
+    {
+      const int wq = tid >> 5, lq = tid & 31;
+      unsigned long long mxb = 0ull;
+      for (int r = wq; r < mt; r += kThreads / 32) {
+        double s = 0.0;
+        for (int c = lq; c < nt; c += 32) s += fabs(static_cast<double>(sh.Y[r + c * LDY]));
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(s));
+        mxb = b > mxb ? b : mxb;
+      }
+      if (lq == 0 && mxb) atomicMax(&sh.umax, mxb);
     }
     for (int idx = tid; idx < mt * nt; idx += kThreads) {
       const int r = idx % mt, c = idx / mt;
@@ -1790,6 +1800,10 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
       const int e = ROBUST ? sh.e_acc + sh.e_diag : 0;
       texp[task.tile] = e;
       tnorm[task.tile] = nrm;
+      __threadfence();
+      st_release(&tflag[task.tile], 1);
+      // The equation's status words are read only after the kernel, so their atomics
+      // follow the release instead of delaying it.
       int fl = sh.flags;
       if (!(nrm <= 1.7976931348623157e308)) fl |= kFlagNonfiniteOut;
       if (fl) atomicOr(&st->flags, fl);
@@ -1797,8 +1811,6 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
         atomicMin(&st->minexp, e);
         if (sh.nscale) atomicAdd(&st->nscale, sh.nscale);
       }
-      __threadfence();
-      st_release(&tflag[task.tile], 1);
     }
     __syncthreads();
   }

@@ -80,7 +80,7 @@ struct View {
   int mask;
 };
 
-// Tiled operand: RB row blocks of R rows, KB blocks of 64 K; slice s at s * slice_elems.
+// Tiled operand: RB row blocks of R rows, KB blocks of BK along K; slice s at s * slice_elems.
 struct Packed {
   __nv_bfloat16* p;
   int* e;  // per-row exponent (rows padded to RB * R)

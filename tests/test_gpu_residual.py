@@ -132,3 +132,22 @@ def test_full_size_sampled(orc, sy):
         scale = np.abs(A[i, max(0, i - 1):]) @ np.abs(X[max(0, i - 1):, j]) + \
             np.abs(X[i, : min(n, j + 2)]) @ np.abs(B[: min(n, j + 2), j])
         assert abs(R[i, j] - float(ref)) <= 2.0 ** -44 * scale + 2.0 ** -52 * abs(float(ref))
+
+
+def test_subnormal_and_huge_rows(orc, sy):
+    """Rows of A in the subnormal range (the splitting reads their bits without the
+    hidden bit) and columns of X near 1e300: the residual stays within the row/column
+    maximum bound of the oracle's definition."""
+    m, n = 150, 90
+    rng = np.random.default_rng(17)
+    A = np.triu(rng.uniform(-1, 1, (m, m)))
+    B = np.triu(rng.uniform(-1, 1, (n, n)))
+    A[10:20] *= 1e-310   # subnormal rows (their diagonal entries too)
+    A[30] *= 5e-324      # the smallest subnormal scale: entries 0 or +-4.9e-324
+    X = rng.uniform(-1, 1, (m, n))
+    X[:, 40:45] *= 1e300
+    C = rng.uniform(-1, 1, (m, n))
+    R = _gpu_residual(sy, A, B, X, C)
+    ref = orc.residual_matrix(A, B, X, C)
+    assert np.all(np.isfinite(R))
+    assert np.all(np.abs(R - ref) <= _rowcol_bound(A, B, X, ref))

@@ -226,15 +226,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
          (static_cast<uint64_t>((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 // Instruction descriptor of kind::f16: binary32 accumulator, bf16 A and B, both
-// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(BN >> 3) << 17) |
-                            (static_cast<uint32_t>(BM >> 4) << 24);
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24 (M = 128; N a multiple of 64 up to 256).
+__host__ __device__ constexpr uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void umma(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t acc) {
+__device__ __forceinline__ void umma(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
           dtm),
-      "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void umma_commit(unsigned long long* bar) {
@@ -300,25 +302,31 @@ constexpr uint64_t kDescSliceA = kTileA * 2 / 16, kDescSliceB = kTileB * 2 / 16;
 constexpr uint64_t kDescStageA = kSlices * kDescSliceA, kDescStageB = kSlices * kDescSliceB;
 static_assert(BK == 16, "one MMA (K = 16) per slice pair and K block");
 
-// Every slice pair (sl, w - sl) of weights W0..W1 of one staged K block, into the
-// accumulator of its weight (TMEM columns 64 (w - 2)..), the first pair of each
-// weight overwriting it unless acc0 is set.  Fully unrolled: the descriptors are the
-// stage's base plus constants (a shared address below 256 KB never carries out of
-// the 14-bit address field), so one thread issues an MMA in a few instructions.
-template <int W0, int W1, int SMAX>
-__device__ __forceinline__ void issue_weights(uint32_t tbase, uint64_t da, uint64_t db, uint32_t acc0) {
+// The slice pairs of one staged K block whose weight is at most kLeadW (LEAD) or
+// above it.  For a left slice s the pairs (s, t) with consecutive t have consecutive
+// weights s + t, whose accumulators are adjacent in TMEM (64 columns each), and
+// their right slices are adjacent in the stage (one 64-row tile each, 2 KB apart,
+// which is 8 core-matrix rows at the 256-byte row stride), so one MMA with
+// N = 64 x (number of t) computes all of them and reads the left tile once.  That is
+// 10 MMAs per K block instead of 28 for the binary64 residual.  The group of s = 1
+// reaches every weight of its part (2..kLeadW, or kLeadW+1..MAXW), so it alone
+// carries acc0 (overwrite when 0) and is issued first.  Fully unrolled: addresses
+// and instruction descriptors are the stage's bases plus constants (a shared address
+// below 256 KB never carries out of the descriptor's 14-bit address field).
+template <bool LEAD, int MAXW, int SMAX>
+__device__ __forceinline__ void issue_part(uint32_t tbase, uint64_t da, uint64_t db, uint32_t acc0) {
+  static_assert(SMAX == MAXW - 1 && SMAX >= kLeadW - 1, "the group of s = 1 spans every weight of its part");
 #pragma unroll
-  for (int w = W0; w <= W1; ++w) {
-    const int first = w - SMAX > 1 ? w - SMAX : 1;
-#pragma unroll
-    for (int sl = 1; sl <= SMAX; ++sl) {
-      const int t = w - sl;
-      if (t < 1 || t > SMAX) continue;
-      umma(tbase + static_cast<uint32_t>((w - 2) * BN), da + (sl - 1) * kDescSliceA, db + (t - 1) * kDescSliceB,
-           sl == first ? acc0 : 1u);
-    }
+  for (int sl = 1; sl <= SMAX; ++sl) {
+    const int wlo = LEAD ? sl + 1 : (sl + 1 > kLeadW + 1 ? sl + 1 : kLeadW + 1);
+    const int whi = LEAD ? (sl + SMAX < kLeadW ? sl + SMAX : kLeadW) : (sl + SMAX < MAXW ? sl + SMAX : MAXW);
+    if (whi < wlo) continue;
+    const int tlo = wlo - sl, cnt = whi - wlo + 1;
+    umma(tbase + static_cast<uint32_t>((wlo - 2) * BN), da + (sl - 1) * kDescSliceA, db + (tlo - 1) * kDescSliceB,
+         idesc_n(cnt * BN), sl == 1 ? acc0 : 1u);
   }
 }
+static_assert(kMaxW - kLeadW <= 4 && kLeadW - 1 <= 4, "N = 64 x (weights per MMA) <= 256");
 
 // The kernel.  One CTA per 128 x 64 tile of R; warp 8 loads, one thread of warp 9
 // issues the MMAs, warps 0-7 drain TMEM (warp w: TMEM lanes 32 (w & 3).., tile
@@ -433,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t da = da0 + st * kDescStageA, db = db0 + st * kDescStageB;
           // weights above kLeadW first (their accumulators live for the whole product),
           // then the leading ones, once their previous chunk has been drained
-          issue_weights<kLeadW + 1, MAXW, SMAX>(tbase, da, db, kb != lo ? 1u : 0u);
+          issue_part<false, MAXW, SMAX>(tbase, da, db, kb != lo ? 1u : 0u);
           if (pend >= 0) {
             if (!mbar_wait(&sh.accempty, pend & 1, err, timeout_ns)) {
               ok = false;
@@ -442,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             pend = -1;
           }
-          issue_weights<2, kLeadW, SMAX>(tbase, da, db, since != 0 ? 1u : 0u);
+          issue_part<true, MAXW, SMAX>(tbase, da, db, since != 0 ? 1u : 0u);
           umma_commit(&sh.empty[st]);
           if (++st == NST) {
             st = 0;

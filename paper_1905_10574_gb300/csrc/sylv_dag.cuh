@@ -51,6 +51,10 @@ struct DagSmem {
   int gside[G], gprod[G], gk[G], goff[G];  // the current group of producers
   int gsop[G];                        // per producer: power of two its Y operand takes (scaled group)
   int gn, gktot, gfast;
+  // The binary32 tile-32 kernel's group product: the four k-interleaved partial tiles
+  // (see gemm_sub_split4), column-major 32 x 32 each.
+  static constexpr bool kSplitK = sizeof(T) == 4 && TT == 32;
+  alignas(16) T kred[kSplitK ? 4 * TT * TT : 1];
   T Y[TT * LDY];                      // the tile being solved (column-major)
   // Small-system inverses in shared memory for tile capacity 32; the tile-64 kernels
   // keep them in the CTA's global slot.
@@ -1271,6 +1275,58 @@ __device__ __forceinline__ void gemm_sub(T (&acc)[MR][NR], const T* L, const T* 
   }
 }
 
+// The binary32 tile-32 group product.  With one 2x2 block per thread (gemm_sub) a
+// warp needs two shared-memory wavefronts per four FFMA instructions, which caps the
+// FP32 pipe at half its rate.  Here four groups of 64 threads each take every fourth
+// k with a 4x4 block per thread (four wavefronts per sixteen FFMA), write their
+// partial tiles to kred, and every thread sums the four partials of its own 2x2
+// block in group order (deterministic).  part receives -sum_k L[k, r] R[k, c], as
+// gemm_sub does; the caller's barrier after the accumulation frees kred again.
+template <int TT, typename T>
+__device__ __forceinline__ void gemm_sub_split4(T (&part)[2][2], const T* L, const T* R, int kdim, int rbase,
+                                                int cbase, T* kred) {
+  static_assert(sizeof(T) == 4 && TT == 32 && kThreads == 256, "binary32, tile 32, 256 threads");
+  constexpr int LDG = DagSmem<TT, T>::LDG;
+  static_assert(LDG % 2 == 0, "paired operand reads");
+  const int tid = threadIdx.x;
+  const int g = tid >> 6, t = tid & 63;
+  const int r4 = (t & 7) * 4, c4 = (t >> 3) * 4;
+  T p[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) p[i][j] = T(0);
+#pragma unroll 2
+  for (int kk = g; kk < kdim; kk += 4) {
+    const float2 a01 = *reinterpret_cast<const float2*>(&L[kk * LDG + r4]);
+    const float2 a23 = *reinterpret_cast<const float2*>(&L[kk * LDG + r4 + 2]);
+    const float2 b01 = *reinterpret_cast<const float2*>(&R[kk * LDG + c4]);
+    const float2 b23 = *reinterpret_cast<const float2*>(&R[kk * LDG + c4 + 2]);
+    const T a[4] = {a01.x, a01.y, a23.x, a23.y};
+    const T b[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) p[i][j] = fma(-a[i], b[j], p[i][j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    *reinterpret_cast<float4*>(&kred[g * TT * TT + (c4 + j) * TT + r4]) = make_float4(p[0][j], p[1][j], p[2][j], p[3][j]);
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    float2 s = *reinterpret_cast<const float2*>(&kred[(cbase + j) * TT + rbase]);
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+      const float2 v = *reinterpret_cast<const float2*>(&kred[q * TT * TT + (cbase + j) * TT + rbase]);
+      s.x += v.x;
+      s.y += v.y;
+    }
+    part[0][j] = s.x;
+    part[1][j] = s.y;
+  }
+}
+
 template <int TT, typename T, bool ROBUST>
 __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
   static_assert(TT == 32 || TT == 64, "tile capacity");
@@ -1722,7 +1778,10 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
         for (int i = 0; i < MR; ++i)
 #pragma unroll
           for (int j = 0; j < NR; ++j) part[i][j] = T(0);
-        gemm_sub<TT, T, MR, NR>(part, sh.L, sh.R, sh.gktot, rbase, cbase);
+        if constexpr (DagSmem<TT, T>::kSplitK)
+          gemm_sub_split4<TT, T>(part, sh.L, sh.R, sh.gktot, rbase, cbase, sh.kred);
+        else
+          gemm_sub<TT, T, MR, NR>(part, sh.L, sh.R, sh.gktot, rbase, cbase);
 #pragma unroll
         for (int i = 0; i < MR; ++i)
 #pragma unroll

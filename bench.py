@@ -102,20 +102,27 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
+        return self.parse(out)
+
+    @staticmethod
+    def parse(out):
+        """Median SM clock, maximum SM clock and the throttle reasons seen active in
+        `nvidia-smi --format=csv,noheader,nounits` lines of FIELDS (others skipped)."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
+            for nm, v in zip(names, parts[5:9]):  # counted even when a clock reads N/A
                 if v.lower() == "active":
                     reasons.add(nm)
+            try:
+                clk, clk_max = float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            sm.append(clk)
+            smax.append(clk_max)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 

@@ -3,20 +3,26 @@
 
 One step = one full robust FP64 solve A Y + Y B = alpha C (Algorithm 4: structure
 scan and tile partition, Bound, the persistent tile-DAG kernel with robust
-updates and diagonal solves, consistency scaling) on the workload
-"overflow_4000": m = n = 4000, tile 32, quasi-triangular A and B whose unscaled
-back substitution grows ~1400 bits (past the binary64 range), C ~ U[-1,1].
+updates and diagonal solves, consistency scaling) on the workload "benign_8000":
+m = n = 8000, tile 32, quasi-triangular A and B with ~50% of eigenvalues in
+standardized 2x2 blocks, eigenvalue real parts U[1,10], strictly-upper entries and
+C ~ U[-1,1] (the FP64 arm of the m = n = 8000 mixed-precision configuration).
 
 Metric: GFLOP/s counting 2mn(m+n) flops per solve (the configuration's count);
 the algorithmic count mn(m+n) (one multiply-add per update term) is reported
-beside it and used for the roofline.  Inputs (3 x 128 MB) exceed the 129 MB L2
+beside it and used for the roofline.  Inputs (3 x 512 MB) exceed the 129 MB L2
 and every step solves a fresh copy of C, so no step starts from a warm L2.
+Secondary lines: robust against non-robust at m = n = 4000 on an input whose
+unscaled substitution overflows; m = n = 256 (latency, microseconds per solve);
+FP32 + refinement at 8000; the 4096-equation batch (FP64 and FP32 + refinement);
+256 Lyapunov forward + backward solves.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 With torchrun (N > 1) every rank solves its own copy of the workload (the solve
 does not shard: replicas); value = all ranks' flops / the slowest rank's time.
---impl reference times the FP64 CPU oracle (Algorithm 2 in plain C) on the host.
+--impl reference times the FP64 CPU oracle (Algorithm 2 in plain C) on the host
+cores: one independent oracle solve per core at a bounded size.
 """
 from __future__ import annotations
 
@@ -31,9 +37,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "overflow_4000"
+WORKLOAD = "benign_8000"
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070  # 152 SMs x 2 DFMA/clk (4 flop) x 2.07 GHz max SM clock
-ORACLE_SAMPLE_M = 900  # bounded CPU sample: same generator family at m = n = 900
+ORACLE_SAMPLE_M = 900  # bounded CPU sample: same generator family at m = n = 900, one solve per host core
 
 
 def flops_2(m, n):
@@ -47,7 +53,7 @@ def flops_alg(m, n):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=None, help="named synthetic workload (each mode has its default)")
@@ -58,12 +64,14 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (mixed precision, batched, adjoint)")
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "mixed", "batched", "adjoint", "smscale", "variants", "robustness", "residual"],
+                    choices=["solve", "mixed", "batched", "adjoint", "smscale", "variants", "robustness", "residual",
+                             "robust_vs_plain", "small"],
                     help="solve: the headline robust FP64 solve; mixed: FP32 + refinement vs FP64 at "
                          "m=n=8000; batched: 4096 uneven equations; adjoint: 256 Lyapunov forward+backward; "
                          "smscale: SM scaling; variants: sign variant, triangular solve, Bartels-Stewart at 4000; "
                          "robustness: robust vs plain on the paper's matrices, m=n=10000; residual: the "
-                         "refinement's tensor-core residual at m=n=4000")
+                         "refinement's tensor-core residual at m=n=4000; robust_vs_plain: robust against non-robust "
+                         "FP64 at m=n=4000 (overflow workload); small: m=n=256 microseconds per solve")
     return ap.parse_args()
 
 
@@ -143,48 +151,148 @@ def traffic_for_dag():
     return rec.get("dram_bytes_per_launch_full_size")
 
 
-def cpu_baseline(w):
-    """The FP64 oracle (single-threaded C) on a bounded sample of the same generator."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_worker(m, seed, kind, upper, steps, warmup, barrier, out):
+    """One host core: `warmup` + `steps` oracle solves of the same m x m sample, each
+    timed between barriers shared with the other cores' workers."""
     from oracle import oracle
     from paper_1905_10574_gb300 import inputs
-    m = n = ORACLE_SAMPLE_M
-    A, B, C = inputs.problem(m, n, w["seed"], kind=w["kind"], upper=w["upper"])
+    A, B, C = inputs.problem(m, m, seed, kind=kind, upper=upper)
     oracle.trsyl(A[:64, :64], B[:64, :64], C[:64, :64])  # load + warm the library
+    ts = []
+    for i in range(warmup + steps):
+        barrier.wait()
+        t0 = time.perf_counter()
+        oracle.trsyl(A, B, C)
+        if i >= warmup:
+            ts.append(time.perf_counter() - t0)
+    out.put(ts)
+
+
+def oracle_on_host_cores(w, steps, warmup, cores=None):
+    """The FP64 oracle (single-threaded C, as it stands) on every host core at once:
+    each core solves its own copy of an m = n = ORACLE_SAMPLE_M sample of the workload's
+    generator per step; a step lasts until the slowest core finishes.  Processes are
+    spawned (never forked after CUDA initialisation).  Returns (GFLOP/s over all
+    cores counted 2mn(m+n), cores, seconds per step)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    cores = cores or host_cores()
+    barrier = ctx.Barrier(cores)
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(ORACLE_SAMPLE_M, w["seed"], w["kind"], w["upper"], steps,
+                                                      warmup, barrier, out)) for _ in range(cores)]
+    for p in procs:
+        p.start()
+    per_core = [out.get() for _ in procs]
+    for p in procs:
+        p.join()
+    step_s = [max(ts[i] for ts in per_core) for i in range(steps)]
+    tot = sum(step_s)
+    m = ORACLE_SAMPLE_M
+    return cores * steps * flops_2(m, m) / tot / 1e9, cores, tot / steps
+
+
+def cpu_baseline(w):
+    """The FP64 oracle on all host cores (one independent sample solve per core)."""
+    val, cores, sec = oracle_on_host_cores(w, steps=2, warmup=0)
+    m = ORACLE_SAMPLE_M
+    return {"value": val, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"each of {cores} host cores solves its own m=n={m} robust FP64 oracle problem (Algorithm 2, "
+                      f"single-threaded C) of the same generator (kind={w['kind']}, upper={w['upper']}); "
+                      f"2 steps of {sec:.2f} s (slowest core); counted 2mn(m+n) per core"}
+
+
+def _lapack_dtrsyl3():
+    """LAPACKE_dtrsyl3 of the OpenBLAS that scipy bundles, found by its exported name
+    (None if this scipy build has none)."""
+    import ctypes
+    import glob
+    import scipy
+    libdir = os.path.join(os.path.dirname(os.path.dirname(scipy.__file__)), "scipy.libs")
+    for path in sorted(glob.glob(os.path.join(libdir, "*openblas*.so*"))):
+        try:
+            L = ctypes.CDLL(path)
+        except OSError:
+            continue
+        for prefix in ("scipy_", ""):
+            fn = getattr(L, prefix + "LAPACKE_dtrsyl3", None)
+            if fn is not None:
+                setn = getattr(L, prefix + "openblas_set_num_threads", None)
+                return fn, setn, os.path.basename(path)
+    return None
+
+
+def cpu_context_dtrsyl3(w):
+    """Time-to-solution context on the host: LAPACK's blocked triangular Sylvester
+    solver dtrsyl3 (OpenBLAS, multithreaded on all host cores), one solve of the full
+    workload in a spawned process.  Context only: a different algorithm and code."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_dtrsyl3_worker, args=(w, q))
+    p.start()
+    try:
+        r = q.get(timeout=300)
+    except Exception as exc:  # noqa: BLE001  report, do not hide
+        r = {"unavailable": f"dtrsyl3 leg did not finish: {type(exc).__name__}"}
+        p.terminate()
+    p.join()
+    return r
+
+
+def _dtrsyl3_worker(w, q):
+    import ctypes
+    import numpy as np
+    from paper_1905_10574_gb300 import inputs
+    found = _lapack_dtrsyl3()
+    if found is None:
+        q.put({"unavailable": "scipy's OpenBLAS exports no LAPACKE_dtrsyl3 on this host"})
+        return
+    fn, setn, libname = found
+    cores = host_cores()
+    if setn is not None:
+        setn(cores)
+    m, n = w["m"], w["n"]
+    A, B, C = inputs.problem(m, n, w["seed"], kind=w["kind"], upper=w["upper"])
+    A, B, C = (np.asfortranarray(x) for x in (A, B, C))
+    i32, pd = ctypes.c_int32, ctypes.POINTER(ctypes.c_double)
+    fn.restype = i32
+    fn.argtypes = [ctypes.c_int, ctypes.c_char, ctypes.c_char, i32, i32, i32, pd, i32, pd, i32, pd, i32, pd]
+    scale = ctypes.c_double(0.0)
+    args = lambda X: X.ctypes.data_as(pd)  # noqa: E731
     t0 = time.perf_counter()
-    oracle.trsyl(A, B, C)
+    info = fn(102, b"N", b"N", 1, m, n, args(A), m, args(B), n, args(C), m, ctypes.byref(scale))
     dt = time.perf_counter() - t0
-    return {"value": flops_2(m, n) / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"one robust FP64 solve (Algorithm 2) at m=n={m}, same generator "
-                      f"(kind={w['kind']}, upper={w['upper']}), {dt:.2f} s, counted 2mn(m+n)"}
+    q.put({"value": flops_2(m, n) / dt / 1e9, "unit": "GFLOP/s", "cores": cores,
+           "kind": "LAPACK dtrsyl3 (" + libname + ")", "seconds": dt, "info": int(info), "scale": scale.value,
+           "sample": f"one solve of the full workload m=n={m}, {cores} OpenBLAS threads; counted 2mn(m+n)"})
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    from oracle import oracle
     from paper_1905_10574_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
-    m = n = ORACLE_SAMPLE_M
-    A, B, C = inputs.problem(m, n, w["seed"], kind=w["kind"], upper=w["upper"])
-    for _ in range(args.warmup):
-        oracle.trsyl(A, B, C)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.trsyl(A, B, C)
-        times.append(time.perf_counter() - t0)
-    tot = sum(times)
-    val = args.steps * flops_2(m, n) / tot / 1e9
+    m = ORACLE_SAMPLE_M
+    val, cores, sec = oracle_on_host_cores(w, steps=max(1, args.steps), warmup=args.warmup)
     line = {"impl": "reference", "metric": "robust Sylvester solve GFLOP/s", "value": val, "unit": "GFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1000 * sec, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "m": w["m"], "n": w["n"], "tile": w["tile"],
                        "flop_count": "2mn(m+n)", "reference_sample_m": m},
-            "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step one robust FP64 oracle solve (Algorithm 2) at m=n={m} of the "
-                                       f"same generator; the GPU arm solves m=n={w['m']}"},
+            "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: each of {cores} host cores solves its own m=n={m} robust FP64 "
+                                       f"oracle problem (Algorithm 2, single-threaded C) of the same generator; the "
+                                       f"GPU arm solves m=n={w['m']}"},
             "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -298,13 +406,14 @@ def run_ours(args):
             "config": {"workload": args.workload, "m": m, "n": n, "tile": tile, "generator": w["kind"],
                        "upper_scale": w["upper"], "flop_count": "2mn(m+n)",
                        "algorithmic_gflops": ws * flops_alg(m, n) / (per_step / 1000) / 1e9,
-                       "l2": "inputs 384 MB > 129 MB L2; fresh C copy per step", "parallelism": f"replicas{ws}"},
+                       "l2": f"inputs {3 * 8 * m * n // 2**20} MB > 129 MB L2; fresh C copy per step",
+                       "parallelism": f"replicas{ws}"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                          "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
                          "kernel": f"dag_kernel<{32 if tile <= 32 else 64},double,robust>",
                          "flops_per_launch": flops_alg(m, n),
-                         "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived); a DFMA loop measured "
-                                      "1184 GFLOP/s at ~1.98 GHz"},
+                         "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived from unit counts and "
+                                      "the maximum SM clock; MEASURED_PEAKS.json has no FP64 entry)"},
             "e2e": {"value": replicas.whole_job_rate(flops_2(m, n), ws, e2e_ms / 1000) / 1e9, "unit": "GFLOP/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 10 * args.steps,  # per solve: set_inst, scan, norms, 3 level kernels, pack, DAG, consistency, results
@@ -315,6 +424,7 @@ def run_ours(args):
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
+            line["cpu_context"] = cpu_context_dtrsyl3(w)
         if not args.no_extras and ws == 1:
             line["secondary"] = secondary(args)
         print(json.dumps(line), flush=True)
@@ -729,6 +839,94 @@ def run_robustness(args):
             "config": {"m": m, "n": n, "nu": nu, "tile": 32}, "rows": rows}
 
 
+def run_robust_vs_plain(args):
+    """Robust FP64 (Algorithm 4) against non-robust FP64 (Algorithm 1 per tile) at
+    m = n = 4000 on "overflow_4000", whose unscaled substitution grows ~1400 bits: the
+    plain solve overflows, the robust one scales (alpha = 2^log2scale).  Roofline of
+    the robust solve's tile kernel as for the headline."""
+    import torch
+    from paper_1905_10574_gb300 import build, inputs, sylv
+    build.build()
+    name = args.workload or "overflow_4000"
+    A, B, C, w = inputs.workload(name)
+    m, n, tile = w["m"], w["n"], args.tile or w["tile"]
+    dev = torch.device("cuda", 0)
+    Ad, Bd, C0 = (torch.from_numpy(x).to(dev) for x in (A, B, C))
+    stream = torch.cuda.current_stream(dev)
+    rows = {}
+    for prec in ("fp64", "fp64_nonrobust"):
+        opts = sylv.make_opts(tile=tile, precision=prec, stream=stream.cuda_stream, sync=True)
+        wsb = sylv.sylv_workspace_size(m, n, opts)
+        wsbuf = torch.empty(wsb + 256, dtype=torch.uint8, device=dev)
+        opts.workspace = (wsbuf.data_ptr() + 255) // 256 * 256
+        opts.workspace_bytes = wsb
+        Cs = [C0.clone() for _ in range(args.warmup + args.steps)]
+        res = sylv.sylv_result()
+
+        def fn(i, opts=opts, Cs=Cs, res=res):
+            rc = sylv.sylv_tri_solve_ex(m, n, Ad.data_ptr(), Ad.stride(1), Bd.data_ptr(), Bd.stride(1),
+                                        Cs[i].data_ptr(), Cs[i].stride(1), opts, res)
+            if rc >= 100 or rc < 0:
+                raise sylv.SylvError(rc, prec)
+
+        sylv.sylv_profile(True)
+        ms, _ = _timed(fn, args.steps, args.warmup, stream)
+        dag_ms, dag_n = sylv.sylv_profile_read()
+        sylv.sylv_profile(False)
+        dag_per = dag_ms / max(dag_n, 1)  # includes the warm-up launches: same kernel, same work
+        ach = flops_alg(m, n) / (dag_per / 1000) / 1e9
+        rows[prec] = {"ms_per_solve": ms, "gflops_2mnmn": flops_2(m, n) / ms / 1e6, "info": int(res.info),
+                      "log2scale": int(res.log2scale), "scale_events": int(res.scale_events),
+                      "finite": bool(torch.isfinite(Cs[-1]).all()), "dag_ms_per_launch": dag_per,
+                      "roofline_frac": ach / FP64_PEAK_GFLOPS}
+        del Cs, wsbuf
+    return {"metric": "robust Sylvester solve GFLOP/s", "value": rows["fp64"]["gflops_2mnmn"], "unit": "GFLOP/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": name, "m": m, "n": n, "tile": tile, "generator": w["kind"],
+                                            "upper_scale": w["upper"]},
+            "robust": rows["fp64"], "nonrobust": rows["fp64_nonrobust"],
+            "robustness_overhead": rows["fp64"]["ms_per_solve"] / rows["fp64_nonrobust"]["ms_per_solve"] - 1.0}
+
+
+def run_small(args):
+    """m = n = 256, tile 64 (benign, seed 0): a latency-bound solve of 4 x 4 tiles with
+    a 7-level critical path; microseconds per solve and solves/s, one call per solve on
+    one stream (each call enqueues the whole launch sequence)."""
+    import torch
+    from paper_1905_10574_gb300 import build, inputs, sylv
+    build.build()
+    name = args.workload or "benign_256"
+    A, B, C, w = inputs.workload(name)
+    m, n, tile = w["m"], w["n"], args.tile or w["tile"]
+    dev = torch.device("cuda", 0)
+    Ad, Bd, C0 = (torch.from_numpy(x).to(dev) for x in (A, B, C))
+    stream = torch.cuda.current_stream(dev)
+    opts = sylv.make_opts(tile=tile, stream=stream.cuda_stream, sync=False)
+    wsb = sylv.sylv_workspace_size(m, n, opts)
+    wsbuf = torch.empty(wsb + 256, dtype=torch.uint8, device=dev)
+    opts.workspace = (wsbuf.data_ptr() + 255) // 256 * 256
+    opts.workspace_bytes = wsb
+    reps = 50
+    Cs = [C0.clone() for _ in range(reps * (args.warmup + args.steps))]
+    rdev = torch.zeros(64, dtype=torch.uint8, device=dev)
+
+    def fn(i):
+        for j in range(reps):
+            c = Cs[i * reps + j]
+            rc = sylv.sylv_tri_solve_ex(m, n, Ad.data_ptr(), Ad.stride(1), Bd.data_ptr(), Bd.stride(1), c.data_ptr(),
+                                        c.stride(1), opts, rdev.data_ptr())
+            if rc != 0:
+                raise sylv.SylvError(rc, "small")
+
+    ms, _ = _timed(fn, args.steps, args.warmup, stream)
+    res = sylv.sylv_result.from_buffer_copy(rdev[:40].cpu().numpy().tobytes())
+    us = 1000.0 * ms / reps
+    return {"metric": "solves/s", "value": 1e6 / us, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "m": m, "n": n, "tile": tile, "solves_per_step": reps},
+            "us_per_solve": us, "gflops_2mnmn": flops_2(m, n) / us / 1e3, "info": int(res.info)}
+
+
 def secondary(args):
     """The other configurations, measured briefly beside the headline solve."""
     import argparse as _ap
@@ -737,8 +935,10 @@ def secondary(args):
     sub = _ap.Namespace(**vars(args))
     sub.workload, sub.tile = None, 0
     sub.steps, sub.warmup = 2, 1
-    for name, fn in (("mixed_precision_8000", run_mixed), ("batched_4096", run_batched),
+    for name, fn in (("robust_vs_nonrobust_4000", run_robust_vs_plain), ("small_256", run_small),
+                     ("mixed_precision_8000", run_mixed), ("batched_4096", run_batched),
                      ("adjoint_256x512", run_adjoint)):
+        sub.steps, sub.warmup = (5, 2) if name in ("robust_vs_nonrobust_4000", "small_256") else (2, 1)
         try:
             r = fn(sub)
             r.pop("n_gpus", None)
@@ -771,6 +971,10 @@ def main():
         print(json.dumps(run_variants(args)), flush=True)
     elif args.mode == "robustness":
         print(json.dumps(run_robustness(args)), flush=True)
+    elif args.mode == "robust_vs_plain":
+        print(json.dumps(run_robust_vs_plain(args)), flush=True)
+    elif args.mode == "small":
+        print(json.dumps(run_small(args)), flush=True)
     else:
         run_ours(args)
 

@@ -50,7 +50,8 @@ extern "C" {
                                   its pivot was raised to smin and the solve went on */
 #define SYLV_SCALE_UNDERFLOW 2 /* alpha < 2^-1074: the double `scale` is 0, use log2scale */
 #define SYLV_NOT_CONVERGED 3   /* FP32 + refinement did not reach opts->tol */
-#define SYLV_OVERFLOWED 4      /* non-robust mode only: Y holds Inf/NaN (Algorithm 1 overflowed) */
+#define SYLV_OVERFLOWED 4      /* Inf/NaN in an output: the non-robust mode overflowed (Algorithm 1), or a
+                                  gradient of the adjoint lies beyond the binary64 range */
 #define SYLV_ERR_STRUCTURE_A 101 /* A has two consecutive nonzero subdiagonal entries */
 #define SYLV_ERR_STRUCTURE_B 102 /* B has two consecutive nonzero subdiagonal entries */
 #define SYLV_ERR_NONFINITE 103   /* NaN or Inf in A, B or C */
@@ -195,8 +196,12 @@ int sylv_tri_solve_batched(int32_t count, const int64_t* m, const int64_t* n,
  * solver reads (upper triangle plus the nonzero subdiagonal entries that mark 2x2
  * blocks); all other entries are set to 0.  dA or dB may be NULL to skip them.
  * log2scale is the forward result's exponent (alpha = 2^log2scale).  If the adjoint
- * solve has to scale (its own factor alpha_G = 2^result->log2scale < 1), all three
- * outputs are returned multiplied by alpha_G.  Y and G are device pointers.
+ * solve has to scale (its own factor alpha_G = 2^result->log2scale < 1), the call
+ * removes alpha_G from all three outputs again on the device, by exact power-of-two
+ * scaling (the exponent is read from the device result record, so the call does not
+ * wait for the host); an output entry that leaves the binary64 range on the way
+ * becomes +-Inf and the status is SYLV_OVERFLOWED.  result->log2scale still
+ * reports alpha_G.  Y and G are device pointers.
  */
 int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, const double* B,
                             int64_t ldb, const double* Y, int64_t ldy, int64_t log2scale,
@@ -209,7 +214,9 @@ int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, 
  * forward exponents log2scale[i]); the adjoint solves run as one batched launch
  * (both transposes flipped), the gradient products and the dC scaling as one
  * launch each.  dA / dB may be NULL (skip all) or hold NULL entries (skip one).
- * results[i] (HOST) receives each adjoint solve's record.  Synchronizes
+ * results[i] (HOST) receives each adjoint solve's record; as in the single form,
+ * each equation's outputs come back with its adjoint factor alpha_G removed (status
+ * SYLV_OVERFLOWED where an entry leaves the binary64 range).  Synchronizes
  * opts->stream; allocates a plan and a small descriptor buffer internally.
  */
 int sylv_tri_solve_backward_batched(int32_t count, const int64_t* m, const int64_t* n,
@@ -222,27 +229,28 @@ int sylv_tri_solve_backward_batched(int32_t count, const int64_t* m, const int64
 
 /*
  * sylv_tri_solve_noalloc -- the robust FP64 solve of sylv_tri_solve, for callers
- * that must not allocate device memory while they run: code that records CUDA
- * graphs or runs inside a stream capture and may not add allocations, real-time
- * loops that forbid allocator calls after start-up, and hosts whose device memory
- * belongs to another allocator.  The paper has no counterpart; it is a service
- * of this library.
+ * that must not allocate device memory while they run: real-time loops that forbid
+ * allocator calls after start-up (an allocation can block on the device or the
+ * driver for an unbounded time), and hosts whose device memory belongs to another
+ * allocator that the library cannot call into.  The paper has no counterpart; it is
+ * a service of this library.
  *
  * It allocates nothing: its scratch is one fixed array of 16 MiB in device memory
  * that this library defines and every GPU that loads the library holds until the
  * process exits.  The caller passes the inputs and the output as for
  * sylv_tri_solve (device pointers; C is overwritten by Y); `tile` as for
- * sylv_tri_solve; `stream` is a cudaStream_t (NULL: legacy default stream); the
- * call waits for the stream and fills the HOST record *result (may be NULL).
+ * sylv_tri_solve; `stream` is a cudaStream_t (NULL: legacy default stream).  The
+ * call copies the result record to host memory and synchronizes `stream` before it
+ * returns, filling the HOST record *result (may be NULL).
  * Problems whose bookkeeping does not fit the array are rejected on the host,
  * before any GPU work, with SYLV_ERR_WORKSPACE (about m, n <= 11000 fit at the
  * default tile); when the per-CTA stores fit only in part, the solve runs with
  * fewer CTAs.  The first call on a device looks up the array's device address
- * (a runtime call, once per device, with that device current); make that first
- * call before any stream capture.  All calls share the one array and it keeps
- * the last call's contents: each call clears what must start at zero, but two
- * calls that overlap on the GPU (different streams or threads) race on it and
- * give wrong results.  Status codes as for sylv_tri_solve_ex.
+ * (a runtime call, once per device, with that device current).  All calls share
+ * the one array and it keeps the last call's contents: each call clears what must
+ * start at zero, but two calls that overlap on the GPU (different streams or
+ * threads) race on it and give wrong results.  Status codes as for
+ * sylv_tri_solve_ex.
  */
 int sylv_tri_solve_noalloc(int64_t m, int64_t n, const double* A, int64_t lda, const double* B,
                            int64_t ldb, double* C, int64_t ldc, int64_t tile, void* stream,
@@ -326,6 +334,22 @@ int sylv_residual(int64_t m, int64_t n, const double* A, int64_t lda, const doub
  * allocates a few bytes of device memory and synchronizes `stream`.
  */
 int sylv_diag_wait_timeout(int64_t timeout_ms, void* stream);
+
+/*
+ * sylv_diag_guards -- diagnostic of the solver's scaling guards.  Evaluates, on the
+ * device, the very ProtectUpdate and ProtectDivision routines the tile kernels call
+ * (Sec. 2.1), so a test can check their contracts directly:
+ *   z_update[i]   = z <= 0 with 2^z (c[i] + t[i] x[i]) <= omega, for c, t, x in [0, omega];
+ *   z_division[i] = the largest z <= 0 with 2^z |b[i]| / |d[i]| <= omega, for
+ *                   |b[i]| <= omega and d[i] != 0.
+ * All seven arrays hold `count` entries in device memory, caller-owned; omega is the
+ * overflow threshold (>= 1, finite; the solver uses 2^1020 in binary64 and 2^124
+ * for its binary32 correction solves).  Runs on `stream` (null: the default stream)
+ * and synchronizes it.  Returns SYLV_OK, -1 (count), -2 (a null array), -9 (omega)
+ * or SYLV_ERR_CUDA.  Allocates nothing.
+ */
+int sylv_diag_guards(int64_t count, const double* c, const double* t, const double* x, int32_t* z_update,
+                     const double* b, const double* d, int32_t* z_division, double omega, void* stream);
 
 /*
  * Kernel timing for benchmarks (not in the paper).  While enabled, every launch of

@@ -253,6 +253,15 @@ __global__ void k_wait_nothing(int* flag, Ctrl* ctrl, long long timeout_ns) {
   if (threadIdx.x == 0) wait_flag(flag, ctrl, timeout_ns);
 }
 
+// The solver's own ProtectUpdate / ProtectDivision, one evaluation per thread.
+__global__ void k_guards(int64_t count, const double* c, const double* t, const double* x, int32_t* zu,
+                         const double* b, const double* d, int32_t* zd, double omega) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= count) return;
+  zu[i] = protect_update(c[i], t[i], x[i], omega);
+  zd[i] = protect_division(b[i], d[i], omega);
+}
+
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? SYLV_OK : SYLV_ERR_CUDA; }
 
 int sm_count() {
@@ -730,13 +739,27 @@ int sylv_diag_wait_timeout(int64_t timeout_ms, void* stream) {
   return rc;
 }
 
+int sylv_diag_guards(int64_t count, const double* c, const double* t, const double* x, int32_t* z_update,
+                     const double* b, const double* d, int32_t* z_division, double omega, void* stream) {
+  if (count < 0) return -1;
+  if (count > 0 && (!c || !t || !x || !z_update || !b || !d || !z_division)) return -2;
+  if (!(omega >= 1.0) || !(omega <= 1.7976931348623157e308)) return -9;
+  if (count == 0) return SYLV_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t blocks = (count + 255) / 256;
+  if (blocks > 0x7fffffff) return -1;
+  k_guards<<<static_cast<unsigned>(blocks), 256, 0, s>>>(count, c, t, x, z_update, b, d, z_division, omega);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return SYLV_ERR_CUDA;
+  return SYLV_OK;
+}
+
 const char* sylv_error_string(int code) {
   switch (code) {
     case SYLV_OK: return "ok";
     case SYLV_NEAR_SINGULAR: return "near-singular block system perturbed (lambda(A)+lambda(B) ~ 0)";
     case SYLV_SCALE_UNDERFLOW: return "scale factor underflows double precision; use log2scale";
     case SYLV_NOT_CONVERGED: return "FP32 + refinement did not reach the tolerance";
-    case SYLV_OVERFLOWED: return "non-robust solve overflowed (Inf/NaN in Y)";
+    case SYLV_OVERFLOWED: return "overflow: Inf/NaN in the output (non-robust solve, or a gradient beyond the binary64 range)";
     case SYLV_ERR_STRUCTURE_A: return "A is not upper quasi-triangular (consecutive nonzero subdiagonal entries)";
     case SYLV_ERR_STRUCTURE_B: return "B is not upper quasi-triangular (consecutive nonzero subdiagonal entries)";
     case SYLV_ERR_NONFINITE: return "NaN or Inf in the input";
@@ -1110,6 +1133,10 @@ int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, 
   if (rc) return rc;
   cudaStream_t s = o.stream;
   const int64_t e = log2scale;
+  // The adjoint solve left alpha_G * Gamma in G, alpha_G = 2^res_dev->log2scale.  The
+  // gradient kernels read that exponent on the device and remove it exactly, so
+  // nothing waits for the host.
+  sylv_result* res_dev = reinterpret_cast<sylv_result*>(ws + P.L.res);
   // dA, dB from alpha_G * Gamma (G now), before G is turned into dL/dC.
   if (dA) {
     // op(A) = A: dA = -Gamma Y^T: P(i,c) = G[i + c ldg], Q(j,c) = Y[j + c ldy]
@@ -1118,7 +1145,7 @@ int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, 
     const double* Qp = o.transa ? G : Y;
     const int64_t lp = o.transa ? ldy : ldg, lq = o.transa ? ldg : ldy;
     k_grad_product<<<dim3((m + GT - 1) / GT, (m + GT - 1) / GT), 256, 0, s>>>(Pp, 1, lp, Qp, 1, lq, m, n, A, lda,
-                                                                                dA, ldda, 1.0);
+                                                                                dA, ldda, 1.0, res_dev);
   }
   if (dB) {
     // op(B) = B: dB = -Y^T Gamma: P(i,r) = Y[r + i ldy], Q(j,r) = G[r + j ldg]
@@ -1128,11 +1155,12 @@ int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, 
     const int64_t lp = o.transb ? ldg : ldy, lq = o.transb ? ldy : ldg;
     // With op(A) Y - Y op(B) = alpha C the B term carries -1: dB changes sign.
     k_grad_product<<<dim3((n + GT - 1) / GT, (n + GT - 1) / GT), 256, 0, s>>>(Pp, lp, 1, Qp, lq, 1, n, m, B, ldb,
-                                                                                dB, lddb, o.isgn < 0 ? -1.0 : 1.0);
+                                                                                dB, lddb, o.isgn < 0 ? -1.0 : 1.0,
+                                                                                res_dev);
   }
-  if (e != 0) k_scale_pow2<<<grid_for(m * n), 256, 0, s>>>(G, ldg, m, n, static_cast<int>(e));
+  // dL/dC = alpha Gamma = 2^(e - log2 alpha_G) G.
+  k_unscale_pow2<<<grid_for(m * n), 256, 0, s>>>(G, ldg, m, n, e, res_dev);
   if (cudaGetLastError() != cudaSuccess) return SYLV_ERR_CUDA;
-  sylv_result* res_dev = reinterpret_cast<sylv_result*>(ws + P.L.res);
   if (sync) {
     sylv_result r{};
     if (cudaMemcpyAsync(&r, res_dev, sizeof(r), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SYLV_ERR_CUDA;
@@ -1183,7 +1211,8 @@ int sylv_tri_solve_backward_batched(int32_t count, const int64_t* m, const int64
     sylv_batch_destroy(P);
     return rc;
   }
-  // Gradient products from alpha_G Gamma (now in G), then dL/dC = alpha Gamma.
+  // Gradient products from alpha_G Gamma (now in G), then dL/dC = alpha Gamma; each
+  // kernel removes alpha_G (read from the equation's device result record) exactly.
   std::vector<GradDesc> gd;
   std::vector<ScaleDesc> sd;
   int64_t maxN = 1;
@@ -1205,6 +1234,7 @@ int sylv_tri_solve_backward_batched(int32_t count, const int64_t* m, const int64
       g.D = dA[i];
       g.ldd = ldda[i];
       g.sign = 1.0;
+      g.rs = P->w.res + i;
       gd.push_back(g);
     }
     if (dB && dB[i]) {
@@ -1222,9 +1252,10 @@ int sylv_tri_solve_backward_batched(int32_t count, const int64_t* m, const int64
       g.D = dB[i];
       g.ldd = lddb[i];
       g.sign = o.isgn < 0 ? -1.0 : 1.0;  // op(A) Y - Y op(B) = alpha C: dB changes sign
+      g.rs = P->w.res + i;
       gd.push_back(g);
     }
-    sd.push_back(ScaleDesc{G[i], ldg[i], m[i], n[i], static_cast<int>(log2scale[i]), 0});
+    sd.push_back(ScaleDesc{G[i], ldg[i], m[i], n[i], log2scale[i], P->w.res + i});
   }
   void* buf = nullptr;
   const size_t bytes = align_up(sizeof(GradDesc) * std::max<size_t>(gd.size(), 1)) + sizeof(ScaleDesc) * std::max<size_t>(sd.size(), 1);
@@ -1256,10 +1287,9 @@ int sylv_tri_solve_backward_batched(int32_t count, const int64_t* m, const int64
 }
 
 // ---------------------------------------------------------------- allocation-free entry point
-// Some callers cannot allocate device memory at solve time: code running inside a
-// CUDA stream capture that must not add allocation nodes, real-time loops that
-// forbid allocator calls after start-up, and embeddings whose memory is owned by
-// another allocator.  sylv_tri_solve_noalloc serves them with scratch that lives in
+// Some callers cannot allocate device memory at solve time: real-time loops that
+// forbid allocator calls after start-up (an allocation may block for an unbounded
+// time), and embeddings whose memory is owned by another allocator.  sylv_tri_solve_noalloc serves them with scratch that lives in
 // a fixed-size device array of this library (g_noalloc_scratch below), so a call
 // itself allocates nothing.
 namespace {
@@ -1354,7 +1384,7 @@ extern "C" int sylv_tri_solve_noalloc(int64_t m, int64_t n, const double* A, int
   k_set_inst<<<1, 1, 0, s>>>(w.inst, I);
   if (run_prep<double>(w, L, 1, std::max(m, n), std::max(shp[0].pmax, shp[0].qmax), s) != cudaSuccess)
     return SYLV_ERR_CUDA;
-  if (launch_dag_f64(t, true, w, std::min(L.max_tiles, L.ncta), s) != cudaSuccess) return SYLV_ERR_CUDA;
+  if (launch_dag_f64(t, true, w, fp64_grid(L.max_tiles, L.ncta), s) != cudaSuccess) return SYLV_ERR_CUDA;
   k_consistency<double><<<grid_for(static_cast<int64_t>(L.max_tiles) * 256), 256, 0, s>>>(w);
   k_results<<<1, 32, 0, s>>>(w);
   if (cudaGetLastError() != cudaSuccess) return SYLV_ERR_CUDA;

@@ -1560,15 +1560,17 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
                 nb = mul2(sh.nb_acc, eta - sh.e_acc);
                 for (int u = 0; u < g; ++u) nb += __shfl_sync(0xffffffffu, inc, u);
               } else {
-                // Terms normalised by 2^-emx (each <= 1, no overflow), summed in
-                // producer order with a 2^-50 rounding margin; z is the largest power
-                // of two with 2^z * sum * 2^emx <= omega.
-                const double tn = lane < g ? mul2(on, -ea) * mul2(pn, (eta - ep) - (emx - ea)) : 0.0;
+                // Terms normalised by 2^-emx (each <= 1, no overflow), multiplied and
+                // summed in producer order rounded towards +inf, plus 2^-1000 for any
+                // subnormal term, so sn bounds the exact normalised sum from above; z is
+                // then the largest power of two with 2^z * sn * 2^emx <= omega.
+                const double tn = lane < g ? __dmul_ru(mul2(on, -ea), mul2(pn, (eta - ep) - (emx - ea))) : 0.0;
                 double sn = mul2(sh.nb_acc, (eta - sh.e_acc) - emx);
-                for (int u = 0; u < g; ++u) sn += __shfl_sync(0xffffffffu, tn, u);
-                sn *= 1.0 + 0x1p-50;
-                // omega = 2^eo f, f in [1, 2): z = (eo - emx) + floor(log2(f / sn))
-                z = sn > 0.0 ? min(0, (eo - emx) + floor_log2(mul2(omega, -eo) / sn)) : 0;
+                for (int u = 0; u < g; ++u) sn = __dadd_ru(sn, __shfl_sync(0xffffffffu, tn, u));
+                sn = __dadd_ru(sn, 0x1p-1000);
+                // omega = 2^eo f, f in [1, 2): z = (eo - emx) + floor(log2(f / sn)), the
+                // quotient rounded towards -inf
+                z = min(0, (eo - emx) + floor_log2(__ddiv_rd(mul2(omega, -eo), sn)));
                 nb = mul2(sn, emx + z);
               }
               fast = (same && z == 0) ? 1 : 2;

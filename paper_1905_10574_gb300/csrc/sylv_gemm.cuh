@@ -101,16 +101,32 @@ __global__ void __launch_bounds__(256) k_residual(const double* __restrict__ A, 
   if ((tid & 31) == 0 && rmax) atomic_max_nonneg(rmax, mx);
 }
 
+// Exponent that undoes the adjoint solve's own scale 2^log2scale (rs: its device
+// result record, null: none), clamped where every finite double is sent to 0 or Inf.
+__device__ __forceinline__ int unscale_exp(const sylv_result* rs, int64_t extra) {
+  const int64_t e = extra - (rs ? rs->log2scale : 0);
+  return static_cast<int>(e < -4000 ? -4000 : (e > 4000 ? 4000 : e));
+}
+// v * 2^e; a finite v that leaves the binary64 range marks the record SYLV_OVERFLOWED.
+__device__ __forceinline__ double unscale(double v, int e, sylv_result* rs) {
+  const double r = mul2(v, e);
+  if (rs && isfinite(v) && !isfinite(r)) atomicMax(&rs->info, SYLV_OVERFLOWED);
+  return r;
+}
+
 // D = -P Q^T-like products for the adjoint: D[i,j] = -sum_c P(i,c) Q(j,c) with
 // P(i,c) = P[i*psi + c*psc], Q(j,c) = Q[j*qsj + c*qsc] (element strides, so the
 // same kernel serves Gamma Y^T, Y Gamma^T, Y^T Gamma and Gamma^T Y), masked to
 // the entries a quasi-triangular operand T (N x N, ldt) exposes: i <= j, or
-// i == j + 1 with T[i, j] != 0.  Other entries of D are set to 0.
+// i == j + 1 with T[i, j] != 0.  Other entries of D are set to 0.  With a result
+// record rs, D is multiplied by 2^-rs->log2scale (exact), undoing the scale of the
+// adjoint solve that produced P or Q.
 __global__ void __launch_bounds__(256) k_grad_product(const double* __restrict__ P, int64_t psi, int64_t psc,
                                                       const double* __restrict__ Q, int64_t qsj, int64_t qsc,
                                                       int64_t N, int64_t K, const double* __restrict__ T,
                                                       int64_t ldt, double* __restrict__ D, int64_t ldd,
-                                                      double sign) {
+                                                      double sign, sylv_result* rs) {
+  const int eu = unscale_exp(rs, 0);
   __shared__ __align__(16) double Ls[GK * GLD];
   __shared__ __align__(16) double Rs[GK * GLD];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -149,7 +165,7 @@ __global__ void __launch_bounds__(256) k_grad_product(const double* __restrict__
       const int64_t r = i0 + tx * 4 + i, c = j0 + ty * 4 + j;
       if (r < N && c < N) {
         const bool keep = (r <= c) || (r == c + 1 && T[r + c * ldt] != 0.0);
-        D[r + c * ldd] = keep ? sign * acc[i][j] : 0.0;
+        D[r + c * ldd] = keep ? unscale(sign * acc[i][j], eu, rs) : 0.0;
       }
     }
 }
@@ -312,6 +328,17 @@ __global__ void k_scale_pow2(double* M, int64_t ld, int64_t m, int64_t n, int e)
        t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t r = t % m, c = t / m;
     M[r + c * ld] = mul2(M[r + c * ld], e);
+  }
+}
+
+// M *= 2^(e - rs->log2scale) (in place, exact unless the range is left; see unscale).
+__global__ void k_unscale_pow2(double* M, int64_t ld, int64_t m, int64_t n, int64_t e, sylv_result* rs) {
+  const int eu = unscale_exp(rs, e);
+  if (eu == 0) return;
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < m * n;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t % m, c = t / m;
+    M[r + c * ld] = unscale(M[r + c * ld], eu, rs);
   }
 }
 
@@ -508,7 +535,8 @@ struct GradDesc {
   int64_t ldt;
   double* D;
   int64_t ldd;
-  double sign;  // -1 for dB of op(A) Y - Y op(B) = alpha C
+  double sign;      // -1 for dB of op(A) Y - Y op(B) = alpha C
+  sylv_result* rs;  // the adjoint solve's record: D is multiplied by 2^-rs->log2scale
 };
 
 __global__ void __launch_bounds__(256) k_grad_product_batched(const GradDesc* __restrict__ gd) {
@@ -519,6 +547,7 @@ __global__ void __launch_bounds__(256) k_grad_product_batched(const GradDesc* __
   const int64_t i0 = static_cast<int64_t>(blockIdx.x) * GT, j0 = static_cast<int64_t>(blockIdx.y) * GT;
   if (i0 >= g.N || j0 >= g.N) return;
   const bool active = i0 <= j0 + GT;
+  const int eu = unscale_exp(g.rs, 0);
   double acc[4][4] = {};
   if (active) {
     for (int64_t k0 = 0; k0 < g.K; k0 += GK) {
@@ -551,25 +580,27 @@ __global__ void __launch_bounds__(256) k_grad_product_batched(const GradDesc* __
       const int64_t r = i0 + tx * 4 + i, c = j0 + ty * 4 + j;
       if (r < g.N && c < g.N) {
         const bool keep = (r <= c) || (r == c + 1 && g.T[r + c * g.ldt] != 0.0);
-        g.D[r + c * g.ldd] = keep ? g.sign * acc[i][j] : 0.0;
+        g.D[r + c * g.ldd] = keep ? unscale(g.sign * acc[i][j], eu, g.rs) : 0.0;
       }
     }
 }
 
-// Batched power-of-two scaling: M_e *= 2^e_e (equation e = blockIdx.y).
+// Batched power-of-two scaling: M_e *= 2^(e_e - rs_e->log2scale) (equation e =
+// blockIdx.y; rs null: 2^e_e).
 struct ScaleDesc {
   double* M;
   int64_t ld, m, n;
-  int e;
-  int pad;
+  int64_t e;
+  sylv_result* rs;
 };
 __global__ void k_scale_pow2_batched(const ScaleDesc* __restrict__ sd) {
   const ScaleDesc s = sd[blockIdx.y];
-  if (s.e == 0) return;
+  const int eu = unscale_exp(s.rs, s.e);
+  if (eu == 0) return;
   for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < s.m * s.n;
        t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t r = t % s.m, c = t / s.m;
-    s.M[r + c * s.ld] = mul2(s.M[r + c * s.ld], s.e);
+    s.M[r + c * s.ld] = unscale(s.M[r + c * s.ld], eu, s.rs);
   }
 }
 

@@ -167,42 +167,56 @@ __device__ __forceinline__ int ceil_log2(double x) {
   return (__popcll(frac) == 1) ? f : f + 1;
 }
 
+// x = f * 2^e with f in [1, 2), for finite x > 0: e from the exponent field
+// (floor_log2), f by an exact power-of-two rescaling.
+struct FracExp {
+  double f;
+  int e;
+};
+__device__ __forceinline__ FracExp frac_exp(double x) {
+  const int e = floor_log2(x);
+  return {mul2(x, -e), e};
+}
+// f * 2^d as an upper bound for f in [1, 4): exact while the result is normal;
+// below that the bound 2^(d+2) is taken at 2^-998 (d < -1000).
+__device__ __forceinline__ double shifted_up(double f, int d) { return d < -1000 ? 0x1p-998 : mul2(f, d); }
+
 // ProtectUpdate (Sec. 2.1).  c, t, x are upper bounds of ||C||, ||A||, ||Y|| in
-// [0, omega]; returns z <= 0 such that 2^z (c + t x) <= omega holds exactly.  The
-// factor is the largest power of two the bound allows (up to rounding):
-// z = -ceil(log2 u), u = (c + t x)/omega computed as c/omega + (t/omega) x -- omega
-// is a power of two, so the quotients are exact and the sum cannot overflow --
-// and enlarged by 2^-50 to absorb the two roundings.  A cheaper test first
-// returns 0 when c + t x <= omega holds with a four-ulp margin.
+// [0, omega]; returns z <= 0 such that 2^z (c + t x) <= omega.  The test works on
+// significands and exponents: with c = f_c 2^e_c, t = f_t 2^e_t, x = f_x 2^e_x and
+// E = max(e_c, e_t + e_x),  c + t x = S 2^E  where S = f_c 2^(e_c-E) + f_t f_x 2^(e_t+e_x-E)
+// lies in [1, 6).  So E + 3 <= log2 omega needs no scaling.  Otherwise S is bounded
+// from above by arithmetic rounded towards +inf (S+ >= S), and with omega = f_w 2^e_w
+// z = e_w - E + floor(log2(f_w / S+)), the quotient rounded towards -inf:
+// 2^z S 2^E <= 2^e_w (f_w / S+) S <= omega.  z is the largest power of two the bound
+// allows unless S+ rounds across a power of two (then it is one binade smaller).
 __device__ __forceinline__ int protect_update(double c, double t, double x, double omega) {
-  const double shrink = 1.0 - 0x1p-51;
-  if (t == 0.0 || x == 0.0) return 0;
-  if (x <= 1.0) {
-    const double lim = (omega - c) * shrink;
-    if (lim > 0.0 && t * x <= lim) return 0;
-  } else if (t <= ((omega - c) / x) * shrink) {
-    return 0;
-  }
-  const double u = c / omega + (t / omega) * x;
-  const int z = -ceil_log2(u * (1.0 + 0x1p-50));
-  return z < 0 ? z : 0;
+  if (!(t > 0.0) || !(x > 0.0)) return 0;  // no update term: c <= omega already
+  const FracExp ft = frac_exp(t), fx = frac_exp(x), fw = frac_exp(omega);
+  const int ep = ft.e + fx.e;
+  FracExp fc{0.0, ep};
+  if (c > 0.0) fc = frac_exp(c);
+  const int E = max(ep, fc.e);
+  if (E + 3 <= fw.e) return 0;
+  const double sp = shifted_up(__dmul_ru(ft.f, fx.f), ep - E);
+  const double sc = c > 0.0 ? shifted_up(fc.f, fc.e - E) : 0.0;
+  const double q = __ddiv_rd(fw.f, __dadd_ru(sc, sp));  // in (1/6, 2)
+  return min(0, fw.e - E + floor_log2(q));
 }
 
 // ProtectDivision (Sec. 2.1) for |b| <= omega and divisor magnitude d > 0: returns
-// z <= 0 with 2^z |b| / d <= omega, the largest such power of two.  d*omega and
-// |b|*2^z are exact (omega is a power of two), so the estimate from the rounded
-// quotient is corrected by exact comparisons.
+// the largest z <= 0 with 2^z |b| / d <= omega.  With |b| = f_b 2^e_b, d = f_d 2^e_d,
+// omega = f_w 2^e_w the bound reads 2^z f_b 2^e_b <= f_d f_w 2^(e_d + e_w), so
+// z = e_d + e_w - e_b + floor(log2(f_d f_w / f_b)), the ratio rounded towards -inf
+// (then 2^z |b| <= d omega holds).  For a power-of-two omega the ratio f_d / f_b lies
+// in (1/2, 2) and its floor(log2) survives the rounding, so z is exactly the largest.
 __device__ __forceinline__ int protect_division(double b, double d, double omega) {
   b = fabs(b);
   d = fabs(d);
-  if (d < 1.0 && b > d * omega) {
-    const double lim = d * omega;
-    int z = floor_log2(lim / b);
-    while (z < 0 && mul2(b, z + 1) <= lim) ++z;
-    while (mul2(b, z) > lim) --z;
-    return z;
-  }
-  return 0;
+  if (!(b > 0.0) || d >= 1.0) return 0;  // |b| <= omega and d >= 1: |b| / d <= omega
+  const FracExp fb = frac_exp(b), fd = frac_exp(d), fw = frac_exp(omega);
+  const double r = __ddiv_rd(__dmul_rd(fd.f, fw.f), fb.f);  // in (1/2, 4)
+  return min(0, fd.e + fw.e - fb.e + floor_log2(r));
 }
 
 // ---------------------------------------------------------------- inter-CTA signalling

@@ -82,6 +82,7 @@ SIGNATURES = {
     "sylv_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sylv_version": (ctypes.c_char_p, []),
     "sylv_diag_wait_timeout": (ctypes.c_int, [_i64, _vp]),
+    "sylv_diag_guards": (ctypes.c_int, [_i64, _pd, _pd, _pd, _pd, _pd, _pd, _pd, ctypes.c_double, _vp]),
     "sylv_residual": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _vp]),
     "sylv_tri_solve_triangular": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, ctypes.POINTER(sylv_opts),
                                                  _vp]),
@@ -139,6 +140,12 @@ def sylv_version() -> str:
 
 def sylv_diag_wait_timeout(timeout_ms: int, stream=None) -> int:
     return load().sylv_diag_wait_timeout(int(timeout_ms), stream)
+
+
+def sylv_diag_guards(count, c, t, x, z_update, b, d, z_division, omega, stream=None) -> int:
+    """Device pointers (ints): the solver's ProtectUpdate/ProtectDivision evaluated
+    element by element; returns the status code."""
+    return load().sylv_diag_guards(int(count), c, t, x, z_update, b, d, z_division, float(omega), stream)
 
 
 def sylv_profile(enable: bool) -> int:
@@ -488,9 +495,6 @@ def _make_autograd_fn():
                                          dB.data_ptr(), _ld(dB), o, res)
             if rc >= 100 or rc < 0:
                 raise SylvError(rc, "sylv_tri_solve_backward")
-            if res.log2scale != 0:  # undo the adjoint solve's own scaling
-                s = 2.0 ** (-res.log2scale)
-                G, dA, dB = G * s, dA * s, dB * s
             return dA, dB, G, None, None, None
 
     return _Fn
@@ -569,10 +573,6 @@ def _make_batch_autograd_fn():
                                                       [max(n, 1)] * cnt, o)
             if rc >= 100 or rc < 0:
                 raise SylvError(rc, "sylv_tri_solve_backward_batched")
-            eg = [r.log2scale for r in res]
-            if any(eg):
-                s = torch.tensor([2.0 ** (-e) for e in eg], dtype=torch.float64, device=G.device).view(-1, 1, 1)
-                G, dA, dB = G * s, dA * s, dB * s
             return dA, dB, G, None, None, None
 
     return _Fn

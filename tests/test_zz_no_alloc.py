@@ -1,11 +1,11 @@
 """The allocation-free entry point, sylv_tri_solve_noalloc, against the regular
 entry point sylv_tri_solve_ex.
 
-Callers that cannot allocate device memory at solve time (inside a stream
-capture, in real-time loops, under a foreign allocator) use the allocation-free
-entry point; it runs the same solver with scratch in a fixed device array of the
-library.  This file is collected last on purpose; it passes alone in a fresh
-process and after the other tests.
+Callers that cannot allocate device memory at solve time (real-time loops that
+forbid allocator calls after start-up, hosts whose device memory belongs to a
+foreign allocator) use the allocation-free entry point; it runs the same solver
+with scratch in a fixed device array of the library.  This file is collected last
+on purpose; it passes alone in a fresh process and after the other tests.
 """
 import numpy as np
 import pytest
@@ -16,7 +16,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-TOL = 1e-12  # the relative Frobenius tolerance the other GPU tests use for Y/alpha
+TOL = 1e-13  # the relative Frobenius tolerance the other FP64 GPU tests use for Y/alpha
+SCRATCH = 16 << 20  # bytes of the fixed device array
 
 
 @pytest.fixture(scope="module")
@@ -71,11 +72,28 @@ def test_noalloc_matches_regular_entry_point_two_calls(sy):
         assert _rel(Ys, Y_ref) <= TOL
 
 
+def test_noalloc_fewer_ctas_than_regular(sy):
+    """m = n = 10000 at tile 32: the bookkeeping leaves room for fewer per-CTA factor
+    stores than the regular entry point's two CTAs per SM, so the allocation-free
+    call runs the tile kernel with fewer CTAs; its result must still match."""
+    m = n = 10000
+    p = q = -(-m // 32)
+    fixed_lower = p * q * (4 + 8 + 4 + 8) + (p * p + q * q) * 8  # flags, tasks, exponents, norms; norm tables
+    per_cta = 5 * 32 * 32 * 8 + 32 * 32 * 4
+    assert fixed_lower + 2 * torch.cuda.get_device_properties(0).multi_processor_count * per_cta > SCRATCH
+    A, B, C = inputs.problem(m, n, 41, kind="wellcond")
+    Y_ref, r_ref = _regular(sy, A, B, C)
+    Y, r = _noalloc(sy, A, B, C)
+    assert r.info == r_ref.info == 0
+    assert r.log2scale == r_ref.log2scale == 0
+    assert _rel(Y, Y_ref) <= TOL
+
+
 def test_noalloc_rejects_too_large(sy):
-    """Sizes whose bookkeeping exceeds the fixed scratch are refused on the host."""
+    """Sizes whose bookkeeping exceeds the fixed scratch are refused on the host from
+    the sizes alone, before any GPU work (so a one-element buffer stands in for the
+    operands)."""
     n = 24000
-    A = torch.zeros((n, n), dtype=torch.float64, device="cuda")
-    rc, _ = sy.sylv_tri_solve_noalloc(n, n, A.data_ptr(), n, A.data_ptr(), n, A.data_ptr(), n, 0, None)
+    buf = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rc, _ = sy.sylv_tri_solve_noalloc(n, n, buf.data_ptr(), n, buf.data_ptr(), n, buf.data_ptr(), n, 0, None)
     assert rc == sy.SYLV_ERR_WORKSPACE
-    del A
-    torch.cuda.empty_cache()

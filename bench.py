@@ -65,13 +65,14 @@ def parse():
                     help="skip the secondary measurements (mixed precision, batched, adjoint)")
     ap.add_argument("--mode", default="solve",
                     choices=["solve", "mixed", "batched", "adjoint", "smscale", "variants", "robustness", "residual",
-                             "robust_vs_plain", "small"],
+                             "robust_vs_plain", "small", "peaks"],
                     help="solve: the headline robust FP64 solve; mixed: FP32 + refinement vs FP64 at "
                          "m=n=8000; batched: 4096 uneven equations; adjoint: 256 Lyapunov forward+backward; "
                          "smscale: SM scaling; variants: sign variant, triangular solve, Bartels-Stewart at 4000; "
                          "robustness: robust vs plain on the paper's matrices, m=n=10000; residual: the "
                          "refinement's tensor-core residual at m=n=4000; robust_vs_plain: robust against non-robust "
-                         "FP64 at m=n=4000 (overflow workload); small: m=n=256 microseconds per solve")
+                         "FP64 at m=n=4000 (overflow workload); small: m=n=256 microseconds per solve; peaks: "
+                         "measured binary64/binary32 FMA pipe rates")
     return ap.parse_args()
 
 
@@ -927,6 +928,40 @@ def run_small(args):
             "us_per_solve": us, "gflops_2mnmn": flops_2(m, n) / us / 1e3, "info": int(res.info)}
 
 
+def run_peaks(args):
+    """Measured peak rates of the FMA pipes the tile kernels are bound by (the
+    denominators of their rooflines): binary64 FMA (the FP64 solve) and binary32 FMA
+    (the FP32 correction solves), from sylv_diag_fma_rate, clocks sampled meanwhile;
+    the derived unit-count peaks beside them."""
+    import torch
+    from paper_1905_10574_gb300 import build, sylv
+    build.build()
+    sylv.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    for kind, name, iters in ((0, "fp64_fma", 120000), (1, "fp32_fma", 6000000)):
+        vals = []
+        for _ in range(max(3, args.steps)):
+            rc, g, ms = sylv.sylv_diag_fma_rate(kind, iters, stream)
+            if rc != 0:
+                raise sylv.SylvError(rc, "sylv_diag_fma_rate")
+            vals.append((g, ms))
+        out[name] = {"gflops_best": max(v[0] for v in vals), "gflops_median": statistics.median(v[0] for v in vals),
+                     "ms_per_launch": statistics.median(v[1] for v in vals), "iters": iters}
+    clocks = sampler.stop()
+    out["fp64_fma"]["derived_gflops"] = nsm * 4 * 2.070
+    out["fp32_fma"]["derived_gflops"] = nsm * 256 * 2.070
+    return {"metric": "FMA pipe peak GFLOP/s", "value": out["fp64_fma"]["gflops_best"], "unit": "GFLOP/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f64 / f32", "data": "synthetic",
+            "config": {"probe": "one full wave of 256-thread CTAs, 8 independent FMA chains per thread", "sms": nsm},
+            "fp64_fma": out["fp64_fma"], "fp32_fma": out["fp32_fma"], "clocks": clocks}
+
+
 def secondary(args):
     """The other configurations, measured briefly beside the headline solve."""
     import argparse as _ap
@@ -975,6 +1010,8 @@ def main():
         print(json.dumps(run_robust_vs_plain(args)), flush=True)
     elif args.mode == "small":
         print(json.dumps(run_small(args)), flush=True)
+    elif args.mode == "peaks":
+        print(json.dumps(run_peaks(args)), flush=True)
     else:
         run_ours(args)
 

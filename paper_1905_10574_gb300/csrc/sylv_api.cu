@@ -262,6 +262,27 @@ __global__ void k_guards(int64_t count, const double* c, const double* t, const 
   zd[i] = protect_division(b[i], d[i], omega);
 }
 
+// Peak-rate probe of the FMA pipes: each thread runs 8 independent FMA chains for
+// `iters` rounds (16 flops per round and thread); the sum is stored only if it
+// matches an impossible value, so the compiler keeps every FMA.
+template <typename T>
+__global__ void __launch_bounds__(256, 8) k_fma_loop(int64_t iters, T seed, T* sink) {
+  T a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = seed + static_cast<T>(threadIdx.x + k);
+  const T b = static_cast<T>(0.999999), c = static_cast<T>(1e-7);
+  const unsigned n = static_cast<unsigned>(iters);
+#pragma unroll 4
+  for (unsigned i = 0; i < n; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+  }
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == static_cast<T>(-12345.0)) *sink = s;
+}
+
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? SYLV_OK : SYLV_ERR_CUDA; }
 
 int sm_count() {
@@ -751,6 +772,55 @@ int sylv_diag_guards(int64_t count, const double* c, const double* t, const doub
   k_guards<<<static_cast<unsigned>(blocks), 256, 0, s>>>(count, c, t, x, z_update, b, d, z_division, omega);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return SYLV_ERR_CUDA;
   return SYLV_OK;
+}
+
+int sylv_diag_fma_rate(int32_t kind, int64_t iters, double* gflops, double* ms, void* stream) {
+  if (kind != 0 && kind != 1) return -1;
+  if (iters <= 0 || iters >= (int64_t(1) << 32)) return -2;
+  if (!gflops) return -3;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Exactly one wave: as many 256-thread CTAs per SM as can be resident (a partial
+  // second wave would leave SMs idle and understate the rate).
+  int per_sm = 0;
+  const cudaError_t oe = kind == 0
+                             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_loop<double>, 256, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_loop<float>, 256, 0);
+  if (oe != cudaSuccess || per_sm <= 0) return SYLV_ERR_CUDA;
+  const int blocks = sm_count() * per_sm;
+  void* sink = nullptr;
+  if (cudaMalloc(&sink, 16) != cudaSuccess) return SYLV_ERR_CUDA;
+  cudaEvent_t e0, e1;
+  int rc = SYLV_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess) rc = SYLV_ERR_CUDA;
+  if (!rc && cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    rc = SYLV_ERR_CUDA;
+  }
+  if (!rc) {
+    auto launch = [&](int64_t it) {
+      if (kind == 0)
+        k_fma_loop<double><<<blocks, 256, 0, s>>>(it, 1.0, static_cast<double*>(sink));
+      else
+        k_fma_loop<float><<<blocks, 256, 0, s>>>(it, 1.0f, static_cast<float*>(sink));
+    };
+    launch(std::max<int64_t>(iters / 8, 1));  // warm-up (clocks up, code loaded)
+    cudaEventRecord(e0, s);
+    launch(iters);
+    cudaEventRecord(e1, s);
+    float t = 0.0f;
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&t, e0, e1) != cudaSuccess || t <= 0.0f) {
+      rc = SYLV_ERR_CUDA;
+    } else {
+      const double flops = 16.0 * static_cast<double>(iters) * blocks * 256.0;
+      *gflops = flops / (t * 1e-3) / 1e9;
+      if (ms) *ms = t;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  cudaFree(sink);
+  return rc;
 }
 
 const char* sylv_error_string(int code) {

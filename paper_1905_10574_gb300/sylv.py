@@ -83,6 +83,8 @@ SIGNATURES = {
     "sylv_version": (ctypes.c_char_p, []),
     "sylv_diag_wait_timeout": (ctypes.c_int, [_i64, _vp]),
     "sylv_diag_guards": (ctypes.c_int, [_i64, _pd, _pd, _pd, _pd, _pd, _pd, _pd, ctypes.c_double, _vp]),
+    "sylv_diag_fma_rate": (ctypes.c_int, [_i32, _i64, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), _vp]),
     "sylv_residual": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _pd, _i64, _vp]),
     "sylv_tri_solve_triangular": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, ctypes.POINTER(sylv_opts),
                                                  _vp]),
@@ -146,6 +148,13 @@ def sylv_diag_guards(count, c, t, x, z_update, b, d, z_division, omega, stream=N
     """Device pointers (ints): the solver's ProtectUpdate/ProtectDivision evaluated
     element by element; returns the status code."""
     return load().sylv_diag_guards(int(count), c, t, x, z_update, b, d, z_division, float(omega), stream)
+
+
+def sylv_diag_fma_rate(kind: int, iters: int, stream=None):
+    """(status, GFLOP/s, ms) of the FMA peak probe: kind 0 binary64, 1 binary32."""
+    g, t = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = load().sylv_diag_fma_rate(int(kind), int(iters), ctypes.byref(g), ctypes.byref(t), stream)
+    return rc, g.value, t.value
 
 
 def sylv_profile(enable: bool) -> int:

@@ -681,6 +681,46 @@ def run_batched(args):
     e1.record(cur)
     torch.cuda.synchronize()
     seq_ms = e0.elapsed_time(e1) * count / len(sample)
+    # FP32 + refinement on the same equations and tiles, at the 1e-12 forward-error
+    # target (MIXED_TOL), graph-captured the same way; its solutions are compared with
+    # the FP64 batch's (Cs holds them after the last replay).
+    Cr = [c.clone() for c in C0s]
+    rstream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(rstream):
+        ropts = sylv.make_opts(stream=rstream.cuda_stream, precision="fp32_refine", tol=MIXED_TOL)
+        rplan = sylv.sylv_batch_create([m for m, _ in shapes], [n for _, n in shapes], [a.data_ptr() for a in As],
+                                       [a.stride(1) for a in As], [b.data_ptr() for b in Bs],
+                                       [b.stride(1) for b in Bs], [c.data_ptr() for c in Cr],
+                                       [c.stride(1) for c in Cr], ropts, tiles=tiles)
+        rrc = sylv.sylv_batch_execute(rplan, rstream.cuda_stream)
+        rstream.synchronize()
+        rgraph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(rgraph, stream=rstream):
+            rrc |= sylv.sylv_batch_execute(rplan, torch.cuda.current_stream().cuda_stream)
+    if rrc:
+        raise sylv.SylvError(rrc, "refined batch")
+    rts = []
+    for i in range(args.warmup + args.steps):
+        for c, c0 in zip(Cr, C0s):
+            c.copy_(c0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(rs)
+        rgraph.replay()
+        b.record(rs)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            rts.append(a.elapsed_time(b))
+    rrc, rres = sylv.sylv_batch_results(rplan, count)
+    sylv.sylv_batch_destroy(rplan)
+    rms = sum(rts) / len(rts)
+    errs = [float(torch.linalg.norm(y - c) / torch.linalg.norm(c)) for y, c in zip(Cr, Cs)]
+    refined = {"solves_per_s": count / (rms / 1000), "ms_per_step": rms, "tol": MIXED_TOL, "accuracy_target": 1e-12,
+               "worst_info": max(r.info for r in rres), "iters_max": max(r.iters for r in rres),
+               "iters_mean": sum(r.iters for r in rres) / count,
+               "max_rel_err_vs_fp64_batch": max(errs), "speedup_vs_fp64_batch": ms / rms}
+    del Cr
     line = {"metric": "batched solves/s", "value": count / (ms / 1000), "unit": "solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64",
             "data": "synthetic",
@@ -688,7 +728,8 @@ def run_batched(args):
                        "tiles": "autotuned per size bucket" if not args.tile else args.tile,
                        "tile_mix": {str(t): tiles.count(t) for t in sorted(set(tiles))}, "cuda_graph": True},
             "gflops_2mnmn": flops / (ms / 1000) / 1e9, "worst_info": max(r.info for r in res),
-            "one_call_per_equation_ms": seq_ms, "speedup_vs_one_call_per_equation": seq_ms / ms}
+            "one_call_per_equation_ms": seq_ms, "speedup_vs_one_call_per_equation": seq_ms / ms,
+            "fp32_refine": refined}
     return line
 
 

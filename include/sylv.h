@@ -145,8 +145,13 @@ size_t sylv_workspace_size(int64_t m, int64_t n, const sylv_opts* opts);
  * dependences).  Not in the paper.
  *
  * opts->transa / opts->transb apply to every equation (the plan keeps
- * anti-transposed copies of A_i / B_i and reverses C_i in place around the solve);
- * FP32_REFINE is not available for batches.
+ * anti-transposed copies of A_i / B_i and reverses C_i in place around the solve).
+ * With opts->precision = SYLV_FP32_REFINE every equation is refined as in
+ * sylv_tri_solve_ex (binary32 robust correction solves, one batched tile-kernel
+ * launch per correction; binary64-accurate residuals in double-float arithmetic on
+ * the binary32 pipes); each equation stops on its own tolerance test, after which
+ * its work is skipped, and results[i].iters / last_update report it.  The launch
+ * sequence is the same whatever converges, so it stays capturable.
  *
  * sylv_batch_create builds a plan: it validates the HOST arrays m[i], n[i],
  * lda[i], ldb[i], ldc[i] and the device pointers A[i], B[i], C[i] (HOST arrays of
@@ -188,7 +193,8 @@ int sylv_tri_solve_batched(int32_t count, const int64_t* m, const int64_t* n,
  * with op(A) X + X op(B) = C, alpha a power of two held fixed (it is piecewise
  * constant in the inputs).  Given G = dL/dY (device, m x n, ldg) this computes
  *   Gamma   solving  op(A)^T Gamma + Gamma op(B)^T = G  (the same robust tiled
- *           solver with both transposes flipped; Y, A, B unchanged),
+ *           solver with both transposes flipped, in opts->precision: FP64, or
+ *           FP32 + refinement; Y, A, B unchanged),
  *   dL/dC = alpha * Gamma                     -> written over G,
  *   dL/dA = -Gamma Y^T  (op(A) = A)  or  -Y Gamma^T  (op(A) = A^T)   -> dA (m x m, ldda),
  *   dL/dB = -Y^T Gamma  (op(B) = B)  or  -Gamma^T Y  (op(B) = B^T)   -> dB (n x n, lddb),
@@ -284,21 +290,27 @@ int sylv_tri_solve_triangular(int64_t m, int64_t n, const double* A, int64_t lda
  * orthogonal, TA, TB upper quasi-triangular, from an external eigensolver), solve
  *     A X + isgn X B = alpha C
  * as C~ = U^T C V, TA Y + isgn Y TB = alpha C~ (sylv_tri_solve_ex), X = U Y V^T.  The
- * four products are plain dense GEMMs (cuBLAS); the solve is the library's.
+ * four dense products run on the library's tensor-core GEMM in its binary64-accurate
+ * form (bf16 operand slices by error-free splitting, exact integer accumulation of
+ * the leading slice pairs): each product term is exact to within 2^-54 of (row
+ * maximum) x (column maximum), as for sylv_residual.  A timeout of that GEMM's
+ * pipeline waits gives SYLV_ERR_TIMEOUT (sync mode).
  *   U, ldu    device, m x m orthogonal, read only
  *   TA, ldta  device, m x m upper quasi-triangular, read only
  *   V, ldv    device, n x n orthogonal, read only
  *   TB, ldtb  device, n x n upper quasi-triangular, read only
  *   C, ldc    device, m x n; on exit X
  *   opts      as for sylv_tri_solve_ex (transa/transb must be 0; the workspace, if
- *             given, must also hold an m x n double matrix: sylv_workspace_size +
- *             8 m n bytes rounded up to 256)
+ *             given, must hold sylv_schur_workspace_size(m, n, opts) bytes)
  *   result    as for sylv_tri_solve_ex
  * Returns as sylv_tri_solve_ex; -3/-4 U, -7/-8 V, -5/-6 TA, -9/-10 TB, -11/-12 C.
  */
 int sylv_solve_schur(int64_t m, int64_t n, const double* U, int64_t ldu, const double* TA, int64_t ldta,
                      const double* V, int64_t ldv, const double* TB, int64_t ldtb, double* C, int64_t ldc,
                      const sylv_opts* opts, sylv_result* result);
+/* Bytes of device workspace sylv_solve_schur needs for these sizes and options
+ * (opts may be NULL; 0 for negative sizes or invalid options). */
+size_t sylv_schur_workspace_size(int64_t m, int64_t n, const sylv_opts* opts);
 
 /*
  * sylv_residual -- R = C - (A X + X B) to binary64 accuracy, the residual of

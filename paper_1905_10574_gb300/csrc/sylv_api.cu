@@ -9,12 +9,12 @@
 #include <new>
 #include <vector>
 
-#include <cublas_v2.h>
 
 #include "sylv_gemm.cuh"
 #include "sylv_internal.cuh"
 #include "sylv_launch.h"
 #include "sylv_prep.cuh"
+#include "sylv_refine_batch.cuh"
 
 using namespace sylv;
 
@@ -879,14 +879,20 @@ int sylv_tri_solve_triangular(int64_t m, int64_t n, const double* A, int64_t lda
   return solve_impl(m, n, A, lda, nullptr, 1, C, ldc, o, nullptr, result);
 }
 
-// cuBLAS handle per device (the back-transform's plain GEMMs), created on first use.
-static cublasHandle_t blas_handle(int dev) {
-  static std::mutex mu;
-  static cublasHandle_t h[64] = {};
-  std::lock_guard<std::mutex> lk(mu);
-  if (dev < 0 || dev >= 64) return nullptr;
-  if (!h[dev] && cublasCreate(&h[dev]) != CUBLAS_STATUS_SUCCESS) h[dev] = nullptr;
-  return h[dev];
+// Bytes of the Bartels-Stewart wrapper's workspace: W (m x n), the operand slices
+// of its products, a flag, and the solve's own workspace.
+static size_t schur_ws_bytes(int64_t m, int64_t n, const Opts& o, size_t* wbytes, size_t* zbytes) {
+  const SolvePlan P = plan_solve(m, n, o);
+  *wbytes = align_up(sizeof(double) * m * n);
+  *zbytes = align_up(oz_dense_bytes(m, n, std::max(m, n)));
+  return *wbytes + *zbytes + kAlign + P.total;
+}
+
+size_t sylv_schur_workspace_size(int64_t m, int64_t n, const sylv_opts* opts) {
+  Opts o{};
+  if (m < 0 || n < 0 || read_opts(opts, &o)) return 0;
+  size_t wb = 0, zb = 0;
+  return schur_ws_bytes(std::max<int64_t>(m, 1), std::max<int64_t>(n, 1), o, &wb, &zb);
 }
 
 int sylv_solve_schur(int64_t m, int64_t n, const double* U, int64_t ldu, const double* TA, int64_t ldta,
@@ -904,34 +910,38 @@ int sylv_solve_schur(int64_t m, int64_t n, const double* U, int64_t ldu, const d
   if (o.transa || o.transb) return SYLV_ERR_UNSUPPORTED;
   if (m == 0 || n == 0) return solve_impl(m, n, TA, ldta, TB, ldtb, C, ldc, o, o.sync ? result : nullptr,
                                           o.sync ? nullptr : result);
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return SYLV_ERR_CUDA;
-  cublasHandle_t h = blas_handle(dev);
-  if (!h || cublasSetStream(h, o.stream) != CUBLAS_STATUS_SUCCESS) return SYLV_ERR_CUDA;
-  // Workspace: W (m x n) for the GEMM intermediates, then the solver's own scratch.
+  // Workspace: W (m x n) for the intermediate products, the slices of the products'
+  // operands, a timeout flag, then the solver's own scratch.
   Opts os = o;
   const SolvePlan P = plan_solve(m, n, os);
-  const size_t wbytes = align_up(sizeof(double) * m * n);
+  size_t wbytes = 0, zbytes = 0;
+  const size_t need = schur_ws_bytes(m, n, o, &wbytes, &zbytes);
+  const size_t fbytes = kAlign;
   char* ws = nullptr;
   if (o.ws) {
-    if (o.ws_bytes < wbytes + P.total || (reinterpret_cast<uintptr_t>(o.ws) & (kAlign - 1))) return SYLV_ERR_WORKSPACE;
+    if (o.ws_bytes < need || (reinterpret_cast<uintptr_t>(o.ws) & (kAlign - 1))) return SYLV_ERR_WORKSPACE;
     ws = static_cast<char*>(o.ws);
   } else {
     void* p = nullptr;
-    const int rc = get_workspace(wbytes + P.total, &p);
+    const int rc = get_workspace(need, &p);
     if (rc) return rc;
     ws = static_cast<char*>(p);
   }
   double* W = reinterpret_cast<double*>(ws);
-  os.ws = ws + wbytes;
+  char* zb = ws + wbytes;
+  int* err = reinterpret_cast<int*>(ws + wbytes + zbytes);
+  os.ws = ws + wbytes + zbytes + fbytes;
   os.ws_bytes = P.total;
-  const double one = 1.0, zero = 0.0;
-  const int M = static_cast<int>(m), N = static_cast<int>(n);
-  // C~ = U^T C V (Bartels-Stewart, eqs. (3) and (5)): W = U^T C, C = W V.
-  if (cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, M, N, M, &one, U, static_cast<int>(ldu), C, static_cast<int>(ldc), &zero,
-                  W, M) != CUBLAS_STATUS_SUCCESS ||
-      cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, M, N, N, &one, W, M, V, static_cast<int>(ldv), &zero, C,
-                  static_cast<int>(ldc)) != CUBLAS_STATUS_SUCCESS)
+  cudaStream_t s = o.stream;
+  const long long tmo = o.timeout_ns;
+  // Every product is R -= L Q^T on the tensor cores (binary64-accurate splitting),
+  // into a zeroed R, so each pair of products carries the sign twice.
+  // C~ = U^T C V (Bartels-Stewart, eqs. (3) and (5)): W = -U^T C, C = -W V.
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess ||
+      cudaMemsetAsync(W, 0, sizeof(double) * m * n, s) != cudaSuccess ||
+      oz_product(zb, U, ldu, 1, C, ldc, 1, m, n, m, W, m, err, tmo, s) != cudaSuccess ||
+      cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * m, n, s) != cudaSuccess ||
+      oz_product(zb, W, 1, m, V, ldv, 1, m, n, n, C, ldc, err, tmo, s) != cudaSuccess)
     return SYLV_ERR_CUDA;
   // The robust triangular solve in the Schur basis; its result record waits on the device.
   const bool sync = o.sync != 0;
@@ -939,20 +949,24 @@ int sylv_solve_schur(int64_t m, int64_t n, const double* U, int64_t ldu, const d
   sylv_result* res_dev = reinterpret_cast<sylv_result*>(static_cast<char*>(os.ws) + P.L.res);
   int rc = solve_impl(m, n, TA, ldta, TB, ldtb, C, ldc, os, nullptr, nullptr);
   if (rc) return rc;
-  // X = U Y V^T: W = U Y, C = W V^T.
-  if (cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, M, N, M, &one, U, static_cast<int>(ldu), C, static_cast<int>(ldc), &zero,
-                  W, M) != CUBLAS_STATUS_SUCCESS ||
-      cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, M, N, N, &one, W, M, V, static_cast<int>(ldv), &zero, C,
-                  static_cast<int>(ldc)) != CUBLAS_STATUS_SUCCESS)
+  // X = U Y V^T: W = -U Y, C = -W V^T.
+  if (cudaMemsetAsync(W, 0, sizeof(double) * m * n, s) != cudaSuccess ||
+      oz_product(zb, U, 1, ldu, C, ldc, 1, m, n, m, W, m, err, tmo, s) != cudaSuccess ||
+      cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * m, n, s) != cudaSuccess ||
+      oz_product(zb, W, 1, m, V, 1, ldv, m, n, n, C, ldc, err, tmo, s) != cudaSuccess)
     return SYLV_ERR_CUDA;
   if (!sync) {
-    if (result && cudaMemcpyAsync(result, res_dev, sizeof(sylv_result), cudaMemcpyDeviceToDevice, o.stream) != cudaSuccess)
+    if (result && cudaMemcpyAsync(result, res_dev, sizeof(sylv_result), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
       return SYLV_ERR_CUDA;
     return cuda_status(cudaGetLastError());
   }
   sylv_result r{};
-  if (cudaMemcpyAsync(&r, res_dev, sizeof(r), cudaMemcpyDeviceToHost, o.stream) != cudaSuccess) return SYLV_ERR_CUDA;
-  if (cudaStreamSynchronize(o.stream) != cudaSuccess) return SYLV_ERR_CUDA;
+  int herr = 0;
+  if (cudaMemcpyAsync(&r, res_dev, sizeof(r), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return SYLV_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SYLV_ERR_CUDA;
+  if (herr && r.info < 100) r.info = herr;
   if (result) *result = r;
   return r.info;
 }
@@ -984,6 +998,16 @@ struct sylv_batch_plan {
   int pmax_all = 0;
   TransDesc* dta = nullptr;  // device descriptors of the anti-transposed copies (transa)
   TransDesc* dtb = nullptr;  // (transb)
+  // FP32 + refinement (precision == SYLV_FP32_REFINE)
+  RefEq* dref = nullptr;      // device descriptors, one per equation
+  char* ref_zero = nullptr;   // slots, refinement states and counters: zeroed by every execute
+  size_t ref_zero_bytes = 0;
+  char* ref_x = nullptr;      // the accumulated solutions X: zeroed by every execute
+  size_t ref_x_bytes = 0;
+  int* ref_counters = nullptr;
+  RefineState* ref_rs = nullptr;
+  int maxit = 6;
+  double tol = 0.0;
 };
 
 int sylv_batch_create(sylv_batch_plan** plan, int32_t count, const int64_t* m, const int64_t* n,
@@ -1003,7 +1027,8 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
   Opts o{};
   int rc = read_opts(opts, &o);
   if (rc) return rc;
-  if (o.precision == SYLV_FP32_REFINE) return SYLV_ERR_UNSUPPORTED;
+  const bool refine = o.precision == SYLV_FP32_REFINE;
+  if (count > 65535) return SYLV_ERR_UNSUPPORTED;  // equations index a grid dimension of the batched kernels
   std::vector<Shape> sh;
   std::vector<const void*> Av, Bv;
   std::vector<void*> Cv;
@@ -1039,7 +1064,10 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
   P->transb = o.transb;
   P->isgn = o.isgn;
   P->max_sms = o.max_sms;
-  P->L = make_layout(sh, 0, 0, 2, static_cast<int>(sizeof(double)));
+  P->maxit = o.maxit;
+  P->tol = o.tol;
+  P->L = refine ? make_layout(sh, 0, 0, max_ctas_per_sm<float>(), static_cast<int>(sizeof(float)))
+                : make_layout(sh, 0, 0, 2, static_cast<int>(sizeof(double)));
   P->maxN = maxN;
   P->pmax_all = pmax_all;
   if (count > 0) {
@@ -1061,6 +1089,49 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
     off = align_up(off + sizeof(TransDesc) * count);
     const size_t off_db = off;
     off = align_up(off + sizeof(TransDesc) * count);
+    // FP32 + refinement: per-equation work arrays (binary32 operand pairs and
+    // right-hand side, binary64 R, X, D), then the zeroed region (slots, states,
+    // counters) and the descriptors.
+    const int nslots = 2 + 3 * (o.maxit + 1);
+    std::vector<size_t> o_ah(count), o_al(count), o_bh(count), o_bl(count), o_rf(count), o_r(count), o_x(count),
+        o_d(count);
+    size_t off_zero = 0, off_rs = 0, off_cnt = 0, off_ref = 0, off_x0 = 0, off_x1 = 0;
+    if (refine) {
+      for (int i = 0; i < count; ++i) {
+        const size_t mm = sh[i].m * sh[i].m, nn = sh[i].n * sh[i].n, mn = sh[i].m * sh[i].n;
+        o_ah[i] = off;
+        off = align_up(off + sizeof(float) * mm);
+        o_al[i] = off;
+        off = align_up(off + sizeof(float) * mm);
+        o_bh[i] = off;
+        off = align_up(off + sizeof(float) * nn);
+        o_bl[i] = off;
+        off = align_up(off + sizeof(float) * nn);
+        o_rf[i] = off;
+        off = align_up(off + sizeof(float) * mn);
+        o_r[i] = off;
+        off = align_up(off + sizeof(double) * mn);
+        o_d[i] = off;
+        off = align_up(off + sizeof(double) * mn);
+      }
+      off_x0 = off;
+      for (int i = 0; i < count; ++i) {
+        o_x[i] = off;
+        off = align_up(off + sizeof(double) * sh[i].m * sh[i].n);
+      }
+      off_x1 = off;
+      off_zero = off;
+      off = align_up(off + sizeof(unsigned long long) * nslots * count);
+      off_rs = off;
+      off = align_up(off + sizeof(RefineState) * count);
+      off_cnt = off;
+      off = align_up(off + 4 * sizeof(int));
+      const size_t zero_end = off;
+      off_ref = off;
+      off = align_up(off + sizeof(RefEq) * count);
+      P->ref_zero_bytes = zero_end - off_zero;
+      P->ref_x_bytes = off_x1 - off_x0;
+    }
     void* p = nullptr;
     if (cudaMalloc(&p, off) != cudaSuccess) {
       cudaGetLastError();
@@ -1086,8 +1157,56 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
     }
     P->dta = reinterpret_cast<TransDesc*>(P->ws + off_da);
     P->dtb = reinterpret_cast<TransDesc*>(P->ws + off_db);
-    std::vector<Inst> I = make_insts(sh, P->L, Av, la, Bv, lb, Cv, lc, o.precision == SYLV_FP64 ? 1 : 0, o.omega);
+    std::vector<RefEq> re;
+    std::vector<Inst> I;
+    if (refine) {
+      // The tile kernel solves the binary32 correction equations: its operands are the
+      // high parts Ah, Bh, its right-hand side (overwritten by D) Rf.
+      std::vector<const void*> Af(count), Bf(count);
+      std::vector<void*> Rfv(count);
+      std::vector<int64_t> lm(count), ln(count);
+      P->ref_zero = P->ws + off_zero;
+      P->ref_x = P->ws + off_x0;
+      P->ref_rs = reinterpret_cast<RefineState*>(P->ws + off_rs);
+      P->ref_counters = reinterpret_cast<int*>(P->ws + off_cnt);
+      P->dref = reinterpret_cast<RefEq*>(P->ws + off_ref);
+      re.resize(count);
+      for (int i = 0; i < count; ++i) {
+        RefEq& e = re[i];
+        e.m = sh[i].m;
+        e.n = sh[i].n;
+        e.A = static_cast<const double*>(Av[i]);
+        e.lda = la[i];
+        e.B = static_cast<const double*>(Bv[i]);
+        e.ldb = lb[i];
+        e.C = static_cast<double*>(Cv[i]);
+        e.ldc = lc[i];
+        e.Ah = reinterpret_cast<float*>(P->ws + o_ah[i]);
+        e.Al = reinterpret_cast<float*>(P->ws + o_al[i]);
+        e.Bh = reinterpret_cast<float*>(P->ws + o_bh[i]);
+        e.Bl = reinterpret_cast<float*>(P->ws + o_bl[i]);
+        e.Rf = reinterpret_cast<float*>(P->ws + o_rf[i]);
+        e.R = reinterpret_cast<double*>(P->ws + o_r[i]);
+        e.X = reinterpret_cast<double*>(P->ws + o_x[i]);
+        e.D = reinterpret_cast<double*>(P->ws + o_d[i]);
+        e.slots = reinterpret_cast<unsigned long long*>(P->ws + off_zero) + static_cast<size_t>(nslots) * i;
+        e.rs = P->ref_rs + i;
+        Af[i] = e.Ah;
+        Bf[i] = e.Bh;
+        Rfv[i] = e.Rf;
+        lm[i] = std::max<int64_t>(e.m, 1);
+        ln[i] = std::max<int64_t>(e.n, 1);
+      }
+      I = make_insts(sh, P->L, Af, lm, Bf, ln, Rfv, lm, 1, o.omega);
+      P->w.eqskip = &P->ref_rs[0].conv;
+      P->w.eqskip_stride = static_cast<int32_t>(sizeof(RefineState) / sizeof(int));
+      P->w.skip = P->ref_counters + 2;
+    } else {
+      I = make_insts(sh, P->L, Av, la, Bv, lb, Cv, lc, o.precision == SYLV_FP64 ? 1 : 0, o.omega);
+    }
     bool ok = cudaMemcpy(P->w.inst, I.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok && refine)
+      ok = cudaMemcpy(P->dref, re.data(), sizeof(RefEq) * count, cudaMemcpyHostToDevice) == cudaSuccess;
     if (ok && o.transa)
       ok = cudaMemcpy(P->dta, ta.data(), sizeof(TransDesc) * count, cudaMemcpyHostToDevice) == cudaSuccess;
     if (ok && (o.transb || o.isgn < 0))
@@ -1102,9 +1221,56 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
   return SYLV_OK;
 }
 
+// The batched FP32 + refinement launch sequence (fixed, so capturable): operand
+// copies and flips for the transposed forms, the binary32 pairs of A and B, the
+// structure scan and task list of the correction equations, then maxit rounds of
+// residual -> binary32 right-hand side -> tile kernel -> X += D -> check.
+static int execute_refine(sylv_batch_plan* P, cudaStream_t s) {
+  const Layout& L = P->L;
+  const int count = P->count;
+  const int nt32 = static_cast<int>((P->maxN + 31) / 32);
+  const int nt64 = static_cast<int>((P->maxN + GT - 1) / GT);
+  const int eg = std::max(1, std::min<int>(static_cast<int>((P->maxN * P->maxN + 255) / 256), 64));
+  if (P->transa) {
+    k_anti_transpose_batched<<<dim3(nt32, nt32, count), 256, 0, s>>>(P->dta);
+    k_bref_flip<<<dim3(eg, count), 256, 0, s>>>(P->dref, 0);
+  }
+  if (P->transb || P->isgn < 0) k_anti_transpose_batched<<<dim3(nt32, nt32, count), 256, 0, s>>>(P->dtb);
+  if (P->transb) k_bref_flip<<<dim3(eg, count), 256, 0, s>>>(P->dref, 1);
+  if (cudaMemsetAsync(P->ref_zero, 0, P->ref_zero_bytes, s) != cudaSuccess) return SYLV_ERR_CUDA;
+  if (cudaMemsetAsync(P->ref_x, 0, P->ref_x_bytes, s) != cudaSuccess) return SYLV_ERR_CUDA;
+  if (cudaMemsetAsync(P->ws + L.zero_lo, 0, L.zero_hi - L.zero_lo, s) != cudaSuccess) return SYLV_ERR_CUDA;
+  k_bref_maxabs<<<dim3(eg, count), 256, 0, s>>>(P->dref);
+  k_bref_split<<<dim3(eg, count), 256, 0, s>>>(P->dref);
+  cudaError_t e = run_prep<float>(P->w, L, count, P->maxN, P->pmax_all, s);
+  if (e != cudaSuccess) return SYLV_ERR_CUDA;
+  const int ntasks = static_cast<int>(std::min<int64_t>(L.sum_tiles, L.ncta));
+  for (int it = 0; it < P->maxit; ++it) {
+    if (it == 0)
+      k_bref_copy_max<<<dim3(eg, count), 256, 0, s>>>(P->dref);
+    else
+      k_bref_residual<<<dim3(nt64, nt64, count), 256, 0, s>>>(P->dref, it);
+    k_bref_to_float<<<dim3(eg, count), 256, 0, s>>>(P->dref, it);
+    if (it > 0) {
+      if (cudaMemsetAsync(P->w.tflag, 0, sizeof(int32_t) * L.sum_tiles, s) != cudaSuccess) return SYLV_ERR_CUDA;
+      if (cudaMemsetAsync(&P->w.ctrl->ticket, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return SYLV_ERR_CUDA;
+    }
+    e = launch_dag_f32(P->tt, P->w, ntasks, s, P->max_sms);
+    if (e != cudaSuccess) return SYLV_ERR_CUDA;
+    k_bref_accumulate<<<grid_for(L.sum_tiles * 256), 256, 0, s>>>(P->w, P->dref, it);
+    if (cudaMemsetAsync(P->ref_counters, 0, 2 * sizeof(int), s) != cudaSuccess) return SYLV_ERR_CUDA;
+    k_bref_check<<<(count + 255) / 256, 256, 0, s>>>(P->dref, count, it, P->tol, P->w, P->ref_counters);
+  }
+  k_bref_finish<<<dim3(eg, count), 256, 0, s>>>(P->dref, P->w.res);
+  if (P->transa) k_bref_flip<<<dim3(eg, count), 256, 0, s>>>(P->dref, 0);
+  if (P->transb) k_bref_flip<<<dim3(eg, count), 256, 0, s>>>(P->dref, 1);
+  return cuda_status(cudaGetLastError());
+}
+
 int sylv_batch_execute(sylv_batch_plan* P, void* stream) {
   if (!P) return -1;
   if (P->count == 0) return SYLV_OK;
+  if (P->precision == SYLV_FP32_REFINE) return execute_refine(P, static_cast<cudaStream_t>(stream));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Layout& L = P->L;
   const int nt32 = static_cast<int>((P->maxN + 31) / 32);
@@ -1172,7 +1338,6 @@ int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, 
   Opts o{};
   int rc = read_opts(opts, &o);
   if (rc) return rc;
-  if (o.precision == SYLV_FP32_REFINE) o.precision = SYLV_FP64;
   if (m == 0 || n == 0) {
     if (result && o.sync) {
       *result = sylv_result{};
@@ -1271,7 +1436,6 @@ int sylv_tri_solve_backward_batched(int32_t count, const int64_t* m, const int64
     sylv_default_opts(&oa);
   oa.transa ^= 1;
   oa.transb ^= 1;
-  oa.precision = SYLV_FP64;
   sylv_batch_plan* P = nullptr;
   rc = sylv_batch_create(&P, count, m, n, A, lda, B, ldb, G, ldg, &oa);
   if (rc) return rc;

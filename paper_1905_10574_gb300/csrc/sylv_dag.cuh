@@ -79,7 +79,7 @@ struct DagSmem {
   unsigned long long umax;
   unsigned long long stage_bar;        // mbarrier of the bulk-copy staging (packed tiles)
   double nb_acc;
-  int task, abort, e_acc, sacc, sop, g, e_diag, pb, qb, nscale, flags, slow;
+  int task, abort, e_acc, sacc, sop, g, e_diag, pb, qb, nscale, flags, slow, skipt;
 };
 
 // Upper bound on log2|v| for finite v (exponent field + 1; 2^-1022 for zero/subnormals).
@@ -1378,9 +1378,23 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
       sh.abort = 0;
       sh.flags = 0;
       sh.nscale = 0;
+      sh.skipt = 0;
+      if (sh.task >= 0 && w.eqskip) {
+        // A converged equation of a batched refinement: its tiles are only marked
+        // final (every consumer belongs to the same equation and skips as well).
+        const Task t0 = w.tasks[sh.task];
+        if (ld_volatile(w.eqskip + static_cast<int64_t>(t0.inst) * w.eqskip_stride)) {
+          st_release(w.tflag + w.inst[t0.inst].tile + t0.tile, 1);
+          sh.skipt = 1;
+        }
+      }
     }
     __syncthreads();
     if (sh.task < 0) break;
+    if (sh.skipt) {
+      __syncthreads();  // thread 0 rewrites sh.task next
+      continue;
+    }
     const Task task = w.tasks[sh.task];
     const Inst I = w.inst[task.inst];
     InstState* st = &w.st[task.inst];

@@ -275,14 +275,15 @@ struct RefineState {
 // corrections contract (ratio rho = max|D_k| / max|D_{k-1}| < 1/2) and the next one
 // would be below the tolerance: rho max|D_k| <= tol max|X|.  dprev: previous max|D|
 // slot (null for the first correction, which is the whole first solution).
-__global__ void k_refine_check(RefineState* rs, const unsigned long long* dmax, const unsigned long long* xmax,
-                               const unsigned long long* dprev, double tol, const Work wf) {
+// The check of one equation; err: the first error of its correction solve (0: none).
+__device__ __forceinline__ void refine_check_one(RefineState* rs, const unsigned long long* dmax,
+                                                 const unsigned long long* xmax, const unsigned long long* dprev,
+                                                 double tol, int e) {
   if (rs->conv) return;
   const double d = __longlong_as_double(static_cast<long long>(*dmax));
   const double x = __longlong_as_double(static_cast<long long>(*xmax));
   rs->iters += 1;
   rs->last = (x > 0.0) ? d / x : (d > 0.0 ? 1.0 : 0.0);
-  int e = wf.ctrl->err ? wf.ctrl->err : wf.st[0].err;
   bool conv = d <= tol * x;
   if (!conv && dprev) {
     const double dp = __longlong_as_double(static_cast<long long>(*dprev));
@@ -300,7 +301,12 @@ __global__ void k_refine_check(RefineState* rs, const unsigned long long* dmax, 
   }
 }
 
-__global__ void k_refine_result(const RefineState* rs, sylv_result* res, int maxit) {
+__global__ void k_refine_check(RefineState* rs, const unsigned long long* dmax, const unsigned long long* xmax,
+                               const unsigned long long* dprev, double tol, const Work wf) {
+  refine_check_one(rs, dmax, xmax, dprev, tol, wf.ctrl->err ? wf.ctrl->err : wf.st[0].err);
+}
+
+__device__ __forceinline__ void refine_result_one(const RefineState* rs, sylv_result* res) {
   sylv_result r;
   r.log2scale = 0;
   r.scale = 1.0;
@@ -311,6 +317,8 @@ __global__ void k_refine_result(const RefineState* rs, sylv_result* res, int max
   r.info = rs->err ? rs->err : (rs->conv ? SYLV_OK : SYLV_NOT_CONVERGED);
   *res = r;
 }
+
+__global__ void k_refine_result(const RefineState* rs, sylv_result* res, int maxit) { refine_result_one(rs, res); }
 
 // Y (m x n, ldy) <- X.
 __global__ void k_copy(const double* __restrict__ X, int64_t ldx, double* __restrict__ Y, int64_t ldy, int64_t m,
@@ -381,21 +389,19 @@ __device__ __forceinline__ void df_acc(float& s, float& comp, float ah, float al
 // kernel computes RS = C 2^-(sa+sx) - (AS XS + XS BS) = R 2^-(sa+sx) and stores
 // R = RS 2^(sa+sx) in binary64, plus max |R| in *rmax.  64 x 64 output tile per CTA,
 // 256 threads, 4 x 4 outputs each; k-chunks of 16 in shared memory.
-__global__ void __launch_bounds__(256) k_residual_df(const float* __restrict__ Ah, const float* __restrict__ Al,
-                                                     int64_t lda, const float* __restrict__ Bh,
-                                                     const float* __restrict__ Bl, int64_t ldb,
-                                                     const double* __restrict__ C, int64_t ldc,
-                                                     const double* __restrict__ X, int64_t ldx,
-                                                     double* __restrict__ R, int64_t ldr, int64_t m, int64_t n,
-                                                     const unsigned long long* slot_a,
-                                                     const unsigned long long* slot_b,
-                                                     const unsigned long long* slot_x, unsigned long long* rmax,
-                                                     const int* skip) {
-  if (skip && ld_volatile(skip)) return;
+// One 64 x 64 output tile (rows i0.., columns j0..) of k_residual_df.
+__device__ __forceinline__ void residual_df_tile(const float* __restrict__ Ah, const float* __restrict__ Al,
+                                                 int64_t lda, const float* __restrict__ Bh,
+                                                 const float* __restrict__ Bl, int64_t ldb,
+                                                 const double* __restrict__ C, int64_t ldc,
+                                                 const double* __restrict__ X, int64_t ldx,
+                                                 double* __restrict__ R, int64_t ldr, int64_t m, int64_t n,
+                                                 const unsigned long long* slot_a, const unsigned long long* slot_b,
+                                                 const unsigned long long* slot_x, unsigned long long* rmax,
+                                                 int64_t i0, int64_t j0) {
   constexpr int LD = GT + 4;  // float rows, 16-byte aligned
   __shared__ __align__(16) float Lh[GK * LD], Ll[GK * LD], Rh[GK * LD], Rl[GK * LD];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * GT, j0 = static_cast<int64_t>(blockIdx.y) * GT;
   const unsigned long long ua = *slot_a, ub = *slot_b;
   const int sa = norm_exp(ua > ub ? slot_a : slot_b);
   const int sx = norm_exp(slot_x);
@@ -488,6 +494,21 @@ __global__ void __launch_bounds__(256) k_residual_df(const float* __restrict__ A
     }
   mx = warp_max(mx);
   if ((tid & 31) == 0 && rmax) atomic_max_nonneg(rmax, mx);
+}
+
+__global__ void __launch_bounds__(256) k_residual_df(const float* __restrict__ Ah, const float* __restrict__ Al,
+                                                     int64_t lda, const float* __restrict__ Bh,
+                                                     const float* __restrict__ Bl, int64_t ldb,
+                                                     const double* __restrict__ C, int64_t ldc,
+                                                     const double* __restrict__ X, int64_t ldx,
+                                                     double* __restrict__ R, int64_t ldr, int64_t m, int64_t n,
+                                                     const unsigned long long* slot_a,
+                                                     const unsigned long long* slot_b,
+                                                     const unsigned long long* slot_x, unsigned long long* rmax,
+                                                     const int* skip) {
+  if (skip && ld_volatile(skip)) return;
+  residual_df_tile(Ah, Al, lda, Bh, Bl, ldb, C, ldc, X, ldx, R, ldr, m, n, slot_a, slot_b, slot_x, rmax,
+                   static_cast<int64_t>(blockIdx.x) * GT, static_cast<int64_t>(blockIdx.y) * GT);
 }
 
 // Float pair (hi, lo) of src * 2^-s, s from the larger of two max slots; quasi != 0
@@ -614,19 +635,18 @@ namespace sylv {
 // parts of the scaled pair (AS = A 2^-sa); D (binary64) scaled by 2^-sd into binary32
 // range; R_new = R - 2^(sa+sd) (AS DS + DS BS) with the final subtraction in
 // binary64.  Records max |R_new|.  64 x 64 outputs per CTA, 4 x 4 per thread.
-__global__ void __launch_bounds__(256) k_residual_update(const float* __restrict__ Ah, int64_t lda,
-                                                         const float* __restrict__ Bh, int64_t ldb,
-                                                         const double* __restrict__ D, int64_t ldd,
-                                                         double* __restrict__ R, int64_t ldr, int64_t m, int64_t n,
-                                                         const unsigned long long* slot_a,
-                                                         const unsigned long long* slot_b,
-                                                         const unsigned long long* slot_d, unsigned long long* rmax,
-                                                         const int* skip) {
-  if (skip && ld_volatile(skip)) return;
+// One 64 x 64 output tile (rows i0.., columns j0..) of k_residual_update.
+__device__ __forceinline__ void residual_update_tile(const float* __restrict__ Ah, int64_t lda,
+                                                     const float* __restrict__ Bh, int64_t ldb,
+                                                     const double* __restrict__ D, int64_t ldd,
+                                                     double* __restrict__ R, int64_t ldr, int64_t m, int64_t n,
+                                                     const unsigned long long* slot_a,
+                                                     const unsigned long long* slot_b,
+                                                     const unsigned long long* slot_d, unsigned long long* rmax,
+                                                     int64_t i0, int64_t j0) {
   constexpr int LD = GT + 4;
   __shared__ __align__(16) float Ls[GK * LD], Rs[GK * LD];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * GT, j0 = static_cast<int64_t>(blockIdx.y) * GT;
   const unsigned long long ua = *slot_a, ub = *slot_b;
   const int sa = norm_exp(ua > ub ? slot_a : slot_b);
   const int sd = norm_exp(slot_d);
@@ -697,6 +717,19 @@ __global__ void __launch_bounds__(256) k_residual_update(const float* __restrict
     }
   mx = warp_max(mx);
   if ((tid & 31) == 0 && rmax) atomic_max_nonneg(rmax, mx);
+}
+
+__global__ void __launch_bounds__(256) k_residual_update(const float* __restrict__ Ah, int64_t lda,
+                                                         const float* __restrict__ Bh, int64_t ldb,
+                                                         const double* __restrict__ D, int64_t ldd,
+                                                         double* __restrict__ R, int64_t ldr, int64_t m, int64_t n,
+                                                         const unsigned long long* slot_a,
+                                                         const unsigned long long* slot_b,
+                                                         const unsigned long long* slot_d, unsigned long long* rmax,
+                                                         const int* skip) {
+  if (skip && ld_volatile(skip)) return;
+  residual_update_tile(Ah, lda, Bh, ldb, D, ldd, R, ldr, m, n, slot_a, slot_b, slot_d, rmax,
+                       static_cast<int64_t>(blockIdx.x) * GT, static_cast<int64_t>(blockIdx.y) * GT);
 }
 
 }  // namespace sylv

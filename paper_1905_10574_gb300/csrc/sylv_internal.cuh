@@ -79,6 +79,10 @@ struct Work {
   double* dbuf;     // off-diagonal tile norms of A and B
   sylv_result* res; // per-equation results
   const int* skip;  // if non-null and nonzero, the DAG kernel returns at once
+  // Per-equation skip (batched refinement): if non-null, the tasks of equation e are
+  // skipped (their tiles only marked final) while eqskip[e * eqskip_stride] != 0.
+  const int* eqskip;
+  int32_t eqskip_stride;
   double* fact;     // per-CTA store of factored small systems (fact_stride doubles each)
   int32_t* factp;   // per-CTA packed pivot data (TT*TT ints each)
   int64_t fact_stride;

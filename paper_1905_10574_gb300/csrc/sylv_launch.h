@@ -47,5 +47,13 @@ cudaError_t oz_split_ab(const OzBuffers& b, const double* A, int64_t lda, const 
 cudaError_t oz_residual(const OzBuffers& b, const double* X, int64_t ldx, const double* C, int64_t ldc, double* R,
                         int64_t ldr, unsigned long long* rmax, int* err, long long timeout_ns, const int* skip,
                         cudaStream_t s, bool binary64);
+// Dense product on the same tensor-core kernel, binary64-accurate (error-free
+// splitting): R -= L Q^T for L (mo x k, element (r, c) at L[r lrs + c lks]) and Q
+// (no x k, element (j, c) at Q[j qrs + c qks]); R is mo x no with leading dimension
+// ldr.  buf: oz_dense_bytes(mo, no, k') bytes for any k' >= k; a timeout sets *err.
+size_t oz_dense_bytes(int64_t mo, int64_t no, int64_t kmax);
+cudaError_t oz_product(char* buf, const double* L, int64_t lrs, int64_t lks, const double* Q, int64_t qrs,
+                       int64_t qks, int64_t mo, int64_t no, int64_t k, double* R, int64_t ldr, int* err,
+                       long long timeout_ns, cudaStream_t s);
 
 }  // namespace sylv

@@ -84,11 +84,51 @@ cudaError_t oz_residual(const OzBuffers& b, const double* X, int64_t ldx, const 
   g.b[0] = packed(b, 1);
   g.a[1] = packed(b, 2);
   g.b[1] = packed(b, 3);
+  g.dense = 0;
   auto kern = binary64 ? oz::k_oz_gemm<oz::kMaxW> : oz::k_oz_gemm<oz::kMaxW32>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sizeof(oz::Smem)));
   if (e != cudaSuccess) return e;
   const dim3 grid(static_cast<unsigned>(cdiv(m, oz::BM)), static_cast<unsigned>(cdiv(n, oz::BN)));
   kern<<<grid, oz::kThreads, sizeof(oz::Smem), s>>>(g, C, ldc, R, ldr, m, n, rmax, err, timeout_ns, skip);
+  return cudaGetLastError();
+}
+
+// ---- dense products (the Bartels-Stewart transformations)
+namespace {
+oz::Packed dense_left(int64_t rows, int64_t k) { return {nullptr, nullptr, cdiv(rows, oz::BM), cdiv(k, oz::BK), oz::BM}; }
+oz::Packed dense_right(int64_t rows, int64_t k) { return {nullptr, nullptr, cdiv(rows, oz::BN), cdiv(k, oz::BK), oz::BN}; }
+size_t packed_bytes(const oz::Packed& P) {
+  return up256(sizeof(__nv_bfloat16) * oz::kSlices * P.slice_elems()) + up256(sizeof(int) * P.RB * P.R);
+}
+}  // namespace
+
+size_t oz_dense_bytes(int64_t mo, int64_t no, int64_t kmax) {
+  return packed_bytes(dense_left(mo, kmax)) + packed_bytes(dense_right(no, kmax));
+}
+
+cudaError_t oz_product(char* buf, const double* L, int64_t lrs, int64_t lks, const double* Q, int64_t qrs,
+                       int64_t qks, int64_t mo, int64_t no, int64_t k, double* R, int64_t ldr, int* err,
+                       long long timeout_ns, cudaStream_t s) {
+  oz::Packed pl = dense_left(mo, k), pr = dense_right(no, k);
+  pl.p = reinterpret_cast<__nv_bfloat16*>(buf);
+  pl.e = reinterpret_cast<int*>(buf + up256(sizeof(__nv_bfloat16) * oz::kSlices * pl.slice_elems()));
+  char* rb = buf + packed_bytes(pl);
+  pr.p = reinterpret_cast<__nv_bfloat16*>(rb);
+  pr.e = reinterpret_cast<int*>(rb + up256(sizeof(__nv_bfloat16) * oz::kSlices * pr.slice_elems()));
+  const oz::View vl{L, lrs, lks, mo, k, 0};
+  const oz::View vq{Q, qrs, qks, no, k, 0};
+  cudaError_t e = split(vl, pl, nullptr, s);
+  if (e == cudaSuccess) e = split(vq, pr, nullptr, s);
+  if (e != cudaSuccess) return e;
+  oz::Gemm g;
+  g.a[0] = g.a[1] = pl;
+  g.b[0] = g.b[1] = pr;
+  g.dense = 1;
+  auto kern = oz::k_oz_gemm<oz::kMaxW>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sizeof(oz::Smem)));
+  if (e != cudaSuccess) return e;
+  const dim3 grid(static_cast<unsigned>(cdiv(mo, oz::BM)), static_cast<unsigned>(cdiv(no, oz::BN)));
+  kern<<<grid, oz::kThreads, sizeof(oz::Smem), s>>>(g, R, ldr, R, ldr, mo, no, nullptr, err, timeout_ns, nullptr);
   return cudaGetLastError();
 }
 

@@ -270,12 +270,17 @@ constexpr int kGroupRows = 8;
 struct Gemm {
   Packed a[2];
   Packed b[2];
+  int dense;  // 1: one unstructured product a[0] b[0]^T over all of K (b[1] unused)
 };
 
 // K blocks of product p for output rows [i0, i0+128) and columns [j0, j0+64): A X
-// reads A[i, k] for k >= i - 1; X B reads B[k, j] for k <= j + 1.
+// reads A[i, k] for k >= i - 1; X B reads B[k, j] for k <= j + 1.  A dense product
+// reads every K block, and there is no second product.
 __device__ __forceinline__ void kb_range(int p, const Gemm& g, int64_t i0, int64_t j0, int& lo, int& hi) {
-  if (p == 0) {
+  if (g.dense) {
+    lo = 0;
+    hi = p == 0 ? static_cast<int>(g.a[0].KB) : 0;
+  } else if (p == 0) {
     lo = i0 > 0 ? static_cast<int>((i0 - 1) / BK) : 0;
     hi = static_cast<int>(g.a[0].KB);
   } else {
@@ -493,6 +498,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int p = 0; p < 2 && ok; ++p) {
       int lo, hi;
       kb_range(p, g, i0, j0, lo, hi);
+      if (hi <= lo) continue;  // no second product (dense form): nothing committed, nothing to drain
       const int erow = g.a[p].e[gi];
       const int nst = hi - lo;
       const int nlead = (nst - 1) / kLeadStages;  // drains of the leading weights before the last

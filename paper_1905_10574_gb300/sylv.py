@@ -67,6 +67,7 @@ SIGNATURES = {
     "sylv_tri_solve_ex": (ctypes.c_int, [_i64, _i64, _pd, _i64, _pd, _i64, _pd, _i64,
                                          ctypes.POINTER(sylv_opts), _vp]),
     "sylv_workspace_size": (ctypes.c_size_t, [_i64, _i64, ctypes.POINTER(sylv_opts)]),
+    "sylv_schur_workspace_size": (ctypes.c_size_t, [_i64, _i64, ctypes.POINTER(sylv_opts)]),
     "sylv_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _i32, _P64, _P64, _PP, _P64, _PP,
                                          _P64, _PP, _P64, ctypes.POINTER(sylv_opts)]),
     "sylv_batch_create_tiles": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _i32, _P64, _P64, _PP, _P64, _PP,
@@ -436,16 +437,18 @@ def residual(A, B, X, C, *, stream=None):
     return R
 
 
-def batch_solve(As, Bs, Cs, *, transa=False, transb=False, tile=0, precision="fp64", timeout_ms=0, isgn=1):
+def batch_solve(As, Bs, Cs, *, transa=False, transb=False, tile=0, precision="fp64", timeout_ms=0, isgn=1,
+                tol=0.0, maxit=0):
     """Solve a list of equations op(A_i) Y_i + Y_i op(B_i) = alpha_i C_i in one batched
     launch; Cs are overwritten when they are column-major float64 CUDA tensors, else
-    copies are solved.  Returns (Ys, [Result])."""
+    copies are solved.  precision "fp32_refine" refines every equation to tol (0: the
+    library default).  Returns (Ys, [Result])."""
     torch = _torch()
     As = [fortran(a) for a in As]
     Bs = [fortran(b) for b in Bs]
     Ys = [fortran(c) for c in Cs]
     o = make_opts(transa=transa, transb=transb, tile=tile, precision=precision, timeout_ms=timeout_ms,
-                  stream=torch.cuda.current_stream().cuda_stream, isgn=isgn)
+                  stream=torch.cuda.current_stream().cuda_stream, isgn=isgn, tol=tol, maxit=maxit)
     plan = sylv_batch_create([y.shape[0] for y in Ys], [y.shape[1] for y in Ys], [a.data_ptr() for a in As],
                              [_ld(a) for a in As], [b.data_ptr() for b in Bs], [_ld(b) for b in Bs],
                              [y.data_ptr() for y in Ys], [_ld(y) for y in Ys], o)

@@ -66,3 +66,16 @@ def test_workspace_size_monotone(lib):
     o.precision = sylv.SYLV_FP32_REFINE
     assert sylv.sylv_workspace_size(256, 256, o) > a
     assert sylv.sylv_workspace_size(0, 5, o) == 0
+
+
+def test_library_links_no_blas(lib):
+    """Every product on the solver's path runs in the library's own kernels: the
+    shared library needs no BLAS library (its dynamic section lists none)."""
+    import shutil
+    import subprocess
+    from paper_1905_10574_gb300 import build
+    if not shutil.which("readelf"):
+        pytest.skip("readelf not available")
+    out = subprocess.run(["readelf", "-d", build.LIB], capture_output=True, text=True, check=True).stdout
+    needed = [ln for ln in out.splitlines() if "NEEDED" in ln]
+    assert needed and not any("blas" in ln.lower() for ln in needed), needed

@@ -93,15 +93,23 @@ def test_mixed_full_size(orc, sy, name, tol):
     assert _rel(Y, Y64) <= REFINE_TOL
 
 
-def test_batched_4096_sampled(orc, sy):
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_batched_4096_sampled(orc, sy, precision):
+    """The 4096-equation batch as the benchmark runs it, in FP64 and in FP32 +
+    refinement at the benchmark's stop tolerance (2^-41): 24 sampled equations
+    against the oracle (FP64 1e-13, refined 1e-12) and their eq. (9) residuals."""
     shapes = inputs.batch_shapes(4096, 16, 512, seed=1234)
     probs = [inputs.problem(m, n, 10000 + i, kind="wellcond") for i, (m, n) in enumerate(shapes)]
     As = [torch.from_numpy(p[0]).cuda() for p in probs]
     Bs = [torch.from_numpy(p[1]).cuda() for p in probs]
     Cs = [torch.from_numpy(p[2]).cuda() for p in probs]
-    Ys, res = sy.batch_solve(As, Bs, Cs)
+    refine = precision == "fp32_refine"
+    Ys, res = sy.batch_solve(As, Bs, Cs, precision=precision, tol=2.0 ** -41 if refine else 0.0)
     torch.cuda.synchronize()
     assert all(r.info == 0 for r in res)
+    if refine:
+        assert all(r.iters >= 2 and r.last_update <= 2.0 ** -41 for r in res)
+    tol = REFINE_TOL if refine else FWD_TOL
     rng = np.random.default_rng(0)
     for i in rng.choice(len(probs), size=24, replace=False):
         A, B, C = probs[i]
@@ -109,7 +117,7 @@ def test_batched_4096_sampled(orc, sy):
         assert np.all(np.isfinite(Yh))
         ref = orc.trsyl(A, B, C)
         assert orc.residual(A, B, Yh, C, res[i].log2scale) <= RESID_TOL
-        assert _rel(np.ldexp(Yh, int(ref["log2scale"]) - int(res[i].log2scale)), ref["Y"]) <= FWD_TOL
+        assert _rel(np.ldexp(Yh, int(ref["log2scale"]) - int(res[i].log2scale)), ref["Y"]) <= tol
 
 
 def test_lyapunov_adjoint_256x512_sampled(orc, sy):

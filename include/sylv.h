@@ -367,10 +367,10 @@ int sylv_diag_guards(int64_t count, const double* c, const double* t, const doub
  * sylv_diag_fma_rate -- measures the peak rate of the FMA pipe that bounds the
  * solver's tile kernels (not in the paper): kind 0 = binary64 FMA (the FP64 solve),
  * 1 = binary32 FMA (the FP32 correction solves).  One launch of one full wave of
- * 256-thread CTAs (as many per SM as fit), each thread running 8 independent FMA
- * chains for `iters` rounds, timed
- * with CUDA events on `stream` after a warm-up launch; *gflops receives
- * 16 x iters x threads / time (two flops per FMA), *ms (may be NULL) the time.
+ * 256-thread CTAs (as many per SM as fit), each thread running 8 (binary64) or 16
+ * (binary32) independent FMA chains for `iters` rounds, timed with CUDA events on
+ * `stream` after a warm-up launch; *gflops receives 2 x chains x iters x threads /
+ * time (two flops per FMA), *ms (may be NULL) the time.
  * Allocates 16 bytes and synchronizes `stream`.  Returns SYLV_OK, -1 (kind), -2
  * (iters outside [1, 2^32 - 1]), -3 (gflops NULL) or SYLV_ERR_CUDA.
  */

@@ -262,26 +262,27 @@ __global__ void k_guards(int64_t count, const double* c, const double* t, const 
   zd[i] = protect_division(b[i], d[i], omega);
 }
 
-// Peak-rate probe of the FMA pipes: each thread runs 8 independent FMA chains for
-// `iters` rounds (16 flops per round and thread); the sum is stored only if it
+// Peak-rate probe of the FMA pipes: each thread runs NC independent FMA chains for
+// `iters` rounds (2 NC flops per round and thread); the sum is stored only if it
 // matches an impossible value, so the compiler keeps every FMA.
-template <typename T>
-__global__ void __launch_bounds__(256, 8) k_fma_loop(int64_t iters, T seed, T* sink) {
-  T a[8];
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_fma_loop(int64_t iters, T seed, T* sink) {
+  T a[NC];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) a[k] = seed + static_cast<T>(threadIdx.x + k);
+  for (int k = 0; k < NC; ++k) a[k] = seed + static_cast<T>(threadIdx.x + k);
   const T b = static_cast<T>(0.999999), c = static_cast<T>(1e-7);
   const unsigned n = static_cast<unsigned>(iters);
 #pragma unroll 4
   for (unsigned i = 0; i < n; ++i) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+    for (int k = 0; k < NC; ++k) a[k] = fma(a[k], b, c);
   }
   T s = 0;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) s += a[k];
+  for (int k = 0; k < NC; ++k) s += a[k];
   if (s == static_cast<T>(-12345.0)) *sink = s;
 }
+constexpr int kFmaChains64 = 8, kFmaChains32 = 16;  // binary32 needs more chains to fill its pipe
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? SYLV_OK : SYLV_ERR_CUDA; }
 
@@ -783,8 +784,8 @@ int sylv_diag_fma_rate(int32_t kind, int64_t iters, double* gflops, double* ms, 
   // second wave would leave SMs idle and understate the rate).
   int per_sm = 0;
   const cudaError_t oe = kind == 0
-                             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_loop<double>, 256, 0)
-                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_loop<float>, 256, 0);
+                             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_loop<double, kFmaChains64>, 256, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_loop<float, kFmaChains32>, 256, 0);
   if (oe != cudaSuccess || per_sm <= 0) return SYLV_ERR_CUDA;
   const int blocks = sm_count() * per_sm;
   void* sink = nullptr;
@@ -799,9 +800,9 @@ int sylv_diag_fma_rate(int32_t kind, int64_t iters, double* gflops, double* ms, 
   if (!rc) {
     auto launch = [&](int64_t it) {
       if (kind == 0)
-        k_fma_loop<double><<<blocks, 256, 0, s>>>(it, 1.0, static_cast<double*>(sink));
+        k_fma_loop<double, kFmaChains64><<<blocks, 256, 0, s>>>(it, 1.0, static_cast<double*>(sink));
       else
-        k_fma_loop<float><<<blocks, 256, 0, s>>>(it, 1.0f, static_cast<float*>(sink));
+        k_fma_loop<float, kFmaChains32><<<blocks, 256, 0, s>>>(it, 1.0f, static_cast<float*>(sink));
     };
     launch(std::max<int64_t>(iters / 8, 1));  // warm-up (clocks up, code loaded)
     cudaEventRecord(e0, s);
@@ -812,7 +813,7 @@ int sylv_diag_fma_rate(int32_t kind, int64_t iters, double* gflops, double* ms, 
         cudaEventElapsedTime(&t, e0, e1) != cudaSuccess || t <= 0.0f) {
       rc = SYLV_ERR_CUDA;
     } else {
-      const double flops = 16.0 * static_cast<double>(iters) * blocks * 256.0;
+      const double flops = 2.0 * (kind == 0 ? kFmaChains64 : kFmaChains32) * static_cast<double>(iters) * blocks * 256.0;
       *gflops = flops / (t * 1e-3) / 1e9;
       if (ms) *ms = t;
     }

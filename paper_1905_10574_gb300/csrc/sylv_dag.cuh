@@ -1614,31 +1614,31 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
             sh.goff[lane] = packed ? lane * TT : ko - kdim;
           }
           if (packed) {
-            // One thread stages the whole group by bulk copies (async proxy) after
-            // every lane's flag acquire (__syncwarp orders them before the copies).
-            __syncwarp();
-            if (lane == 0) {
-              asm volatile("fence.proxy.async.global;" ::: "memory");
-              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the last GEMM's reads
-              const uint32_t bytes = static_cast<uint32_t>(w.pack_slot);
-              const uint32_t bar = smem_addr(&sh.stage_bar);
+            // The group is staged by bulk copies (async proxy): lane 0 sets the
+            // transaction count, then every member's lane issues its own two copies,
+            // after its own flag acquire and proxy fences, so the issue runs in
+            // parallel instead of 2g copies in a row on one lane.
+            const uint32_t bytes = static_cast<uint32_t>(w.pack_slot);
+            const uint32_t bar = smem_addr(&sh.stage_bar);
+            if (lane == 0)
               asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2u * g * bytes)
                            : "memory");
-              for (int u = 0; u < g; ++u) {
-                const int pu = sh.gprod[u];
-                int64_t sl, sr;
-                if (sh.gside[u] == 0) {  // A_ki and Y_il
-                  const int i = pu / I.qmax;
-                  sl = pack_a(I, k, i);
-                  sr = pack_yr(I, i, l);
-                } else {  // Y_kj and B_jl
-                  const int j = pu % I.qmax;
-                  sl = pack_yl(I, k, j);
-                  sr = pack_b(I, j, l);
-                }
-                bulk_copy_g2s(sh.L + u * TT * DagSmem<TT, T>::LDG, w.pack + sl * w.pack_slot, bytes, bar);
-                bulk_copy_g2s(sh.R + u * TT * DagSmem<TT, T>::LDG, w.pack + sr * w.pack_slot, bytes, bar);
+            __syncwarp();
+            if (lane < g) {
+              asm volatile("fence.proxy.async.global;" ::: "memory");
+              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the last GEMM's reads
+              int64_t sl, sr;
+              if (side == 0) {  // A_ki and Y_il
+                const int i = prod / I.qmax;
+                sl = pack_a(I, k, i);
+                sr = pack_yr(I, i, l);
+              } else {  // Y_kj and B_jl
+                const int j = prod % I.qmax;
+                sl = pack_yl(I, k, j);
+                sr = pack_b(I, j, l);
               }
+              bulk_copy_g2s(sh.L + lane * TT * DagSmem<TT, T>::LDG, w.pack + sl * w.pack_slot, bytes, bar);
+              bulk_copy_g2s(sh.R + lane * TT * DagSmem<TT, T>::LDG, w.pack + sr * w.pack_slot, bytes, bar);
             }
           }
           if (lane == 0) {

@@ -931,42 +931,50 @@ def run_robust_vs_plain(args):
 
 
 def run_small(args):
-    """m = n = 256, tile 64 (benign, seed 0): a latency-bound solve of 4 x 4 tiles with
-    a 7-level critical path; microseconds per solve and solves/s, one call per solve on
-    one stream (each call enqueues the whole launch sequence)."""
+    """m = n = 256 (benign, seed 0): a latency-bound solve with a short critical path of
+    diagonal-tile solves; microseconds per solve and solves/s, one call per solve on
+    one stream (each call enqueues the whole launch sequence).  The value is at the
+    configuration's tile 64; tiles 32, 24 and 16 are timed beside it."""
     import torch
     from paper_1905_10574_gb300 import build, inputs, sylv
     build.build()
     name = args.workload or "benign_256"
     A, B, C, w = inputs.workload(name)
-    m, n, tile = w["m"], w["n"], args.tile or w["tile"]
+    m, n = w["m"], w["n"]
     dev = torch.device("cuda", 0)
     Ad, Bd, C0 = (torch.from_numpy(x).to(dev) for x in (A, B, C))
     stream = torch.cuda.current_stream(dev)
-    opts = sylv.make_opts(tile=tile, stream=stream.cuda_stream, sync=False)
-    wsb = sylv.sylv_workspace_size(m, n, opts)
-    wsbuf = torch.empty(wsb + 256, dtype=torch.uint8, device=dev)
-    opts.workspace = (wsbuf.data_ptr() + 255) // 256 * 256
-    opts.workspace_bytes = wsb
     reps = 50
-    Cs = [C0.clone() for _ in range(reps * (args.warmup + args.steps))]
     rdev = torch.zeros(64, dtype=torch.uint8, device=dev)
+    by_tile = {}
+    tiles = [args.tile or w["tile"]] + [t for t in (32, 24, 16) if t != (args.tile or w["tile"])]
+    for tile in tiles:
+        opts = sylv.make_opts(tile=tile, stream=stream.cuda_stream, sync=False)
+        wsb = sylv.sylv_workspace_size(m, n, opts)
+        wsbuf = torch.empty(wsb + 256, dtype=torch.uint8, device=dev)
+        opts.workspace = (wsbuf.data_ptr() + 255) // 256 * 256
+        opts.workspace_bytes = wsb
+        Cs = [C0.clone() for _ in range(reps * (args.warmup + args.steps))]
 
-    def fn(i):
-        for j in range(reps):
-            c = Cs[i * reps + j]
-            rc = sylv.sylv_tri_solve_ex(m, n, Ad.data_ptr(), Ad.stride(1), Bd.data_ptr(), Bd.stride(1), c.data_ptr(),
-                                        c.stride(1), opts, rdev.data_ptr())
-            if rc != 0:
-                raise sylv.SylvError(rc, "small")
+        def fn(i, opts=opts, Cs=Cs):
+            for j in range(reps):
+                c = Cs[i * reps + j]
+                rc = sylv.sylv_tri_solve_ex(m, n, Ad.data_ptr(), Ad.stride(1), Bd.data_ptr(), Bd.stride(1),
+                                            c.data_ptr(), c.stride(1), opts, rdev.data_ptr())
+                if rc != 0:
+                    raise sylv.SylvError(rc, "small")
 
-    ms, _ = _timed(fn, args.steps, args.warmup, stream)
-    res = sylv.sylv_result.from_buffer_copy(rdev[:40].cpu().numpy().tobytes())
-    us = 1000.0 * ms / reps
-    return {"metric": "solves/s", "value": 1e6 / us, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "m": m, "n": n, "tile": tile, "solves_per_step": reps},
-            "us_per_solve": us, "gflops_2mnmn": flops_2(m, n) / us / 1e3, "info": int(res.info)}
+        ms, _ = _timed(fn, args.steps, args.warmup, stream)
+        res = sylv.sylv_result.from_buffer_copy(rdev[:40].cpu().numpy().tobytes())
+        us = 1000.0 * ms / reps
+        by_tile[str(tile)] = {"us_per_solve": us, "solves_per_s": 1e6 / us, "info": int(res.info)}
+        del Cs, wsbuf
+    t0 = str(tiles[0])
+    return {"metric": "solves/s", "value": by_tile[t0]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "m": m, "n": n, "tile": tiles[0], "solves_per_step": reps},
+            "us_per_solve": by_tile[t0]["us_per_solve"], "gflops_2mnmn": flops_2(m, n) / by_tile[t0]["us_per_solve"] / 1e3,
+            "by_tile": by_tile}
 
 
 def run_peaks(args):

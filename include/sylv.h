@@ -73,7 +73,8 @@ typedef struct sylv_opts {
   int32_t precision;       /* SYLV_FP64, SYLV_FP64_NONROBUST or SYLV_FP32_REFINE */
   int32_t tile;            /* nominal tile size t (Sec. 2.2); 0 = automatic.  Tiles
                               hold t or t-1 rows so that no 2x2 block is split */
-  double omega;            /* overflow threshold Omega; 0 = 2^1020 (2^124 for binary32) */
+  double omega;            /* overflow threshold Omega; 0 = 2^1020 (2^124 for binary32); the binary32
+                              correction solves of SYLV_FP32_REFINE use min(omega, 2^124) */
   double tol;              /* refinement: stop when max|dY| <= tol * max|Y|, or when the
                               corrections contract and the next one is predicted that small;
                               0 = 2^-43 */

@@ -134,7 +134,7 @@ Layout make_layout_seq(const Seq& sh, size_t base, int cta_cap, int per_sm = 2, 
   L.lvl_cur = o;
   o = align_up(o + nlev * sizeof(int32_t));
   L.tflag = o;
-  o = align_up(o + tiles * sizeof(int32_t));
+  o = align_up(o + tiles * sizeof(unsigned long long));
   L.smbusy = o;
   o = align_up(o + 1024 * sizeof(int32_t));
   L.zero_hi = o;
@@ -229,7 +229,7 @@ Work make_work(char* ws, const Layout& L, int count, int64_t timeout_ns) {
   w.lvl_cur = reinterpret_cast<int32_t*>(ws + L.lvl_cur);
   w.ibuf = reinterpret_cast<int32_t*>(ws + L.ibuf);
   w.texp = reinterpret_cast<int32_t*>(ws + L.texp);
-  w.tflag = reinterpret_cast<int32_t*>(ws + L.tflag);
+  w.tflag = reinterpret_cast<unsigned long long*>(ws + L.tflag);
   w.tnorm = reinterpret_cast<double*>(ws + L.tnorm);
   w.dbuf = reinterpret_cast<double*>(ws + L.dbuf);
   w.res = reinterpret_cast<sylv_result*>(ws + L.res);
@@ -392,6 +392,7 @@ int read_opts(const sylv_opts* o, Opts* out) {
   out->maxit = o->maxit > 0 ? o->maxit : 6;
   out->sync = o->sync;
   out->omega = o->omega > 0 ? o->omega : (o->precision == SYLV_FP32_REFINE ? 0x1p124 : 0x1p1020);
+  if (o->precision == SYLV_FP32_REFINE && out->omega > 0x1p124) out->omega = 0x1p124;  // binary32 tiles
   out->tol = o->tol > 0 ? o->tol : 0x1p-43;  // ~1.1e-13: a 9x margin under a 1e-12 forward-error target
   out->timeout_ns = (o->timeout_ms > 0 ? o->timeout_ms : 20000) * 1000000LL;
   out->stream = static_cast<cudaStream_t>(o->stream);
@@ -591,7 +592,7 @@ int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, c
     }
     k_to_float<<<grid_for(m * n), 256, 0, s>>>(R, m, Rf, m, m, n, rmax, nullptr, 0, &rs->conv);
     if (it > 0) {
-      if (cudaMemsetAsync(w.tflag, 0, sizeof(int32_t) * L.sum_tiles, s) != cudaSuccess) return SYLV_ERR_CUDA;
+      if (cudaMemsetAsync(w.tflag, 0, sizeof(unsigned long long) * L.sum_tiles, s) != cudaSuccess) return SYLV_ERR_CUDA;
       if (cudaMemsetAsync(&w.ctrl->ticket, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return SYLV_ERR_CUDA;
     }
     e = launch_dag_f32(P.shape.t, w, std::min(L.max_tiles, L.ncta), s, o.max_sms);
@@ -1253,7 +1254,7 @@ static int execute_refine(sylv_batch_plan* P, cudaStream_t s) {
       k_bref_residual<<<dim3(nt64, nt64, count), 256, 0, s>>>(P->dref, it);
     k_bref_to_float<<<dim3(eg, count), 256, 0, s>>>(P->dref, it);
     if (it > 0) {
-      if (cudaMemsetAsync(P->w.tflag, 0, sizeof(int32_t) * L.sum_tiles, s) != cudaSuccess) return SYLV_ERR_CUDA;
+      if (cudaMemsetAsync(P->w.tflag, 0, sizeof(unsigned long long) * L.sum_tiles, s) != cudaSuccess) return SYLV_ERR_CUDA;
       if (cudaMemsetAsync(&P->w.ctrl->ticket, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return SYLV_ERR_CUDA;
     }
     e = launch_dag_f32(P->tt, P->w, ntasks, s, P->max_sms);

@@ -1384,7 +1384,7 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
         // final (every consumer belongs to the same equation and skips as well).
         const Task t0 = w.tasks[sh.task];
         if (ld_volatile(w.eqskip + static_cast<int64_t>(t0.inst) * w.eqskip_stride)) {
-          st_release(w.tflag + w.inst[t0.inst].tile + t0.tile, 1);
+          st_release64(w.tflag + w.inst[t0.inst].tile + t0.tile, tile_word(0, 0.0));
           sh.skipt = 1;
         }
       }
@@ -1411,7 +1411,7 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
     const double* an = w.dbuf + I.an;
     const double* bn = w.dbuf + I.bn;
     int32_t* texp = w.texp + I.tile;
-    int32_t* tflag = w.tflag + I.tile;
+    unsigned long long* tflag = w.tflag + I.tile;
     double* tnorm = w.tnorm + I.tile;
 
     double* fact = w.fact + static_cast<int64_t>(blockIdx.x) * w.fact_stride;
@@ -1522,11 +1522,11 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
         int side = 0, prod = 0, kdim = 0;
         const bool cand = lane < G && q + lane < d;
         if (cand) producer(q + lane, side, prod, kdim);
-        int fl = cand ? ld_acquire(&tflag[prod]) : 0;
+        unsigned long long fl = cand ? ld_acquire64(&tflag[prod]) : 0ull;
         double on = 0.0;
         if (ROBUST && cand) on = opnorm(side, prod);
         int okw = 1;
-        if (lane == 0 && !fl) okw = wait_flag(&tflag[prod], ctrl, w.timeout_ns) ? 1 : 0;
+        if (lane == 0 && !fl) okw = wait_word(&tflag[prod], ctrl, w.timeout_ns, &fl) ? 1 : 0;
         okw = __shfl_sync(0xffffffffu, okw, 0);
         if (!okw) {
           if (lane == 0) sh.abort = 1;
@@ -1537,9 +1537,9 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
           int fast = 1;
           int ep = 0;
           double pn = 0.0;
-          if (ROBUST && lane < g) {
-            ep = texp[prod];
-            pn = tnorm[prod];
+          if (ROBUST && lane < g) {  // from the ready word: no second round trip
+            ep = word_exp(fl);
+            pn = word_norm(fl);
           }
           if (lane >= g) on = 0.0;
           int gsacc = 0;
@@ -1876,7 +1876,7 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
       texp[task.tile] = e;
       tnorm[task.tile] = nrm;
       __threadfence();
-      st_release(&tflag[task.tile], 1);
+      st_release64(&tflag[task.tile], tile_word(e, nrm));
       // The equation's status words are read only after the kernel, so their atomics
       // follow the release instead of delaying it.
       int fl = sh.flags;

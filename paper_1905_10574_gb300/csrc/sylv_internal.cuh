@@ -74,7 +74,11 @@ struct Work {
   int32_t* lvl_cur;
   int32_t* ibuf;    // tile boundaries
   int32_t* texp;    // local exponent per tile
-  int32_t* tflag;   // 1 once a tile is final (release/acquire)
+  // Ready word of each tile, 0 until the tile is final (release/acquire): bit 63 set,
+  // bits 62..32 the high word of its infinity norm rounded up (an upper bound of the
+  // norm with a 20-bit significand), bits 31..0 its exponent, so a consumer learns
+  // readiness, exponent and norm bound from one load.
+  unsigned long long* tflag;
   double* tnorm;    // infinity norm of each final tile (as stored, i.e. scaled)
   double* dbuf;     // off-diagonal tile norms of A and B
   sylv_result* res; // per-equation results
@@ -239,6 +243,26 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 __device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
 
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// The ready word of a final tile (see Work::tflag) and its two fields.
+__device__ __forceinline__ unsigned long long tile_word(int e, double nrm) {
+  unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(nrm)) & 0x7FFFFFFFFFFFFFFFull;
+  unsigned long long hi = b >> 32;
+  if ((b & 0xFFFFFFFFull) && hi < 0x7FF00000ull) ++hi;  // round the kept high word up
+  return (1ull << 63) | ((hi & 0x7FFFFFFFull) << 32) | static_cast<uint32_t>(e);
+}
+__device__ __forceinline__ int word_exp(unsigned long long w) { return static_cast<int>(static_cast<uint32_t>(w)); }
+__device__ __forceinline__ double word_norm(unsigned long long w) {
+  return __longlong_as_double(static_cast<long long>(((w >> 32) & 0x7FFFFFFFull) << 32));
+}
+
 // Wait (thread-level) until *flag != 0.  Bounded: gives up after timeout_ns of
 // global time or as soon as another CTA has recorded a launch-wide error, and
 // then records SYLV_ERR_TIMEOUT (first error wins) and returns false.
@@ -250,6 +274,24 @@ __device__ __forceinline__ bool wait_flag(const int* flag, Ctrl* ctrl, long long
     __nanosleep(ns);
     if (ns < 512) ns <<= 1;
     if (ld_acquire(flag)) return true;
+    if (ld_volatile(&ctrl->err)) return false;
+    if (static_cast<long long>(global_ns() - t0) > timeout_ns) {
+      atomicCAS(&ctrl->err, 0, SYLV_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+// The same wait on a tile's 64-bit ready word; *word receives it.
+__device__ __forceinline__ bool wait_word(const unsigned long long* flag, Ctrl* ctrl, long long timeout_ns,
+                                          unsigned long long* word) {
+  if ((*word = ld_acquire64(flag)) != 0) return true;
+  const unsigned long long t0 = global_ns();
+  unsigned ns = 32;
+  for (;;) {
+    __nanosleep(ns);
+    if (ns < 512) ns <<= 1;
+    if ((*word = ld_acquire64(flag)) != 0) return true;
     if (ld_volatile(&ctrl->err)) return false;
     if (static_cast<long long>(global_ns() - t0) > timeout_ns) {
       atomicCAS(&ctrl->err, 0, SYLV_ERR_TIMEOUT);

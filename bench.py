@@ -60,19 +60,22 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--tile", type=int, default=0, help="override the workload's tile size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--count", type=int, default=1024, help="batch mode: equations in the batch")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_refine"], help="batch mode: precision")
     ap.add_argument("--sms", default="", help="smscale mode: comma-separated SM counts")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (mixed precision, batched, adjoint)")
     ap.add_argument("--mode", default="solve",
                     choices=["solve", "mixed", "batched", "adjoint", "smscale", "variants", "robustness", "residual",
-                             "robust_vs_plain", "small", "peaks"],
+                             "robust_vs_plain", "small", "peaks", "batch"],
                     help="solve: the headline robust FP64 solve; mixed: FP32 + refinement vs FP64 at "
                          "m=n=8000; batched: 4096 uneven equations; adjoint: 256 Lyapunov forward+backward; "
                          "smscale: SM scaling; variants: sign variant, triangular solve, Bartels-Stewart at 4000; "
                          "robustness: robust vs plain on the paper's matrices, m=n=10000; residual: the "
                          "refinement's tensor-core residual at m=n=4000; robust_vs_plain: robust against non-robust "
                          "FP64 at m=n=4000 (overflow workload); small: m=n=256 microseconds per solve; peaks: "
-                         "measured binary64/binary32 FMA pipe rates")
+                         "measured binary64/binary32 FMA pipe rates; batch: --count equations of the batched "
+                         "distribution at --precision, no graph")
     return ap.parse_args()
 
 
@@ -831,7 +834,7 @@ def run_variants(args):
             raise sylv.SylvError(rc, "schur")
     ms, _ = _timed(schur, steps, warm, stream)
     rows["bartels_stewart"] = {"ms": ms, "gflops_6mnmn": 3 * flops_2(m, n) / ms / 1e6,
-                               "note": "4 cuBLAS DGEMMs (4mn(m+n) flops) + the robust solve"}
+                               "note": "4 products on the tensor-core GEMM, dense binary64-accurate mode (4mn(m+n) flops) + the robust solve"}
     return {"metric": "variant solves, m = n = 4000", "value": rows["bartels_stewart"]["ms"], "unit": "ms",
             "n_gpus": 1, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
             "config": {"m": m, "n": n, "tile": 32}, "rows": rows}
@@ -977,6 +980,53 @@ def run_small(args):
             "by_tile": by_tile}
 
 
+def run_batch(args):
+    """A batch of --count equations of the 4096-equation distribution (m, n
+    log-uniform in [16, 512], wellcond, per-equation seeds), one plan, executed
+    --warmup + --steps times without a graph at --precision (tile 32): solves/s.  The
+    plain form of the batched configuration, for profiles at a reduced count."""
+    import torch
+    from paper_1905_10574_gb300 import build, inputs, sylv
+    build.build()
+    sylv.load()
+    count = args.count
+    shapes = inputs.batch_shapes(count, 16, 512, seed=1234)
+    dev = torch.device("cuda", 0)
+    As, Bs, C0s = [], [], []
+    for i, (m, n) in enumerate(shapes):
+        A, B, C = inputs.problem(m, n, 10000 + i, kind="wellcond")
+        As.append(torch.from_numpy(A).to(dev))
+        Bs.append(torch.from_numpy(B).to(dev))
+        C0s.append(torch.from_numpy(C).to(dev))
+    Cs = [c.clone() for c in C0s]
+    stream = torch.cuda.current_stream(dev)
+    o = sylv.make_opts(stream=stream.cuda_stream, precision=args.precision, tile=args.tile or 32,
+                       tol=MIXED_TOL if args.precision == "fp32_refine" else 0.0)
+    plan = sylv.sylv_batch_create([m for m, _ in shapes], [n for _, n in shapes], [a.data_ptr() for a in As],
+                                  [a.stride(1) for a in As], [b.data_ptr() for b in Bs], [b.stride(1) for b in Bs],
+                                  [c.data_ptr() for c in Cs], [c.stride(1) for c in Cs], o)
+
+    def fn(_):
+        for c, c0 in zip(Cs, C0s):
+            c.copy_(c0)
+        rc = sylv.sylv_batch_execute(plan, stream.cuda_stream)
+        if rc:
+            raise sylv.SylvError(rc, "batch")
+
+    try:
+        ms, _ = _timed(fn, max(1, args.steps), args.warmup, stream)
+        rc, res = sylv.sylv_batch_results(plan, count)
+    finally:
+        sylv.sylv_batch_destroy(plan)
+    return {"metric": "batched solves/s", "value": count / (ms / 1000), "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"count": count, "m_n": "log-uniform [16,512]", "generator": "wellcond",
+                       "precision": args.precision, "tile": args.tile or 32, "cuda_graph": False,
+                       "note": "timed steps include the refill of the right-hand sides"},
+            "worst_info": max(r.info for r in res)}
+
+
 def run_peaks(args):
     """Measured peak rates of the FMA pipes the tile kernels are bound by (the
     denominators of their rooflines): binary64 FMA (the FP64 solve) and binary32 FMA
@@ -1061,6 +1111,8 @@ def main():
         print(json.dumps(run_small(args)), flush=True)
     elif args.mode == "peaks":
         print(json.dumps(run_peaks(args)), flush=True)
+    elif args.mode == "batch":
+        print(json.dumps(run_batch(args)), flush=True)
     else:
         run_ours(args)
 

@@ -157,7 +157,9 @@ Layout make_layout_seq(const Seq& sh, size_t base, int cta_cap, int per_sm = 2, 
   // Factor store of the diagonal-tile solves: per CTA, 5 TT^2 doubles bound
   // sum over block pairs of (s^2 + s), s = ma nb, and TT^2 packed pivot words.
   const int tt = tt_of(sh);
-  L.ncta = std::min<int64_t>(std::max<int64_t>(mt, 1), static_cast<int64_t>(sm_count()) * per_sm);
+  // CTAs of the tile kernel: never more than there are tiles in the launch (a batch's
+  // equations all run at once, so that is the sum over equations, not one equation's).
+  L.ncta = std::min<int64_t>(std::max<int64_t>(tiles, 1), static_cast<int64_t>(sm_count()) * per_sm);
   if (cta_cap > 0 && L.ncta > cta_cap) L.ncta = cta_cap;
   L.fstride = 5LL * tt * tt;
   L.fact = o;

@@ -155,3 +155,24 @@ def test_adjoint_in_refined_precision(orc, sy):
         assert rel(host(Gs[i]), rC) <= REFINE_TOL
         assert rel(host(dAs[i]), rA) <= REFINE_TOL
         assert rel(host(dBs[i]), rB) <= REFINE_TOL
+
+
+def test_batched_refine_degenerate_and_unconverged(orc, sy):
+    """Single-row and single-column equations in a refined batch converge like the
+    others; with maxit = 1 no equation can pass the stop test, so each reports
+    SYLV_NOT_CONVERGED and returns its first (binary32-accurate) solution."""
+    shapes = [(1, 5), (40, 30), (7, 1), (64, 65)]
+    probs = [inputs.problem(m, n, 950 + i, kind="wellcond") for i, (m, n) in enumerate(shapes)]
+    Ys, res = sy.batch_solve([dev(p[0]) for p in probs], [dev(p[1]) for p in probs], [dev(p[2]) for p in probs],
+                             precision="fp32_refine")
+    torch.cuda.synchronize()
+    for (A, B, C), Y, r in zip(probs, Ys, res):
+        assert r.info == 0, r
+        assert rel(host(Y), orc.trsyl(A, B, C)["Y"]) <= REFINE_TOL
+    Ys, res = sy.batch_solve([dev(p[0]) for p in probs], [dev(p[1]) for p in probs], [dev(p[2]) for p in probs],
+                             precision="fp32_refine", maxit=1)
+    torch.cuda.synchronize()
+    for (A, B, C), Y, r in zip(probs, Ys, res):
+        assert r.info == sy.SYLV_NOT_CONVERGED and r.iters == 1, r
+        err = rel(host(Y), orc.trsyl(A, B, C)["Y"])
+        assert err <= 1e-4  # binary32-accurate, not refined

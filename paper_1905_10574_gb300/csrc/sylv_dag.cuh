@@ -75,6 +75,8 @@ struct DagSmem {
   int qb2[TT + 1];                    // prefix sums of squared B block sizes
   short rowblk[TT], colblk[TT];       // block index of every row / column of the tile
   short astart[TT + 1], bstart[TT + 1];
+  short aord[TT], bord[TT];           // blocks grouped by kind for the pair preparation (order_blocks)
+  int acnt[3], bcnt[3];               // blocks of each kind: merged pseudo, 2x2, 1x1
   unsigned apsd, bpsd;                // diagonal solve: blocks that are two merged 1x1 blocks (bit per block)
   unsigned long long umax;
   unsigned long long stage_bar;        // mbarrier of the bulk-copy staging (packed tiles)
@@ -665,6 +667,39 @@ __device__ __noinline__ int pair_half_prepare(int ma, int nb, bool pa, double a0
 
 // Offset of pair (kb, lb) in the factor store: pairs are stored block row by block
 // row, each taking s^2 + s doubles (s = ma nb).
+// Blocks grouped by kind for the pair preparation: merged pseudo blocks first, then
+// 2x2 blocks, then 1x1 blocks (stable within a kind).  The small systems of different
+// kinds take different code, so a warp whose pairs mix kinds executes every kind's
+// code in turn, which on the 1/64-rate FP64 pipe costs as much as the updates of
+// several producers; with pairs enumerated kind by kind a warp mostly runs one.  One
+// warp; writes ord[0..nblk) and cnt[3].
+__device__ inline void order_blocks(const short* start, int nblk, unsigned pseudo, short* ord, int* cnt, int lane) {
+  int n[3] = {0, 0, 0};
+  for (int b0 = 0; b0 < nblk; b0 += 32) {
+    const int b = b0 + lane;
+    const bool v = b < nblk;
+    const bool ps = v && b < 32 && ((pseudo >> b) & 1u);
+    const int kind = !v ? 3 : ps ? 0 : (start[b + 1] - start[b] == 2 ? 1 : 2);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) n[t] += __popc(__ballot_sync(0xffffffffu, kind == t));
+  }
+  int off[3] = {0, n[0], n[0] + n[1]};
+  const unsigned below = (1u << lane) - 1u;
+  for (int b0 = 0; b0 < nblk; b0 += 32) {
+    const int b = b0 + lane;
+    const bool v = b < nblk;
+    const bool ps = v && b < 32 && ((pseudo >> b) & 1u);
+    const int kind = !v ? 3 : ps ? 0 : (start[b + 1] - start[b] == 2 ? 1 : 2);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const unsigned m = __ballot_sync(0xffffffffu, kind == t);
+      if (kind == t) ord[off[t] + __popc(m & below)] = static_cast<short>(b);
+      off[t] += __popc(m);
+    }
+  }
+  if (lane < 3) cnt[lane] = n[lane];
+}
+
 template <int TT, typename T>
 __device__ __forceinline__ int pair_offset(const DagSmem<TT, T>& sh, int kb, int lb, int ma) {
   return sh.pa[kb] + ma * ma * sh.qb2[lb] + ma * sh.bstart[lb];
@@ -726,6 +761,10 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
   }
   __syncthreads();
   const int pb = sh.pb, qb = sh.qb;
+  if (warp == 0)
+    order_blocks(sh.astart, pb, kMerge ? sh.apsd : 0u, sh.aord, sh.acnt, lane);
+  else if (warp == 1)
+    order_blocks(sh.bstart, qb, kMerge ? sh.bpsd : 0u, sh.bord, sh.bcnt, lane);
   if (tid == 0) {
     int acc = 0;
     for (int lb = 0; lb < qb; ++lb) {
@@ -764,8 +803,33 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
     }
   }
   __syncthreads();
+  // Pairs enumerated kind by kind (A kind major, then B kind; order_blocks).
+  const int na0 = sh.acnt[0], na1 = sh.acnt[1], nb0 = sh.bcnt[0], nb1 = sh.bcnt[1];
   for (int pidx = tid; pidx < pb * qb; pidx += kThreads) {
-    const int kb = pidx / qb, lb = pidx % qb;
+    int r = pidx, ao = 0, na = na0;
+    if (r >= na0 * qb) {
+      r -= na0 * qb;
+      ao = na0;
+      na = na1;
+      if (r >= na1 * qb) {
+        r -= na1 * qb;
+        ao = na0 + na1;
+        na = pb - na0 - na1;
+      }
+    }
+    // within this A kind: B kinds in turn, each a na x (blocks of that kind) class
+    int bo = 0, nbk = nb0;
+    if (r >= na * nb0) {
+      r -= na * nb0;
+      bo = nb0;
+      nbk = nb1;
+      if (r >= na * nb1) {
+        r -= na * nb1;
+        bo = nb0 + nb1;
+        nbk = qb - nb0 - nb1;
+      }
+    }
+    const int kb = sh.aord[ao + r / nbk], lb = sh.bord[bo + r % nbk];
     const int ra = sh.astart[kb], ma = sh.astart[kb + 1] - ra;
     const int cb0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - cb0;
     double a[4], b[4];

@@ -38,6 +38,11 @@ namespace sylv {
 #ifndef SYLV_MERGE_DIAG
 #define SYLV_MERGE_DIAG 1
 #endif
+// Left-looking diagonal solves (diag_solve's first phase); a build may turn it off
+// for comparison, leaving the right-looking wavefront alone.
+#ifndef SYLV_LEFT_DIAG
+#define SYLV_LEFT_DIAG 1
+#endif
 
 template <int TT, typename T>
 struct DagSmem {
@@ -70,6 +75,7 @@ struct DagSmem {
   unsigned long long bcolmax[TT];     // per B block lb: max_c>=end(lb) sum_j in lb |B[j,c]| (bits)
   short pr0[TT], pma[TT];             // this step: first row and height of the block solved in column block lb
   unsigned wmax[kThreads / 32];       // per-warp bound on |y| over unsolved elements (high word, rounded up)
+  unsigned wz[2][kThreads / 32];      // left-looking phase: per-warp bound on |z| of a step (by step parity)
   int pe[TT];                         // scale exponent of each solved block of this step
   int pa[TT + 1];                     // factor-store offset of block row kb (see pair_offset)
   int qb2[TT + 1];                    // prefix sums of squared B block sizes
@@ -911,7 +917,29 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
 
 // Diagonal-tile solve: Algorithm 2 applied to one tile, in wavefront order over its
 // 1x1/2x2 blocks.  The blocks (kb, lb) on the anti-diagonal s = (pb-1-kb) + lb are
-// independent; a step solves them (Phase A: one thread per element, the stored
+// independent (without a B term, step s is block row pb-1-s in every column).
+//
+// Left-looking phase.  Step s forms each of its elements' complete right-hand side
+//   r = Y0 - A(row, rows below its block) Z(those rows, col) - Z(row, cols left of its
+//       block) B(those cols, col)
+// from elements solved in earlier steps: a dot product split across L lanes and summed
+// by shuffles, so the FP64 work is dense (a fixed per-element ownership would issue a
+// warp instruction whenever any of its lanes has a term).  The block's stored inverse
+// then gives its solution (the members of a block sit in one warp and exchange their
+// right-hand sides by shuffles).  Robustness: every partial sum is bounded by
+//   U0 + (RA + CB) max|Z|,  RA = sum_kb acolmax[kb],  CB = sum_lb bcolmax[lb]
+// (U0 bounds |Y0|; RA bounds the A row sums right of any block, CB the B column sums
+// above any block), so while that bound stays two binades under omega' = omega/2 (an
+// exponent test after every step) no intermediate can exceed omega' and the step needs
+// no scaling, which is the outcome the guards of Algorithm 2 reach as well.  The first
+// step where the test fails, or where a block's solution would fail the inverse's
+// bound test (the guarded elimination is needed), is taken back: its elements get
+// their right-hand sides again, every unsolved element owned below receives the
+// contributions of the steps before it, and the right-looking phase continues from
+// that step.
+//
+// Right-looking phase (from the hand-over step; the whole solve when the left-looking
+// phase is off).  A step solves its blocks (Phase A: one thread per element, the stored
 // inverses; a block whose bound test fails is solved by its first thread with the
 // guarded elimination), agrees on one tile-wide power of two (Phase B, only when
 // some bound comes near omega), and every unsolved element's owner applies the
@@ -956,7 +984,8 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
   // pb-1-s in every column block, and no element takes a B-side contribution.
   const int lw = nob ? 0 : 1;
 
-  // Element ownership: row tid % TT, columns tid / TT + j * CSTEP (j < NC).
+  // Element ownership of the right-looking phase: row tid % TT, columns
+  // tid / TT + j * CSTEP (j < NC).
   const int my_r = tid % TT;
   const int my_c0 = tid / TT;
   const bool row_ok = my_r < mt;
@@ -970,7 +999,6 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
     const int c = my_c0 + j * CSTEP;
     okj[j] = row_ok && c < nt;
     lbcj[j] = okj[j] ? sh.colblk[c] : 0;
-    yv[j] = okj[j] ? Ys[my_r + c * LDY] : T(0);
   }
 
   // Initial U (and a pre-scaling if the tile exceeds omega').
@@ -978,7 +1006,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
     unsigned um = 0;
 #pragma unroll
     for (int j = 0; j < NC; ++j)
-      if (okj[j]) um = max(um, hi_bound(yv[j]));
+      if (okj[j]) um = max(um, hi_bound(Ys[my_r + (my_c0 + j * CSTEP) * LDY]));
     um = __reduce_max_sync(0xffffffffu, um);
     if (lane == 0) sh.wmax[warp] = um;
   }
@@ -998,9 +1026,9 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
 #pragma unroll
       for (int j = 0; j < NC; ++j)
         if (okj[j]) {
-          yv[j] = mul2(yv[j], z);
-          Ys[my_r + (my_c0 + j * CSTEP) * LDY] = yv[j];
-          um = max(um, hi_bound(yv[j]));
+          T* yp = &Ys[my_r + (my_c0 + j * CSTEP) * LDY];
+          *yp = mul2(*yp, z);
+          um = max(um, hi_bound(*yp));
         }
       if (tid == 0) sh.e_diag = z;
       um = __reduce_max_sync(0xffffffffu, um);
@@ -1012,7 +1040,140 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
   bool near = false;
   int local_scale_events = 0;
   const int nsteps = pb + lw * (qb - 1);
-  for (int s = 0; s < nsteps; ++s) {
+  int s0 = 0;  // first step of the right-looking phase
+
+  if constexpr (SYLV_LEFT_DIAG) {
+    // Exponent bounds of the left-looking test: U0, and RA, CB (a sum of at most TT
+    // terms, each below 2^max, is below 2^(max + log2 TT)).
+    constexpr int kSumE = (TT <= 32) ? 5 : 6;
+    int U0e = 0, RCe = 0;
+    if (ROBUST) {
+      unsigned u0 = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) u0 = max(u0, sh.wmax[w]);
+      U0e = ub_log2(from_hi_bound(u0));
+      int ra = -1100;
+      for (int b = lane; b < pb; b += 32) ra = max(ra, ub_log2(bits_to_double(sh.acolmax[b])));
+      for (int b = lane; b < qb && lw; b += 32) ra = max(ra, ub_log2(bits_to_double(sh.bcolmax[b])));
+      RCe = __reduce_max_sync(0xffffffffu, ra) + kSumE + 1;  // RA + CB <= 2 max(RA, CB)
+    }
+    int zrun = -1100;  // upper bound on log2 max |z| over the solved elements
+    s0 = nsteps;
+    if (ROBUST && U0e + 2 > eo) s0 = 0;
+    for (int s = 0; s < s0; ++s) {
+      const int e0 = sh.sstart[s];
+      const int E = sh.sstart[s + 1] - e0;
+      // lanes per element: binary64 aims at four busy warps (its pipe is the limit),
+      // binary32 at all eight (the step's latency is); at most 8, so that the members
+      // of a 2x2-by-2x2 block share a warp
+      int lg;
+      if constexpr (sizeof(T) == 8)
+        lg = E <= 16 ? 3 : E <= 32 ? 2 : E <= 64 ? 1 : 0;
+      else
+        lg = E <= 32 ? 3 : E <= 64 ? 2 : E <= 128 ? 1 : 0;
+      const int L = 1 << lg;
+      const int g = tid >> lg, jl = tid & (L - 1);
+      const bool act = g < E;
+      int r = 0, c = 0, ev = 0, kb = 0, lb = 0, ma = 1, sz = 1;
+      T acc = T(0);
+      if (act) {
+        const unsigned code = sh.eord[e0 + g];
+        r = code & 63;
+        c = (code >> 6) & 63;
+        ev = code >> 12;
+        kb = sh.rowblk[r];
+        lb = sh.colblk[c];
+        const int ra = sh.astart[kb];
+        ma = sh.astart[kb + 1] - ra;
+        const int cb0 = sh.bstart[lb];
+        sz = ma * (sh.bstart[lb + 1] - cb0);
+        T acc2 = T(0);
+        for (int t = ra + ma + jl; t < mt; t += L) acc = fma(Ak[r + t * LDY], Ys[t + c * LDY], acc);
+        if (lw)
+          for (int t = jl; t < cb0; t += L) acc2 = fma(Ys[r + t * LDY], Bk[t + c * LDY], acc2);
+        acc += acc2;
+      }
+      for (int o = L >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      const T rhs = act ? Ys[r + c * LDY] - acc : T(0);
+      // the block's right-hand sides, from its members' first lanes
+      const int gl = ((g - ev) << lg) & 31;
+      T rt[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) rt[u] = __shfl_sync(0xffffffffu, rhs, u < sz ? gl + (u << lg) : lane);
+      bool bad = false;
+      unsigned hb = 0;
+      if (act) {
+        const FactT* f = fact + pair_offset(sh, kb, lb, ma);
+        if (factp[kb * TT + lb] & (1 << 16)) near = true;
+        int rexp = -1022;
+        FactT z = FactT(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (u < sz) {
+            rexp = max(rexp, ub_log2(rt[u]));
+            z = fma(f[ev * sz + u], static_cast<FactT>(rt[u]), z);
+          }
+        bad = ROBUST && ub_log2(f[sz * sz]) + rexp + 1 > eo;
+        const T zt = static_cast<T>(z);
+        if (!bad) {
+          if (jl == 0) Ys[r + c * LDY] = zt;
+          hb = hi_bound(zt);
+        }
+      }
+      if (ROBUST) {
+        hb = __reduce_max_sync(0xffffffffu, hb);
+        if (lane == 0) sh.wz[s & 1][warp] = hb;
+      }
+      const int anybad = __syncthreads_or(bad);
+      if (ROBUST) {
+        unsigned zb = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) zb = max(zb, sh.wz[s & 1][w]);
+        zrun = max(zrun, ub_log2(from_hi_bound(zb)));
+        if (anybad || max(U0e, RCe + zrun) + 2 > eo) {
+          // hand this step to the right-looking phase: its elements get their
+          // right-hand sides back
+          if (act && jl == 0) Ys[r + c * LDY] = rhs;
+          s0 = s;
+          __syncthreads();
+        }
+      }
+    }
+  }
+
+  if constexpr (ROBUST || !SYLV_LEFT_DIAG) {
+    if (s0 < nsteps) {
+      // Owned unsolved elements into registers, with the contributions of the steps
+      // before s0 (solved in the left-looking phase): the X bottom blocks of their
+      // column and the Yb left blocks of their row.  The bound test of step s0 - 1
+      // covers these sums.
+      unsigned um = 0;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        yv[j] = T(0);
+        if (!okj[j]) continue;
+        const int c = my_c0 + j * CSTEP;
+        const int dd = dr + lw * lbcj[j];
+        if (dd < s0) continue;
+        T y = Ys[my_r + c * LDY];
+        if (dd > s0 && s0 > 0) {
+          const int X = s0 - lw * lbcj[j];
+          if (X > 0)
+            for (int t = sh.astart[pb - X]; t < mt; ++t) y = fma(-Ak[my_r + t * LDY], Ys[t + c * LDY], y);
+          const int Yb = s0 - dr;
+          if (lw && Yb > 0)
+            for (int t = 0; t < sh.bstart[Yb]; ++t) y = fma(-Ys[my_r + t * LDY], Bk[t + c * LDY], y);
+        }
+        yv[j] = y;
+        if (ROBUST) um = max(um, hi_bound(y));
+      }
+      if (ROBUST) {
+        um = __reduce_max_sync(0xffffffffu, um);
+        if (lane == 0) sh.wmax[warp] = um;
+      }
+      __syncthreads();
+    }
+  for (int s = s0; s < nsteps; ++s) {
     // Phase C's coefficients do not depend on this step's solutions: the binary32
     // tile-32 kernel (latency bound, with registers to spare) fetches them now, while
     // Phase A runs; the others read them after the barrier.  The block solved in
@@ -1261,6 +1422,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
       if (lane == 0) sh.wmax[warp] = wm;
     }
     __syncthreads();
+  }
   }
   if (near) atomicOr(&sh.flags, kFlagNearSingular);
   if (local_scale_events) atomicAdd(&sh.nscale, local_scale_events);

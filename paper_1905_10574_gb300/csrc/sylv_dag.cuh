@@ -1060,60 +1060,107 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
     int zrun = -1100;  // upper bound on log2 max |z| over the solved elements
     s0 = nsteps;
     if (ROBUST && U0e + 2 > eo) s0 = 0;
-    for (int s = 0; s < s0; ++s) {
+    // A step's bookkeeping does not depend on the solutions: it is read for step s+1
+    // before the barrier that ends step s, so that after the barrier only the dot
+    // products, the shuffles and the small solve remain on the step's critical path.
+    struct Meta {
+      int lg, g, E;          // log2 lanes per element, this thread's element (group), elements of the step
+      int r, c, ev, sz;      // element, its index in the block, block size
+      int ka0, Ka, Kt;       // first row below the block, A-side terms, all terms
+      int fo;                // offset of the block's inverse in the factor store
+      FactT fr[4], fn;       // binary32: the element's row of the inverse, and ||Minv||_inf
+      bool nr;               // a pivot of the block's small system was raised
+    };
+    // The binary64 kernels read all of it after the barrier (registers: the prefetch
+    // would spill in them, and their steps are bound by the FP64 pipe, not latency).
+    constexpr bool kPreF = sizeof(T) == 4;
+    auto load_inv = [&](Meta& m) {
+      const FactT* f = fact + m.fo;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (u < m.sz) m.fr[u] = f[m.ev * m.sz + u];
+      m.fn = f[m.sz * m.sz];
+    };
+    auto meta = [&](int s, Meta& m) {
       const int e0 = sh.sstart[s];
-      const int E = sh.sstart[s + 1] - e0;
-      // lanes per element: binary64 aims at four busy warps (its pipe is the limit),
-      // binary32 at all eight (the step's latency is); at most 8, so that the members
-      // of a 2x2-by-2x2 block share a warp
-      int lg;
+      m.E = sh.sstart[s + 1] - e0;
+      // lanes per element: binary64 aims at about four busy warps (its pipe is the
+      // limit), binary32 at all eight (the step's latency is); at most 8, so that the
+      // members of a 2x2-by-2x2 block share a warp
       if constexpr (sizeof(T) == 8)
-        lg = E <= 16 ? 3 : E <= 32 ? 2 : E <= 64 ? 1 : 0;
+        m.lg = m.E <= 16 ? 3 : m.E <= 32 ? 2 : m.E <= 64 ? 1 : 0;
       else
-        lg = E <= 32 ? 3 : E <= 64 ? 2 : E <= 128 ? 1 : 0;
-      const int L = 1 << lg;
-      const int g = tid >> lg, jl = tid & (L - 1);
-      const bool act = g < E;
-      int r = 0, c = 0, ev = 0, kb = 0, lb = 0, ma = 1, sz = 1;
+        m.lg = m.E <= 32 ? 3 : m.E <= 64 ? 2 : m.E <= 128 ? 1 : 0;
+      m.g = tid >> m.lg;
+      m.r = m.c = m.ev = m.ka0 = m.Ka = m.Kt = m.fo = 0;
+      m.sz = 1;
+      m.nr = false;
+      m.fn = FactT(0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) m.fr[u] = FactT(0);
+      if (m.g < m.E) {
+        const unsigned code = sh.eord[e0 + m.g];
+        m.r = code & 63;
+        m.c = (code >> 6) & 63;
+        m.ev = code >> 12;
+        const int kb = sh.rowblk[m.r], lb = sh.colblk[m.c];
+        const int ra = sh.astart[kb];
+        const int ma = sh.astart[kb + 1] - ra;
+        const int cb0 = sh.bstart[lb];
+        m.sz = ma * (sh.bstart[lb + 1] - cb0);
+        m.ka0 = ra + ma;
+        m.Ka = mt - m.ka0;
+        m.Kt = m.Ka + lw * cb0;
+        m.fo = pair_offset(sh, kb, lb, ma);
+        if constexpr (kPreF) load_inv(m);
+        m.nr = (factp[kb * TT + lb] & (1 << 16)) != 0;
+      }
+    };
+    Meta m;
+    if (kPreF && s0 > 0) meta(0, m);
+    for (int s = 0; s < s0; ++s) {
+      if constexpr (!kPreF) meta(s, m);
+      const int L = 1 << m.lg;
+      const int jl = tid & (L - 1);
+      const bool act = m.g < m.E;
+      // r = Y0 - sum over the element's terms: A side (rows below its block) then B
+      // side (columns left of it), one index space split across the group's lanes; the
+      // first lane starts from Y0.  Both sides read the left factor with stride LDY and
+      // the right one with stride 1.
       T acc = T(0);
       if (act) {
-        const unsigned code = sh.eord[e0 + g];
-        r = code & 63;
-        c = (code >> 6) & 63;
-        ev = code >> 12;
-        kb = sh.rowblk[r];
-        lb = sh.colblk[c];
-        const int ra = sh.astart[kb];
-        ma = sh.astart[kb + 1] - ra;
-        const int cb0 = sh.bstart[lb];
-        sz = ma * (sh.bstart[lb + 1] - cb0);
-        T acc2 = T(0);
-        for (int t = ra + ma + jl; t < mt; t += L) acc = fma(Ak[r + t * LDY], Ys[t + c * LDY], acc);
-        if (lw)
-          for (int t = jl; t < cb0; t += L) acc2 = fma(Ys[r + t * LDY], Bk[t + c * LDY], acc2);
-        acc += acc2;
+        if (jl == 0) acc = Ys[m.r + m.c * LDY];
+        const T* xa = Ak + m.r + m.ka0 * LDY;
+        const T* ya = Ys + m.ka0 + m.c * LDY;
+        const T* xb = Ys + m.r - m.Ka * LDY;
+        const T* yb = Bk + m.c * LDY - m.Ka;
+        for (int t = jl; t < m.Kt; t += L) {
+          const bool sa = t < m.Ka;
+          acc = fma(-(sa ? xa : xb)[t * LDY], (sa ? ya : yb)[t], acc);
+        }
       }
       for (int o = L >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      const T rhs = act ? Ys[r + c * LDY] - acc : T(0);
+      const T rhs = acc;
       // the block's right-hand sides, from its members' first lanes
-      const int gl = ((g - ev) << lg) & 31;
+      const int gl = ((m.g - m.ev) << m.lg) & 31;
       T rt[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) rt[u] = __shfl_sync(0xffffffffu, rhs, u < sz ? gl + (u << lg) : lane);
+      for (int u = 0; u < 4; ++u) rt[u] = __shfl_sync(0xffffffffu, rhs, u < m.sz ? gl + (u << m.lg) : lane);
       bool bad = false;
       unsigned hb = 0;
+      const int r = m.r, c = m.c;
       if (act) {
-        const FactT* f = fact + pair_offset(sh, kb, lb, ma);
-        if (factp[kb * TT + lb] & (1 << 16)) near = true;
+        if constexpr (!kPreF) load_inv(m);
+        if (m.nr) near = true;
         int rexp = -1022;
         FactT z = FactT(0);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (u < sz) {
+          if (u < m.sz) {
             rexp = max(rexp, ub_log2(rt[u]));
-            z = fma(f[ev * sz + u], static_cast<FactT>(rt[u]), z);
+            z = fma(m.fr[u], static_cast<FactT>(rt[u]), z);
           }
-        bad = ROBUST && ub_log2(f[sz * sz]) + rexp + 1 > eo;
+        bad = ROBUST && ub_log2(m.fn) + rexp + 1 > eo;
         const T zt = static_cast<T>(z);
         if (!bad) {
           if (jl == 0) Ys[r + c * LDY] = zt;
@@ -1124,6 +1171,7 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
         hb = __reduce_max_sync(0xffffffffu, hb);
         if (lane == 0) sh.wz[s & 1][warp] = hb;
       }
+      if (kPreF && s + 1 < s0) meta(s + 1, m);
       const int anybad = __syncthreads_or(bad);
       if (ROBUST) {
         unsigned zb = 0;

@@ -3,6 +3,7 @@
 // transposed forms, the FP32 + refinement loop, the adjoint, and batch plans.
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <array>
 #include <cstring>
 #include <mutex>
@@ -1010,6 +1011,9 @@ struct sylv_batch_plan {
   size_t ref_x_bytes = 0;
   int* ref_counters = nullptr;
   RefineState* ref_rs = nullptr;
+  OzBatchEq* doz = nullptr;   // tensor-core residual: per-equation descriptors (device)
+  OzTask* dtask = nullptr;    // and its output tiles
+  int noz_tasks = 0;
   int maxit = 6;
   double tol = 0.0;
 };
@@ -1100,6 +1104,27 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
     std::vector<size_t> o_ah(count), o_al(count), o_bh(count), o_bl(count), o_rf(count), o_r(count), o_x(count),
         o_d(count);
     size_t off_zero = 0, off_rs = 0, off_cnt = 0, off_ref = 0, off_x0 = 0, off_x1 = 0;
+    // the first residual on the tensor cores: packed slices per equation, descriptors, tiles
+    std::vector<size_t> o_oz(count);
+    std::vector<OzTask> oz_tasks;
+    size_t off_oz = 0, off_task = 0;
+    const bool oz = refine && residual_on_tensor_cores();
+    if (oz) {
+      for (int i = 0; i < count; ++i) {
+        o_oz[i] = off;
+        off = align_up(off + oz_workspace_bytes(sh[i].m, sh[i].n));
+      }
+      // larger equations first: their tiles hold the longest K ranges
+      std::vector<int> ordr(count);
+      for (int i = 0; i < count; ++i) ordr[i] = i;
+      std::stable_sort(ordr.begin(), ordr.end(),
+                       [&](int a, int b) { return sh[a].m + sh[a].n > sh[b].m + sh[b].n; });
+      for (int i : ordr) oz_batch_tasks(i, sh[i].m, sh[i].n, &oz_tasks);
+      off_oz = off;
+      off = align_up(off + sizeof(OzBatchEq) * count);
+      off_task = off;
+      off = align_up(off + sizeof(OzTask) * oz_tasks.size());
+    }
     if (refine) {
       for (int i = 0; i < count; ++i) {
         const size_t mm = sh[i].m * sh[i].m, nn = sh[i].n * sh[i].n, mn = sh[i].m * sh[i].n;
@@ -1202,6 +1227,35 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
         ln[i] = std::max<int64_t>(e.n, 1);
       }
       I = make_insts(sh, P->L, Af, lm, Bf, ln, Rfv, lm, 1, o.omega);
+      if (oz) {
+        std::vector<OzBatchEq> q(count);
+        for (int i = 0; i < count; ++i) {
+          const RefEq& e = re[i];
+          oz_carve(P->ws + o_oz[i], e.m, e.n, &q[i].b);
+          q[i].A = e.A;
+          q[i].lda = e.lda;
+          q[i].B = e.B;
+          q[i].ldb = e.ldb;
+          q[i].X = e.X;
+          q[i].ldx = lm[i];
+          q[i].C = e.C;
+          q[i].ldc = e.ldc;
+          q[i].R = e.R;
+          q[i].ldr = lm[i];
+          q[i].rmax = e.slots + 2 + 3 * 1;  // max |R| before correction 1
+          q[i].skip = &e.rs->conv;
+        }
+        P->doz = reinterpret_cast<OzBatchEq*>(P->ws + off_oz);
+        P->dtask = reinterpret_cast<OzTask*>(P->ws + off_task);
+        P->noz_tasks = static_cast<int>(oz_tasks.size());
+        if (cudaMemcpy(P->doz, q.data(), sizeof(OzBatchEq) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(P->dtask, oz_tasks.data(), sizeof(OzTask) * oz_tasks.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+          cudaFree(P->ws);
+          delete P;
+          return SYLV_ERR_CUDA;
+        }
+      }
       P->w.eqskip = &P->ref_rs[0].conv;
       P->w.eqskip_stride = static_cast<int32_t>(sizeof(RefineState) / sizeof(int));
       P->w.skip = P->ref_counters + 2;
@@ -1234,7 +1288,8 @@ static int execute_refine(sylv_batch_plan* P, cudaStream_t s) {
   const int count = P->count;
   const int nt32 = static_cast<int>((P->maxN + 31) / 32);
   const int nt64 = static_cast<int>((P->maxN + GT - 1) / GT);
-  const int eg = std::max(1, std::min<int>(static_cast<int>((P->maxN * P->maxN + 255) / 256), 64));
+  // elementwise kernels: a warp per column, 8 per CTA, columns strided over <= 64 CTAs
+  const int eg = std::max(1, std::min<int>(static_cast<int>((P->maxN + 7) / 8), 64));
   if (P->transa) {
     k_anti_transpose_batched<<<dim3(nt32, nt32, count), 256, 0, s>>>(P->dta);
     k_bref_flip<<<dim3(eg, count), 256, 0, s>>>(P->dref, 0);
@@ -1246,14 +1301,23 @@ static int execute_refine(sylv_batch_plan* P, cudaStream_t s) {
   if (cudaMemsetAsync(P->ws + L.zero_lo, 0, L.zero_hi - L.zero_lo, s) != cudaSuccess) return SYLV_ERR_CUDA;
   k_bref_maxabs<<<dim3(eg, count), 256, 0, s>>>(P->dref);
   k_bref_split<<<dim3(eg, count), 256, 0, s>>>(P->dref);
+  // slices of A and B for the first residual on the tensor cores
+  if (P->doz && oz_batch_split(P->doz, count, 0x9u, P->maxN, s) != cudaSuccess) return SYLV_ERR_CUDA;
   cudaError_t e = run_prep<float>(P->w, L, count, P->maxN, P->pmax_all, s);
   if (e != cudaSuccess) return SYLV_ERR_CUDA;
   const int ntasks = static_cast<int>(std::min<int64_t>(L.sum_tiles, L.ncta));
   for (int it = 0; it < P->maxit; ++it) {
-    if (it == 0)
+    if (it == 0) {
       k_bref_copy_max<<<dim3(eg, count), 256, 0, s>>>(P->dref);
-    else
+    } else if (it == 1 && P->doz) {
+      // first residual of the solution, binary64-accurate: error-free bf16 splitting on
+      // the tensor cores (double-float products on the FP32 pipe under SYLV_RESIDUAL=df)
+      if (oz_batch_split(P->doz, count, 0x6u, P->maxN, s) != cudaSuccess) return SYLV_ERR_CUDA;
+      if (oz_batch_residual(P->doz, P->dtask, P->noz_tasks, &P->w.ctrl->err, P->w.timeout_ns, s) != cudaSuccess)
+        return SYLV_ERR_CUDA;
+    } else {
       k_bref_residual<<<dim3(nt64, nt64, count), 256, 0, s>>>(P->dref, it);
+    }
     k_bref_to_float<<<dim3(eg, count), 256, 0, s>>>(P->dref, it);
     if (it > 0) {
       if (cudaMemsetAsync(P->w.tflag, 0, sizeof(unsigned long long) * L.sum_tiles, s) != cudaSuccess) return SYLV_ERR_CUDA;

@@ -671,8 +671,6 @@ __device__ __noinline__ int pair_half_prepare(int ma, int nb, bool pa, double a0
   return flags & (1 << 16);
 }
 
-// Offset of pair (kb, lb) in the factor store: pairs are stored block row by block
-// row, each taking s^2 + s doubles (s = ma nb).
 // Blocks grouped by kind for the pair preparation: merged pseudo blocks first, then
 // 2x2 blocks, then 1x1 blocks (stable within a kind).  The small systems of different
 // kinds take different code, so a warp whose pairs mix kinds executes every kind's
@@ -706,6 +704,8 @@ __device__ inline void order_blocks(const short* start, int nblk, unsigned pseud
   if (lane < 3) cnt[lane] = n[lane];
 }
 
+// Offset of pair (kb, lb) in the factor store: pairs are stored block row by block
+// row, each taking s^2 + s doubles (s = ma nb).
 template <int TT, typename T>
 __device__ __forceinline__ int pair_offset(const DagSmem<TT, T>& sh, int kb, int lb, int ma) {
   return sh.pa[kb] + ma * ma * sh.qb2[lb] + ma * sh.bstart[lb];

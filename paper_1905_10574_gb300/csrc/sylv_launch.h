@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "sylv_internal.cuh"
 
 namespace sylv {
@@ -47,6 +49,36 @@ cudaError_t oz_split_ab(const OzBuffers& b, const double* A, int64_t lda, const 
 cudaError_t oz_residual(const OzBuffers& b, const double* X, int64_t ldx, const double* C, int64_t ldc, double* R,
                         int64_t ldr, unsigned long long* rmax, int* err, long long timeout_ns, const int* skip,
                         cudaStream_t s, bool binary64);
+// Batched form: one equation's operands, outputs and packed slices (oz_carve).
+struct OzBatchEq {
+  OzBuffers b;  // packed slices and exponents; b.m, b.n the equation's orders
+  const double* A;
+  int64_t lda;
+  const double* B;
+  int64_t ldb;
+  const double* X;  // the current solution, m x n
+  int64_t ldx;
+  const double* C;
+  int64_t ldc;
+  double* R;        // R = C - (A X + X B)
+  int64_t ldr;
+  unsigned long long* rmax;  // max |R| of the equation (atomic maximum of the bit patterns)
+  const int* skip;           // nonzero: the equation is passed over (converged)
+};
+// One 128 x 64 output tile of one equation.
+struct OzTask {
+  int32_t eq;
+  int16_t mb, nb;
+};
+// Slices of the operands in `mask` (bit 0 A, 1 X by columns, 2 X by rows, 3 B) of
+// every equation; max_rows / max_k bound every equation's orders.
+cudaError_t oz_batch_split(const OzBatchEq* eqs, int count, unsigned mask, int64_t max_rows, cudaStream_t s);
+// R = C - (A X + X B) and max |R| for every task's tile (binary64-accurate).
+cudaError_t oz_batch_residual(const OzBatchEq* eqs, const OzTask* tasks, int ntasks, int* err, long long timeout_ns,
+                              cudaStream_t s);
+// The tasks of an equation of orders m x n (appended to `out`).
+void oz_batch_tasks(int32_t eq, int64_t m, int64_t n, std::vector<OzTask>* out);
+
 // Dense product on the same tensor-core kernel, binary64-accurate (error-free
 // splitting): R -= L Q^T for L (mo x k, element (r, c) at L[r lrs + c lks]) and Q
 // (no x k, element (j, c) at Q[j qrs + c qks]); R is mo x no with leading dimension

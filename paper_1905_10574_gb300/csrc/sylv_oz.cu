@@ -93,6 +93,38 @@ cudaError_t oz_residual(const OzBuffers& b, const double* X, int64_t ldx, const 
   return cudaGetLastError();
 }
 
+// ---- batched residuals (FP32 + refinement of many equations)
+cudaError_t oz_batch_split(const OzBatchEq* eqs, int count, unsigned mask, int64_t max_rows, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  // rows: a warp each (8 per CTA); tiles: a CTA each, both strided over <= 64 CTAs per equation
+  const unsigned gr = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(cdiv(max_rows + oz::BM, 8), 64)));
+  const unsigned gt = static_cast<unsigned>(
+      std::max<int64_t>(1, std::min<int64_t>(cdiv(max_rows, oz::BN) * cdiv(max_rows, oz::BK), 64)));
+  for (int which = 0; which < 4; ++which) {
+    if (!(mask & (1u << which))) continue;
+    oz::k_oz_rowexp_batched<<<dim3(gr, count), 256, 0, s>>>(eqs, which);
+    oz::k_oz_split_batched<<<dim3(gt, count), 256, 0, s>>>(eqs, which);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t oz_batch_residual(const OzBatchEq* eqs, const OzTask* tasks, int ntasks, int* err, long long timeout_ns,
+                              cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  auto kern = oz::k_oz_gemm_batched<oz::kMaxW>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sizeof(oz::Smem)));
+  if (e != cudaSuccess) return e;
+  kern<<<ntasks, oz::kThreads, sizeof(oz::Smem), s>>>(eqs, tasks, err, timeout_ns);
+  return cudaGetLastError();
+}
+
+void oz_batch_tasks(int32_t eq, int64_t m, int64_t n, std::vector<OzTask>* out) {
+  for (int64_t nb = 0; nb < cdiv(n, oz::BN); ++nb)
+    for (int64_t mb = 0; mb < cdiv(m, oz::BM); ++mb)
+      out->push_back(OzTask{eq, static_cast<int16_t>(mb), static_cast<int16_t>(nb)});
+}
+
 // ---- dense products (the Bartels-Stewart transformations)
 namespace {
 oz::Packed dense_left(int64_t rows, int64_t k) { return {nullptr, nullptr, cdiv(rows, oz::BM), cdiv(k, oz::BK), oz::BM}; }

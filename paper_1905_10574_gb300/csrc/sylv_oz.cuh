@@ -63,13 +63,6 @@ constexpr int kTileB = BN * BK;        // of a right-operand tile (2 KB)
 constexpr int kEpiWarps = 8;           // two per TMEM lane quarter, 32 columns each
 constexpr int kThreads = 32 * (kEpiWarps + 2);
 
-struct Smem {
-  __nv_bfloat16 a[NST][kSlices][kTileA];
-  __nv_bfloat16 b[NST][kSlices][kTileB];
-  int ecol[2][BN];
-  unsigned long long full[NST], empty[NST], accfull, accempty;
-  uint32_t tmem;
-};
 
 // One operand view: element (r, k) of the operand is src[r * rs + k * ks] within
 // rows x kdim; mask 1 keeps r <= k + 1 (A), mask 2 keeps k <= r + 1 (B as columns).
@@ -98,8 +91,7 @@ __device__ __forceinline__ double view_at(const View& v, int64_t r, int64_t k) {
 
 // Per-row exponent: smallest e with max_k |op(r, k)| < 2^e (0 for a zero row).
 // One warp per row, lanes over K.
-__global__ void k_oz_rowexp(View v, int* e, int64_t rows_padded, const int* skip) {
-  if (skip && ld_volatile(skip)) return;
+__device__ __forceinline__ void oz_rowexp(const View& v, int* e, int64_t rows_padded) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -117,6 +109,10 @@ __global__ void k_oz_rowexp(View v, int* e, int64_t rows_padded, const int* skip
     }
     if (lane == 0) e[r] = mx ? static_cast<int>((mx >> 52) & 0x7ff) - 1022 : 0;
   }
+}
+__global__ void k_oz_rowexp(View v, int* e, int64_t rows_padded, const int* skip) {
+  if (skip && ld_volatile(skip)) return;
+  oz_rowexp(v, e, rows_padded);
 }
 
 // round(x * 2^(56 - e)) as an integer, for |x| < 2^e: the element on the grid of
@@ -146,9 +142,7 @@ __device__ __forceinline__ long long fixed56(double x, int e) {
 // 2^(e_r - 57).  Slice s is stored pre-scaled, q_s 2^(-8(s-1)) (exact in bf16), so
 // that a product of slices s and t carries its weight 2^(-8(s+t-2)) relative to
 // the leading pair.  Infinities and NaN give NaN slices.
-__global__ void __launch_bounds__(256) k_oz_split(View v, Packed P, const int* skip) {
-  if (skip && ld_volatile(skip)) return;
-  __shared__ double tile[BM * (BK + 1)];
+__device__ __forceinline__ void oz_split(const View& v, const Packed& P, double* tile) {
   const int64_t per = P.slice_elems();
   const int tsz = P.R * BK;
   const bool rcontig = v.rs == 1;
@@ -182,6 +176,11 @@ __global__ void __launch_bounds__(256) k_oz_split(View v, Packed P, const int* s
       }
     }
   }
+}
+__global__ void __launch_bounds__(256) k_oz_split(View v, Packed P, const int* skip) {
+  if (skip && ld_volatile(skip)) return;
+  __shared__ double tile[BM * (BK + 1)];
+  oz_split(v, P, tile);
 }
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -273,6 +272,15 @@ struct Gemm {
   int dense;  // 1: one unstructured product a[0] b[0]^T over all of K (b[1] unused)
 };
 
+struct Smem {
+  __nv_bfloat16 a[NST][kSlices][kTileA];
+  __nv_bfloat16 b[NST][kSlices][kTileB];
+  int ecol[2][BN];
+  unsigned long long full[NST], empty[NST], accfull, accempty;
+  uint32_t tmem;
+  Gemm g;  // batched launches: the tile's equation
+};
+
 // K blocks of product p for output rows [i0, i0+128) and columns [j0, j0+64): A X
 // reads A[i, k] for k >= i - 1; X B reads B[k, j] for k <= j + 1.  A dense product
 // reads every K block, and there is no second product.
@@ -339,29 +347,14 @@ static_assert(kMaxW - kLeadW <= 4 && kLeadW - 1 <= 4, "N = 64 x (weights per MMA
 // and every slice pair of weight <= MAXW goes into the accumulator of its weight
 // (TMEM columns 64 (w - 2)..).  R starts as C and the end of each product subtracts
 // its terms.
+// One 128 x 64 output tile (row panel mb, column panel nb) of R = C - (A X + X B)
+// (or of R -= L Q^T in the dense form); the whole CTA.
 template <int MAXW>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_oz_gemm(Gemm g, const double* C, int64_t ldc, double* R, int64_t ldr, int64_t m, int64_t n,
-              unsigned long long* rmax, int* err, long long timeout_ns, const int* skip) {
+__device__ __forceinline__ void oz_tile(Smem& sh, const Gemm& g, const double* C, int64_t ldc, double* R, int64_t ldr,
+                                        int64_t m, int64_t n, unsigned long long* rmax, int* err,
+                                        long long timeout_ns, int mb, int nb) {
   constexpr int SMAX = MAXW - 1 < kSlices ? MAXW - 1 : kSlices;  // slices in use
-  if (skip && ld_volatile(skip)) return;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  Smem& sh = *reinterpret_cast<Smem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // Output tiles in L2-friendly order: the launch runs through groups of kGroupRows
-  // row panels, column panels fastest within a group, so that the CTAs resident at
-  // once share a few row panels of A (and of X) and a set of column panels instead
-  // of streaming every row panel's slices through L2 again for each column wave.
-  int mb, nb;
-  {
-    const int MBt = gridDim.x, NBt = gridDim.y;
-    const int id = blockIdx.x + MBt * blockIdx.y;
-    const int gsize = kGroupRows * NBt;
-    const int grp = id / gsize, in = id - grp * gsize;
-    const int rows = min(kGroupRows, MBt - grp * kGroupRows);
-    mb = grp * kGroupRows + in % rows;
-    nb = in / rows;
-  }
   const int64_t i0 = static_cast<int64_t>(mb) * BM, j0 = static_cast<int64_t>(nb) * BN;
 
   if (tid == 0) {
@@ -584,6 +577,97 @@ __global__ void __launch_bounds__(kThreads, 1)
     mx = warp_max(mx);
     if (lane == 0) atomic_max_nonneg(rmax, mx);
   }
+}
+
+template <int MAXW>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_oz_gemm(Gemm g, const double* C, int64_t ldc, double* R, int64_t ldr, int64_t m, int64_t n,
+              unsigned long long* rmax, int* err, long long timeout_ns, const int* skip) {
+  if (skip && ld_volatile(skip)) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  Smem& sh = *reinterpret_cast<Smem*>(smem_raw);
+  // Output tiles in L2-friendly order: the launch runs through groups of kGroupRows
+  // row panels, column panels fastest within a group, so that the CTAs resident at
+  // once share a few row panels of A (and of X) and a set of column panels instead
+  // of streaming every row panel's slices through L2 again for each column wave.
+  int mb, nb;
+  {
+    const int MBt = gridDim.x, NBt = gridDim.y;
+    const int id = blockIdx.x + MBt * blockIdx.y;
+    const int gsize = kGroupRows * NBt;
+    const int grp = id / gsize, in = id - grp * gsize;
+    const int rows = min(kGroupRows, MBt - grp * kGroupRows);
+    mb = grp * kGroupRows + in % rows;
+    nb = in / rows;
+  }
+  oz_tile<MAXW>(sh, g, C, ldc, R, ldr, m, n, rmax, err, timeout_ns, mb, nb);
+}
+
+// ---- batched residuals: many independent equations, one launch per step.
+// Packed operand shapes of an m x n equation (see the host's carving): operand 0 is
+// A (rows of A, K = its columns), 1 X by columns, 2 X by rows, 3 B by columns.
+__host__ __device__ inline void oz_shape(int64_t m, int64_t n, int which, int64_t& RB, int64_t& KB, int& R) {
+  const int64_t rows = (which == 0 || which == 2) ? m : n;
+  const int64_t kd = (which <= 1) ? m : n;
+  R = (which == 0 || which == 2) ? BM : BN;
+  RB = (rows + R - 1) / R;
+  KB = (kd + BK - 1) / BK;
+}
+__device__ __forceinline__ Packed oz_packed(const OzBatchEq& q, int which) {
+  Packed P;
+  P.p = static_cast<__nv_bfloat16*>(q.b.p[which]);
+  P.e = q.b.e[which];
+  oz_shape(q.b.m, q.b.n, which, P.RB, P.KB, P.R);
+  return P;
+}
+__device__ __forceinline__ View oz_view(const OzBatchEq& q, int which) {
+  const int64_t m = q.b.m, n = q.b.n;
+  switch (which) {
+    case 0: return View{q.A, 1, q.lda, m, m, 1};   // A as rows, r <= k + 1
+    case 1: return View{q.X, q.ldx, 1, n, m, 0};   // X by columns: element (j, i) = X[i, j]
+    case 2: return View{q.X, 1, q.ldx, m, n, 0};   // X by rows
+    default: return View{q.B, q.ldb, 1, n, n, 2};  // B by columns: element (j, k) = B[k, j], k <= j + 1
+  }
+}
+
+// Per-row exponents of operand `which` of every equation (equation blockIdx.y).
+__global__ void k_oz_rowexp_batched(const OzBatchEq* __restrict__ eqs, int which) {
+  const OzBatchEq& q = eqs[blockIdx.y];
+  if (q.skip && ld_volatile(q.skip)) return;
+  const Packed P = oz_packed(q, which);
+  oz_rowexp(oz_view(q, which), P.e, P.RB * P.R);
+}
+
+// Slices of operand `which` of every equation (equation blockIdx.y).
+__global__ void __launch_bounds__(256) k_oz_split_batched(const OzBatchEq* __restrict__ eqs, int which) {
+  __shared__ double tile[BM * (BK + 1)];
+  const OzBatchEq& q = eqs[blockIdx.y];
+  if (q.skip && ld_volatile(q.skip)) return;
+  oz_split(oz_view(q, which), oz_packed(q, which), tile);
+}
+
+// One output tile per CTA from the task list (equation, row panel, column panel).
+template <int MAXW>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_oz_gemm_batched(const OzBatchEq* __restrict__ eqs, const OzTask* __restrict__ tasks, int* err,
+                      long long timeout_ns) {
+  const OzTask t = tasks[blockIdx.x];
+  const OzBatchEq& q = eqs[t.eq];
+  if (q.skip && ld_volatile(q.skip)) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  Smem& sh = *reinterpret_cast<Smem*>(smem_raw);
+  // The equation's operand descriptors in shared memory (registers are scarce in the
+  // drain warps).
+  if (threadIdx.x < 4) {
+    const Packed P = oz_packed(q, threadIdx.x);
+    if (threadIdx.x & 1)
+      sh.g.b[threadIdx.x >> 1] = P;
+    else
+      sh.g.a[threadIdx.x >> 1] = P;
+  }
+  if (threadIdx.x == 0) sh.g.dense = 0;
+  __syncthreads();
+  oz_tile<MAXW>(sh, sh.g, q.C, q.ldc, q.R, q.ldr, q.b.m, q.b.n, q.rmax, err, timeout_ns, t.mb, t.nb);
 }
 
 }  // namespace oz

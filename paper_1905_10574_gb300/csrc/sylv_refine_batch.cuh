@@ -45,19 +45,26 @@ __device__ __forceinline__ int ref_sa(const RefEq& E) {
   return norm_exp(E.slots[0] > E.slots[1] ? E.slots : E.slots + 1);
 }
 
+// Visits every (r, c) of a rows x cols column-major array from the CTAs along grid
+// dimension x: a warp per column (coalesced along the rows), the warps of the grid
+// strided over the columns; no index division.
+template <typename F>
+__device__ __forceinline__ void for_each_rc(int64_t rows, int64_t cols, F&& f) {
+  const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t c = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); c < cols; c += nw)
+    for (int64_t r = threadIdx.x & 31; r < rows; r += 32) f(r, c);
+}
+
 // max |A| and max |B| over the quasi-triangular parts (equation blockIdx.y).
 __global__ void k_bref_maxabs(const RefEq* __restrict__ eq) {
   const RefEq E = eq[blockIdx.y];
   double ma = 0.0, mb = 0.0;
-  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < E.m * E.m; t += step) {
-    const int64_t r = t % E.m, c = t / E.m;
+  for_each_rc(E.m, E.m, [&](int64_t r, int64_t c) {
     if (r <= c + 1) ma = fmax(ma, fabs(E.A[r + c * E.lda]));
-  }
-  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < E.n * E.n; t += step) {
-    const int64_t r = t % E.n, c = t / E.n;
+  });
+  for_each_rc(E.n, E.n, [&](int64_t r, int64_t c) {
     if (r <= c + 1) mb = fmax(mb, fabs(E.B[r + c * E.ldb]));
-  }
+  });
   ma = warp_max(ma);
   mb = warp_max(mb);
   if ((threadIdx.x & 31) == 0) {
@@ -70,31 +77,27 @@ __global__ void k_bref_maxabs(const RefEq* __restrict__ eq) {
 __global__ void k_bref_split(const RefEq* __restrict__ eq) {
   const RefEq E = eq[blockIdx.y];
   const int s = ref_sa(E);
-  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < E.m * E.m; t += step) {
-    const int64_t r = t % E.m, c = t / E.m;
+  for_each_rc(E.m, E.m, [&](int64_t r, int64_t c) {
     const DF d = split_df(r <= c + 1 ? mul2(E.A[r + c * E.lda], -s) : 0.0);
-    E.Ah[t] = d.hi;
-    E.Al[t] = d.lo;
-  }
-  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < E.n * E.n; t += step) {
-    const int64_t r = t % E.n, c = t / E.n;
+    E.Ah[r + c * E.m] = d.hi;
+    E.Al[r + c * E.m] = d.lo;
+  });
+  for_each_rc(E.n, E.n, [&](int64_t r, int64_t c) {
     const DF d = split_df(r <= c + 1 ? mul2(E.B[r + c * E.ldb], -s) : 0.0);
-    E.Bh[t] = d.hi;
-    E.Bl[t] = d.lo;
-  }
+    E.Bh[r + c * E.n] = d.hi;
+    E.Bl[r + c * E.n] = d.lo;
+  });
 }
 
 // First right-hand side: R = C (X = 0), and max |C|.
 __global__ void k_bref_copy_max(const RefEq* __restrict__ eq) {
   const RefEq E = eq[blockIdx.y];
   double mx = 0.0;
-  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < E.m * E.n;
-       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const double v = E.C[(t % E.m) + (t / E.m) * E.ldc];
-    E.R[t] = v;
+  for_each_rc(E.m, E.n, [&](int64_t r, int64_t c) {
+    const double v = E.C[r + c * E.ldc];
+    E.R[r + c * E.m] = v;
     mx = fmax(mx, fabs(v));
-  }
+  });
   mx = warp_max(mx);
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(ref_slot(E, 0, 0), mx);
 }
@@ -119,9 +122,10 @@ __global__ void k_bref_to_float(const RefEq* __restrict__ eq, int it) {
   const RefEq E = eq[blockIdx.y];
   if (ref_done(E)) return;
   const int s = norm_exp(ref_slot(E, it, 0));
-  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < E.m * E.n;
-       t += static_cast<int64_t>(gridDim.x) * blockDim.x)
+  for_each_rc(E.m, E.n, [&](int64_t r, int64_t c) {
+    const int64_t t = r + c * E.m;
     E.Rf[t] = static_cast<float>(mul2(E.R[t], -s));
+  });
 }
 
 // X += D per solved tile (the correction solve left tile (k,l) of D' = 2^(sa-sr) D as
@@ -181,9 +185,7 @@ __global__ void k_bref_check(const RefEq* __restrict__ eq, int count, int it, do
 // C = X and the result record of each equation (equation blockIdx.y).
 __global__ void k_bref_finish(const RefEq* __restrict__ eq, sylv_result* res) {
   const RefEq E = eq[blockIdx.y];
-  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < E.m * E.n;
-       t += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    E.C[(t % E.m) + (t / E.m) * E.ldc] = E.X[t];
+  for_each_rc(E.m, E.n, [&](int64_t r, int64_t c) { E.C[r + c * E.ldc] = E.X[r + c * E.m]; });
   if (blockIdx.x == 0 && threadIdx.x == 0) refine_result_one(E.rs, res + blockIdx.y);
 }
 

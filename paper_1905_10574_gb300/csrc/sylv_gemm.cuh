@@ -370,6 +370,64 @@ __device__ __forceinline__ DF split_df(double v) {
   const float h = static_cast<float>(v);
   return DF{h, static_cast<float>(v - static_cast<double>(h))};
 }
+// The same conversions from the bit patterns, for elementwise kernels: on this GPU
+// every binary64 instruction (a multiply by 2^e, a conversion, a maximum) runs at
+// 1/64 of the binary32 rate, so one per element already costs as much time as the
+// element's memory traffic.  Results are those of the arithmetic forms; values
+// outside the binary32 normal range take the arithmetic path.
+//   f32_mul2(v, e)      = (float)(v 2^e), rounded to nearest even
+//   split_df_mul2(v, e) = split_df(v 2^e)
+//   f64_mul2(f, e)      = (double)f 2^e
+//   abs_key(v)          = a key that orders |v| like the values (NaN above infinity)
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+  return static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+__device__ __forceinline__ float f32_mul2(double v, int e) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  if ((b << 1) == 0) return __uint_as_float(static_cast<unsigned>(b >> 32));  // signed zero
+  const int E = static_cast<int>((b >> 52) & 0x7ff);
+  const int Ef = E - 896 + e;  // binary32 biased exponent before rounding
+  if (E == 0 || E == 0x7ff || Ef <= 0 || Ef >= 254) return static_cast<float>(mul2(v, e));
+  const unsigned keep = static_cast<unsigned>((b >> 29) & 0x7fffff);
+  const unsigned rem = static_cast<unsigned>(b & 0x1fffffff);
+  unsigned r = (static_cast<unsigned>(Ef) << 23) | keep;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u))) r += 1;  // a carry moves into the exponent
+  return __uint_as_float(r | (static_cast<unsigned>(b >> 32) & 0x80000000u));
+}
+__device__ __forceinline__ DF split_df_mul2(double v, int e) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  if ((b << 1) == 0) return DF{__uint_as_float(static_cast<unsigned>(b >> 32)), 0.0f};
+  const int E = static_cast<int>((b >> 52) & 0x7ff);
+  const int Ef = E - 896 + e;
+  if (E == 0 || E == 0x7ff || Ef <= 0 || Ef >= 254) return split_df(mul2(v, e));
+  const unsigned sign = static_cast<unsigned>(b >> 32) & 0x80000000u;
+  const unsigned keep = static_cast<unsigned>((b >> 29) & 0x7fffff);
+  int rem = static_cast<int>(b & 0x1fffffff);
+  unsigned r = (static_cast<unsigned>(Ef) << 23) | keep;
+  if (rem > 0x10000000 || (rem == 0x10000000 && (keep & 1u))) {
+    r += 1;
+    rem -= 0x20000000;  // the remainder below the rounded-up high part
+  }
+  // v 2^e - hi = +-rem 2^(Ef - 150): an integer below 2^29 converted with one rounding
+  const float lo = mul2(static_cast<float>(sign ? -rem : rem), Ef - 150);
+  return DF{__uint_as_float(r | sign), lo};
+}
+__device__ __forceinline__ double f64_mul2(float f, int e) {
+  const unsigned b = __float_as_uint(f);
+  const int Ef = static_cast<int>((b >> 23) & 0xff);
+  const int Ed = Ef + 896 + e;
+  if (Ef == 0 || Ef == 255 || Ed <= 0 || Ed >= 2047) return mul2(static_cast<double>(f), e);
+  return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(b & 0x80000000u) << 32) |
+                                                     (static_cast<unsigned long long>(Ed) << 52) |
+                                                     (static_cast<unsigned long long>(b & 0x7fffffu) << 29)));
+}
 __device__ __forceinline__ void df_acc(float& s, float& comp, float ah, float al, float xh, float xl) {
   const float p = ah * xh;
   const float q = fmaf(ah, xh, -p);

@@ -98,6 +98,7 @@ __device__ __forceinline__ void oz_rowexp(const View& v, int* e, int64_t rows_pa
   for (int64_t r = wid; r < rows_padded; r += nw) {
     unsigned long long mx = 0;
     if (r < v.rows)
+#pragma unroll 4
       for (int64_t k = lane; k < v.kdim; k += 32) {
         const unsigned long long b =
             static_cast<unsigned long long>(__double_as_longlong(view_at(v, r, k))) & 0x7FFFFFFFFFFFFFFFull;
@@ -148,6 +149,9 @@ __device__ __forceinline__ void oz_split(const View& v, const Packed& P, double*
   const bool rcontig = v.rs == 1;
   for (int64_t t = blockIdx.x; t < P.RB * P.KB; t += gridDim.x) {
     const int64_t r0 = (t / P.KB) * P.R, k0 = (t % P.KB) * BK;
+    // Tiles the products never read (kb_range): A's K blocks left of its row panel's
+    // diagonal, B's (as columns) beyond its column panel's; all masked zeros.
+    if ((v.mask == 1 && r0 > 0 && k0 / BK < (r0 - 1) / BK) || (v.mask == 2 && k0 / BK > (r0 + P.R) / BK)) continue;
     __syncthreads();  // the previous tile's reads are done
     for (int idx = threadIdx.x; idx < tsz; idx += blockDim.x) {
       const int r = rcontig ? idx % P.R : idx / BK;
@@ -162,6 +166,11 @@ __device__ __forceinline__ void oz_split(const View& v, const Packed& P, double*
       const bool finite = ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
       long long V = finite ? fixed56(x, P.e[r0 + rr]) : 0;
       const int64_t idx = t * tsz + o;
+      if (finite && V == 0) {  // zeros (padding, masked entries): every slice is zero
+#pragma unroll
+        for (int s = 0; s < kSlices; ++s) P.p[idx + s * per] = __float2bfloat16_rn(0.0f);
+        continue;
+      }
 #pragma unroll
       for (int s = 0; s < kSlices; ++s) {
         const int sh = 8 * (kSlices - 1 - s);
@@ -472,11 +481,13 @@ __device__ __forceinline__ void oz_tile(Smem& sh, const Gemm& g, const double* C
     const int cb0 = 32 * (warp >> 2);
     const int64_t gi = i0 + row;
     const uint32_t tl = tbase + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
-    if (gi < m && C != R)
-      for (int j = 0; j < 32; ++j) {
-        const int64_t gj = j0 + cb0 + j;
-        if (gj < n) R[gi + gj * ldr] = C[gi + gj * ldc];
-      }
+    // R is written once per product: the first product's drain writes R = C - P_0, a
+    // later one R -= P_1; mx is the largest |R| written by the last pass.  Each pass
+    // reads its values in chunks of 8 before storing any (the compiler cannot move a
+    // load above a store that may alias it, so element by element every access would
+    // be a memory round trip of its own).
+    bool wrote = false;
+    double mx = 0.0;
     // Leading weights of each column, over the chunks of a product:
     //   L = 2^16 S_2 + 2^8 S_3 + S_4   (S_w the integer sum of weight w),
     // so that their part of the product is 2^(e_row + e_col - 32) L.  A chunk adds
@@ -541,42 +552,57 @@ __device__ __forceinline__ void oz_tile(Smem& sh, const Gemm& g, const double* C
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(&sh.accempty);
         if (last) {
-          // R -= 2^(e_row + e_col - 32) (L + 2^16 T')
+          // R = (C, or R after an earlier product) - 2^(e_row + e_col - 32) (L + 2^16 T')
+          const double* src = wrote ? R : C;
+          const int64_t lds = wrote ? ldr : ldc;
+          mx = 0.0;
           if (gi < m)
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int64_t gj = j0 + cb0 + j;
-              const long long L = lacc[j];
-              if (gj < n && (L != 0 || tf[j] != 0.0f)) {
-                const double dv = fma(static_cast<double>(tf[j]), 0x1p16, static_cast<double>(L));
-                R[gi + gj * ldr] -= mul2(dv, erow + sh.ecol[p][cb0 + j] - 32);
+            for (int c8 = 0; c8 < 32; c8 += 8) {
+              double v[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int64_t gj = j0 + cb0 + c8 + j;
+                v[j] = gj < n ? src[gi + gj * lds] : 0.0;
+              }
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int64_t gj = j0 + cb0 + c8 + j;
+                if (gj < n) {
+                  const long long L = lacc[c8 + j];
+                  double r = v[j];
+                  if (L != 0 || tf[c8 + j] != 0.0f) {
+                    const double dv = fma(static_cast<double>(tf[c8 + j]), 0x1p16, static_cast<double>(L));
+                    r -= mul2(dv, erow + sh.ecol[p][cb0 + c8 + j] - 32);
+                  }
+                  R[gi + gj * ldr] = r;
+                  mx = fmax(mx, fabs(r));
+                }
               }
             }
+          wrote = true;
 #pragma unroll
           for (int j = 0; j < 32; ++j) lacc[j] = 0;
         }
       }
     }
+    if (ok && !wrote && gi < m)  // no product drained (no K blocks): R = C
+      for (int j = 0; j < 32; ++j) {
+        const int64_t gj = j0 + cb0 + j;
+        if (gj < n) {
+          const double r = C[gi + gj * ldc];
+          R[gi + gj * ldr] = r;
+          mx = fmax(mx, fabs(r));
+        }
+      }
     if (!ok) atomicCAS(err, 0, SYLV_ERR_TIMEOUT);
+    // ---- max |R| of the tile (from the last pass)
+    mx = warp_max(mx);
+    if (lane == 0 && rmax && !ld_volatile(err)) atomic_max_nonneg(rmax, mx);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
-  if (ld_volatile(err) || !rmax) return;
-  // ---- max |R| of the tile
-  if (warp < kEpiWarps) {
-    const int row = 32 * (warp & 3) + lane;
-    const int cb0 = 32 * (warp >> 2);
-    const int64_t gi = i0 + row;
-    double mx = 0.0;
-    if (gi < m)
-      for (int j = 0; j < 32; ++j) {
-        const int64_t gj = j0 + cb0 + j;
-        if (gj < n) mx = fmax(mx, fabs(R[gi + gj * ldr]));
-      }
-    mx = warp_max(mx);
-    if (lane == 0) atomic_max_nonneg(rmax, mx);
-  }
 }
 
 template <int MAXW>

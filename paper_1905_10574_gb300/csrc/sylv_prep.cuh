@@ -80,21 +80,35 @@ __global__ void k_norms(Work w) {
   const int cap = isA ? I.pmax : I.qmax;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int rs = bnd[rt], re = bnd[rt + 1];
-  double emax = 0.0;
+  // Per element only the sum's addition is floating point: the maximum and the finite
+  // test work on the bit patterns (a binary64 instruction costs 64 binary32 ones).  A
+  // binary32 tile sums in binary32 rounded upwards (an upper bound of its norm).
+  constexpr bool kF32 = sizeof(T) == 4;
+  using Bits = typename std::conditional<kF32, unsigned, unsigned long long>::type;
+  constexpr Bits kMag = kF32 ? Bits(0x7fffffffu) : Bits(0x7FFFFFFFFFFFFFFFull);
+  constexpr Bits kInf = kF32 ? Bits(0x7f800000u) : Bits(0x7FF0000000000000ull);
+  Bits emax = 0;
   bool bad = false;
   for (int ct = rt + warp; ct < ntile; ct += nwarp) {
     const int cs = bnd[ct], ce = bnd[ct + 1];
     double best = 0.0;
     for (int r = rs + lane; r < re; r += 32) {
-      double s = 0.0;
+      T s = T(0);
       for (int c = cs; c < ce; ++c) {
         if (r > c + 1) continue;
-        const double v = fabs(static_cast<double>(M[r + static_cast<int64_t>(c) * ld]));
-        if (!(v <= 1.7976931348623157e308)) bad = true;
-        s += v;
-        emax = fmax(emax, v);
+        Bits b;
+        memcpy(&b, &M[r + static_cast<int64_t>(c) * ld], sizeof(T));
+        b &= kMag;
+        if (b >= kInf) bad = true;
+        emax = b > emax ? b : emax;
+        T v;
+        memcpy(&v, &b, sizeof(T));
+        if constexpr (kF32)
+          s = __fadd_ru(s, v);
+        else
+          s += v;
       }
-      best = fmax(best, s);
+      best = fmax(best, static_cast<double>(s));
     }
     best = warp_max(best);
     const bool any_bad = __any_sync(0xffffffffu, bad);
@@ -107,8 +121,15 @@ __global__ void k_norms(Work w) {
     }
   }
   if (bad) set_err(st, SYLV_ERR_NONFINITE);
-  emax = warp_max(emax);
-  if (lane == 0) atomic_max_nonneg(isA ? &st->amax : &st->bmax, emax);
+  for (int o = 16; o > 0; o >>= 1) {
+    const Bits u = __shfl_xor_sync(0xffffffffu, emax, o);
+    emax = u > emax ? u : emax;
+  }
+  if (lane == 0 && emax && emax < kInf) {
+    T v;
+    memcpy(&v, &emax, sizeof(T));
+    atomic_max_nonneg(isA ? &st->amax : &st->bmax, static_cast<double>(v));
+  }
 }
 
 // ---------------------------------------------------------------------------

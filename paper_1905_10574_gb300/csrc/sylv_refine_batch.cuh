@@ -47,29 +47,41 @@ __device__ __forceinline__ int ref_sa(const RefEq& E) {
 
 // Visits every (r, c) of a rows x cols column-major array from the CTAs along grid
 // dimension x: a warp per column (coalesced along the rows), the warps of the grid
-// strided over the columns; no index division.
-template <typename F>
-__device__ __forceinline__ void for_each_rc(int64_t rows, int64_t cols, F&& f) {
+// strided over the columns; no index division.  Each lane loads four elements
+// (load(r, c), a value) before it stores any (store(r, c, value)): the compiler may
+// not move a load above a store that might alias it, so element by element every
+// access would wait for the one before.
+template <typename LD, typename ST>
+__device__ __forceinline__ void for_each_rc(int64_t rows, int64_t cols, LD&& load, ST&& store) {
   const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  const int lane = threadIdx.x & 31;
   for (int64_t c = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); c < cols; c += nw)
-    for (int64_t r = threadIdx.x & 31; r < rows; r += 32) f(r, c);
+    for (int64_t r0 = lane; r0 < rows; r0 += 128) {
+      decltype(load(r0, c)) v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (r0 + 32 * u < rows) v[u] = load(r0 + 32 * u, c);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (r0 + 32 * u < rows) store(r0 + 32 * u, c, v[u]);
+    }
 }
 
 // max |A| and max |B| over the quasi-triangular parts (equation blockIdx.y).
 __global__ void k_bref_maxabs(const RefEq* __restrict__ eq) {
   const RefEq E = eq[blockIdx.y];
-  double ma = 0.0, mb = 0.0;
-  for_each_rc(E.m, E.m, [&](int64_t r, int64_t c) {
-    if (r <= c + 1) ma = fmax(ma, fabs(E.A[r + c * E.lda]));
-  });
-  for_each_rc(E.n, E.n, [&](int64_t r, int64_t c) {
-    if (r <= c + 1) mb = fmax(mb, fabs(E.B[r + c * E.ldb]));
-  });
-  ma = warp_max(ma);
-  mb = warp_max(mb);
+  unsigned long long ma = 0, mb = 0;  // maxima as bit patterns of |value| (abs_key)
+  for_each_rc(
+      E.m, E.m, [&](int64_t r, int64_t c) { return r <= c + 1 ? E.A[r + c * E.lda] : 0.0; },
+      [&](int64_t, int64_t, double v) { ma = max(ma, abs_key(v)); });
+  for_each_rc(
+      E.n, E.n, [&](int64_t r, int64_t c) { return r <= c + 1 ? E.B[r + c * E.ldb] : 0.0; },
+      [&](int64_t, int64_t, double v) { mb = max(mb, abs_key(v)); });
+  ma = warp_max_key(ma);
+  mb = warp_max_key(mb);
   if ((threadIdx.x & 31) == 0) {
-    atomic_max_nonneg(E.slots, ma);
-    atomic_max_nonneg(E.slots + 1, mb);
+    atomicMax(E.slots, ma);
+    atomicMax(E.slots + 1, mb);
   }
 }
 
@@ -77,29 +89,34 @@ __global__ void k_bref_maxabs(const RefEq* __restrict__ eq) {
 __global__ void k_bref_split(const RefEq* __restrict__ eq) {
   const RefEq E = eq[blockIdx.y];
   const int s = ref_sa(E);
-  for_each_rc(E.m, E.m, [&](int64_t r, int64_t c) {
-    const DF d = split_df(r <= c + 1 ? mul2(E.A[r + c * E.lda], -s) : 0.0);
-    E.Ah[r + c * E.m] = d.hi;
-    E.Al[r + c * E.m] = d.lo;
-  });
-  for_each_rc(E.n, E.n, [&](int64_t r, int64_t c) {
-    const DF d = split_df(r <= c + 1 ? mul2(E.B[r + c * E.ldb], -s) : 0.0);
-    E.Bh[r + c * E.n] = d.hi;
-    E.Bl[r + c * E.n] = d.lo;
-  });
+  for_each_rc(
+      E.m, E.m, [&](int64_t r, int64_t c) { return r <= c + 1 ? E.A[r + c * E.lda] : 0.0; },
+      [&](int64_t r, int64_t c, double v) {
+        const DF d = split_df_mul2(v, -s);
+        E.Ah[r + c * E.m] = d.hi;
+        E.Al[r + c * E.m] = d.lo;
+      });
+  for_each_rc(
+      E.n, E.n, [&](int64_t r, int64_t c) { return r <= c + 1 ? E.B[r + c * E.ldb] : 0.0; },
+      [&](int64_t r, int64_t c, double v) {
+        const DF d = split_df_mul2(v, -s);
+        E.Bh[r + c * E.n] = d.hi;
+        E.Bl[r + c * E.n] = d.lo;
+      });
 }
 
 // First right-hand side: R = C (X = 0), and max |C|.
 __global__ void k_bref_copy_max(const RefEq* __restrict__ eq) {
   const RefEq E = eq[blockIdx.y];
-  double mx = 0.0;
-  for_each_rc(E.m, E.n, [&](int64_t r, int64_t c) {
-    const double v = E.C[r + c * E.ldc];
-    E.R[r + c * E.m] = v;
-    mx = fmax(mx, fabs(v));
-  });
-  mx = warp_max(mx);
-  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(ref_slot(E, 0, 0), mx);
+  unsigned long long mx = 0;
+  for_each_rc(
+      E.m, E.n, [&](int64_t r, int64_t c) { return E.C[r + c * E.ldc]; },
+      [&](int64_t r, int64_t c, double v) {
+        E.R[r + c * E.m] = v;
+        mx = max(mx, abs_key(v));
+      });
+  mx = warp_max_key(mx);
+  if ((threadIdx.x & 31) == 0) atomicMax(ref_slot(E, 0, 0), mx);
 }
 
 // Residual before correction `it` (>= 1), one 64 x 64 tile per CTA (equation
@@ -122,10 +139,9 @@ __global__ void k_bref_to_float(const RefEq* __restrict__ eq, int it) {
   const RefEq E = eq[blockIdx.y];
   if (ref_done(E)) return;
   const int s = norm_exp(ref_slot(E, it, 0));
-  for_each_rc(E.m, E.n, [&](int64_t r, int64_t c) {
-    const int64_t t = r + c * E.m;
-    E.Rf[t] = static_cast<float>(mul2(E.R[t], -s));
-  });
+  for_each_rc(
+      E.m, E.n, [&](int64_t r, int64_t c) { return E.R[r + c * E.m]; },
+      [&](int64_t r, int64_t c, double v) { E.Rf[r + c * E.m] = f32_mul2(v, -s); });
 }
 
 // X += D per solved tile (the correction solve left tile (k,l) of D' = 2^(sa-sr) D as
@@ -145,21 +161,35 @@ __global__ void k_bref_accumulate(Work wf, const RefEq* __restrict__ eq, int it)
     const int32_t* rb = wf.ibuf + I.rb;
     const int32_t* cb = wf.ibuf + I.cb;
     const int r0 = rb[k], mt = rb[k + 1] - r0, c0 = cb[l], nt = cb[l + 1] - c0;
-    double md = 0.0, mxv = 0.0;
-    for (int i = threadIdx.x; i < mt * nt; i += blockDim.x) {
-      const int64_t x = (r0 + i % mt) + static_cast<int64_t>(c0 + i / mt) * E.m;
-      const double dv = mul2(static_cast<double>(E.Rf[x]), sr - sa - e);
-      const double xv = E.X[x] + dv;
-      E.X[x] = xv;
-      E.D[x] = dv;
-      md = fmax(md, fabs(dv));
-      mxv = fmax(mxv, fabs(xv));
+    unsigned long long md = 0, mxv = 0;  // abs_key maxima
+    // loads of four elements before their stores (see for_each_rc)
+    for (int i0 = threadIdx.x; i0 < mt * nt; i0 += 4 * blockDim.x) {
+      float rf[4];
+      double xo[4];
+      int64_t xi[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        xi[u] = i < mt * nt ? (r0 + i % mt) + static_cast<int64_t>(c0 + i / mt) * E.m : -1;
+        rf[u] = xi[u] >= 0 ? E.Rf[xi[u]] : 0.0f;
+        xo[u] = xi[u] >= 0 ? E.X[xi[u]] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (xi[u] >= 0) {
+          const double dv = f64_mul2(rf[u], sr - sa - e);
+          const double xv = xo[u] + dv;
+          E.X[xi[u]] = xv;
+          E.D[xi[u]] = dv;
+          md = max(md, abs_key(dv));
+          mxv = max(mxv, abs_key(xv));
+        }
     }
-    md = warp_max(md);
-    mxv = warp_max(mxv);
+    md = warp_max_key(md);
+    mxv = warp_max_key(mxv);
     if ((threadIdx.x & 31) == 0) {
-      atomic_max_nonneg(ref_slot(E, it, 1), md);
-      atomic_max_nonneg(ref_slot(E, it, 2), mxv);
+      atomicMax(ref_slot(E, it, 1), md);
+      atomicMax(ref_slot(E, it, 2), mxv);
     }
   }
 }
@@ -185,7 +215,9 @@ __global__ void k_bref_check(const RefEq* __restrict__ eq, int count, int it, do
 // C = X and the result record of each equation (equation blockIdx.y).
 __global__ void k_bref_finish(const RefEq* __restrict__ eq, sylv_result* res) {
   const RefEq E = eq[blockIdx.y];
-  for_each_rc(E.m, E.n, [&](int64_t r, int64_t c) { E.C[r + c * E.ldc] = E.X[r + c * E.m]; });
+  for_each_rc(
+      E.m, E.n, [&](int64_t r, int64_t c) { return E.X[r + c * E.m]; },
+      [&](int64_t r, int64_t c, double v) { E.C[r + c * E.ldc] = v; });
   if (blockIdx.x == 0 && threadIdx.x == 0) refine_result_one(E.rs, res + blockIdx.y);
 }
 

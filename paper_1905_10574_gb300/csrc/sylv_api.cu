@@ -1108,18 +1108,25 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
     std::vector<size_t> o_oz(count);
     std::vector<OzTask> oz_tasks;
     size_t off_oz = 0, off_task = 0;
+    // Equations of order above kOzMin take the tensor-core residual; smaller ones, whose
+    // 128 x 64 tiles would be mostly padding and whose K ranges are short, keep the
+    // double-float kernel (many CTAs per SM where the tensor-core kernel has one).
+    constexpr int64_t kOzMin = 128;
     const bool oz = refine && residual_on_tensor_cores();
+    std::vector<char> use_oz(count, 0);
     if (oz) {
       for (int i = 0; i < count; ++i) {
+        use_oz[i] = std::max(sh[i].m, sh[i].n) > kOzMin;
         o_oz[i] = off;
-        off = align_up(off + oz_workspace_bytes(sh[i].m, sh[i].n));
+        if (use_oz[i]) off = align_up(off + oz_workspace_bytes(sh[i].m, sh[i].n));
       }
       // larger equations first: their tiles hold the longest K ranges
       std::vector<int> ordr(count);
       for (int i = 0; i < count; ++i) ordr[i] = i;
       std::stable_sort(ordr.begin(), ordr.end(),
                        [&](int a, int b) { return sh[a].m + sh[a].n > sh[b].m + sh[b].n; });
-      for (int i : ordr) oz_batch_tasks(i, sh[i].m, sh[i].n, &oz_tasks);
+      for (int i : ordr)
+        if (use_oz[i]) oz_batch_tasks(i, sh[i].m, sh[i].n, &oz_tasks);
       off_oz = off;
       off = align_up(off + sizeof(OzBatchEq) * count);
       off_task = off;
@@ -1230,7 +1237,10 @@ int sylv_batch_create_tiles(sylv_batch_plan** plan, int32_t count, const int64_t
       if (oz) {
         std::vector<OzBatchEq> q(count);
         for (int i = 0; i < count; ++i) {
-          const RefEq& e = re[i];
+          RefEq& e = re[i];
+          e.oz = use_oz[i];
+          q[i].active = use_oz[i];
+          q[i].pad = 0;
           oz_carve(P->ws + o_oz[i], e.m, e.n, &q[i].b);
           q[i].A = e.A;
           q[i].lda = e.lda;
@@ -1311,10 +1321,12 @@ static int execute_refine(sylv_batch_plan* P, cudaStream_t s) {
       k_bref_copy_max<<<dim3(eg, count), 256, 0, s>>>(P->dref);
     } else if (it == 1 && P->doz) {
       // first residual of the solution, binary64-accurate: error-free bf16 splitting on
-      // the tensor cores (double-float products on the FP32 pipe under SYLV_RESIDUAL=df)
+      // the tensor cores for the larger equations, double-float products on the FP32
+      // pipe for the others (and for all of them under SYLV_RESIDUAL=df)
       if (oz_batch_split(P->doz, count, 0x6u, P->maxN, s) != cudaSuccess) return SYLV_ERR_CUDA;
       if (oz_batch_residual(P->doz, P->dtask, P->noz_tasks, &P->w.ctrl->err, P->w.timeout_ns, s) != cudaSuccess)
         return SYLV_ERR_CUDA;
+      k_bref_residual<<<dim3(nt64, nt64, count), 256, 0, s>>>(P->dref, it);
     } else {
       k_bref_residual<<<dim3(nt64, nt64, count), 256, 0, s>>>(P->dref, it);
     }

@@ -102,6 +102,10 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
 __device__ __forceinline__ double bits_to_double(unsigned long long b) {
   return __longlong_as_double(static_cast<long long>(b));
 }
+// x + y, rounded upwards in binary32 (sums that must bound a norm from above); plain
+// binary64 addition otherwise.
+__device__ __forceinline__ double add_up(double x, double y) { return x + y; }
+__device__ __forceinline__ float add_up(float x, float y) { return __fadd_ru(x, y); }
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
@@ -325,7 +329,7 @@ struct Lim<float> {
 // norm, which sends every solve of the pair to the guarded path.  Returns the
 // packed interchanges.
 template <int MA, int NB, typename CT = double>
-__device__ __forceinline__ int pair_prepare(const double (&a)[4], const double (&b)[4], double smin, CT* out) {
+__device__ __forceinline__ int pair_prepare(const CT (&a)[4], const CT (&b)[4], double smin, CT* out) {
   constexpr int S = MA * NB;
   const CT sm = static_cast<CT>(smin);
   CT M[S][S];
@@ -333,10 +337,10 @@ __device__ __forceinline__ int pair_prepare(const double (&a)[4], const double (
   for (int u = 0; u < S; ++u)
 #pragma unroll
     for (int v = 0; v < S; ++v) {
-      double e = 0.0;
+      CT e = CT(0);
       if (u / MA == v / MA) e += a[(u % MA) + 2 * (v % MA)];
       if (u % MA == v % MA) e += b[(v / MA) + 2 * (u / MA)];
-      M[u][v] = static_cast<CT>(e);
+      M[u][v] = e;
     }
   int cperm[S];
 #pragma unroll
@@ -550,11 +554,10 @@ __device__ inline int merge_blocks(short* blk, short* start, int n, int nblk, un
 // Writes Minv row-major and ||Minv||_inf (infinity if not finite) in OutT; returns
 // bit 16 if a part raised its pivot.
 template <typename CT>
-__device__ __forceinline__ int pair_quad_prepare(const double (&a)[4], const double (&b)[4], double smin, CT* out) {
+__device__ __forceinline__ int pair_quad_prepare(const CT (&a)[4], const CT (&b)[4], double smin, CT* out) {
   int flag = 0;
   const CT sm = static_cast<CT>(smin);
-  auto inv = [&](double dd) {
-    CT d = static_cast<CT>(dd);
+  auto inv = [&](CT d) {
     if (fabs(d) < sm) {
       d = sm;
       flag = 1 << 16;
@@ -562,7 +565,7 @@ __device__ __forceinline__ int pair_quad_prepare(const double (&a)[4], const dou
     return CT(1) / d;
   };
   const CT i00 = inv(a[0] + b[0]), i10 = inv(a[3] + b[0]), i01 = inv(a[0] + b[3]), i11 = inv(a[3] + b[3]);
-  const CT a12 = static_cast<CT>(a[2]), b12 = static_cast<CT>(b[2]);
+  const CT a12 = a[2], b12 = b[2];
   const CT m[16] = {i00,
                         -a12 * i00 * i10,
                         CT(0),
@@ -603,15 +606,15 @@ __device__ __forceinline__ int pair_quad_prepare(const double (&a)[4], const dou
 // Minv = [[Il, 0], [-b12 Ir Il, Ir]] over (left, right) columns.  Each part has the
 // other side's whole block (1x1 or 2x2).  Same output layout as pair_prepare.
 template <typename CT>
-__device__ __noinline__ int pair_half_prepare(int ma, int nb, bool pa, double a0_, double a1_, double a2_, double a3_,
-                                              double b0_, double b1_, double b2_, double b3_, double smin, CT* out) {
+__device__ __noinline__ int pair_half_prepare(int ma, int nb, bool pa, CT a0_, CT a1_, CT a2_, CT a3_, CT b0_, CT b1_,
+                                              CT b2_, CT b3_, double smin, CT* out) {
   // The blocks' entries arrive as scalars, so the caller's arrays stay in registers.
-  const double a[4] = {a0_, a1_, a2_, a3_}, b[4] = {b0_, b1_, b2_, b3_};
+  const CT a[4] = {a0_, a1_, a2_, a3_}, b[4] = {b0_, b1_, b2_, b3_};
   const int s = ma * nb;
   const int h = pa ? nb : ma;  // size of each part's system (the other side's block)
   CT P0[5], P1[5];              // part inverses (<= 2 x 2, row-major) and norms
-  double a0[4] = {0.0, 0.0, 0.0, 0.0}, a1[4] = {0.0, 0.0, 0.0, 0.0};
-  double b0[4] = {0.0, 0.0, 0.0, 0.0}, b1[4] = {0.0, 0.0, 0.0, 0.0};
+  CT a0[4] = {CT(0), CT(0), CT(0), CT(0)}, a1[4] = {CT(0), CT(0), CT(0), CT(0)};
+  CT b0[4] = {CT(0), CT(0), CT(0), CT(0)}, b1[4] = {CT(0), CT(0), CT(0), CT(0)};
   int flags;
   if (pa) {  // part 0: top row (a00), part 1: bottom row (a11); both with B
     a0[0] = a[0];
@@ -626,7 +629,7 @@ __device__ __noinline__ int pair_half_prepare(int ma, int nb, bool pa, double a0
   }
   // Coupled block: pseudo A: top += -a12 It Ib (rows of the top part, columns of the
   // bottom part); pseudo B: right += -b12 Ir Il.
-  const CT cpl = static_cast<CT>(pa ? a[2] : b[2]);
+  const CT cpl = pa ? a[2] : b[2];
   CT m[4][4];
 #pragma unroll
   for (int e = 0; e < 4; ++e)
@@ -793,18 +796,18 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
       const int kb = idx / TT, r = idx % TT;
       const int ra = sh.astart[kb], re = sh.astart[kb + 1];
       if (r < ra) {
-        double sum = 0.0;
-        for (int i = ra; i < re; ++i) sum += fabs(static_cast<double>(Ak[r + i * LDY]));
-        atomicMax(&sh.acolmax[kb], abs_bits(sum));
+        T sum = T(0);  // binary32 tiles: summed rounded upwards, an upper bound
+        for (int i = ra; i < re; ++i) sum = add_up(sum, fabs(Ak[r + i * LDY]));
+        atomicMax(&sh.acolmax[kb], abs_bits(static_cast<double>(sum)));
       }
     }
     for (int idx = tid; idx < qb * TT; idx += kThreads) {
       const int lb = idx / TT, c = idx % TT;
       const int j0 = sh.bstart[lb], j1 = sh.bstart[lb + 1];
       if (c >= j1 && c < nt) {
-        double sum = 0.0;
-        for (int j = j0; j < j1; ++j) sum += fabs(static_cast<double>(Bk[j + c * LDY]));
-        atomicMax(&sh.bcolmax[lb], abs_bits(sum));
+        T sum = T(0);
+        for (int j = j0; j < j1; ++j) sum = add_up(sum, fabs(Bk[j + c * LDY]));
+        atomicMax(&sh.bcolmax[lb], abs_bits(static_cast<double>(sum)));
       }
     }
   }
@@ -838,11 +841,13 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
     const int kb = sh.aord[ao + r / nbk], lb = sh.bord[bo + r % nbk];
     const int ra = sh.astart[kb], ma = sh.astart[kb + 1] - ra;
     const int cb0 = sh.bstart[lb], nb = sh.bstart[lb + 1] - cb0;
-    double a[4], b[4];
+    // the blocks' entries in the store's precision (no binary64 instruction in the
+    // binary32 kernel, where each would cost 64 binary32 ones)
+    FactT a[4], b[4];
     for (int i = 0; i < 2; ++i)
       for (int j = 0; j < 2; ++j) {
-        a[i + 2 * j] = (i < ma && j < ma) ? static_cast<double>(Ak[(ra + i) + (ra + j) * LDY]) : 0.0;
-        b[i + 2 * j] = (i < nb && j < nb) ? static_cast<double>(Bk[(cb0 + i) + (cb0 + j) * LDY]) : 0.0;
+        a[i + 2 * j] = (i < ma && j < ma) ? static_cast<FactT>(Ak[(ra + i) + (ra + j) * LDY]) : FactT(0);
+        b[i + 2 * j] = (i < nb && j < nb) ? static_cast<FactT>(Bk[(cb0 + i) + (cb0 + j) * LDY]) : FactT(0);
       }
     const bool psa = kMerge && ((sh.apsd >> kb) & 1u), psb = kMerge && ((sh.bpsd >> lb) & 1u);
     FactT* fo = fact + pair_offset(sh, kb, lb, ma);
@@ -1601,6 +1606,25 @@ __device__ __forceinline__ void gemm_sub_split4(T (&part)[2][2], const T* L, con
   }
 }
 
+// Infinity norm of the tile in sh.Y (mt x nt) into sh.umax (bit pattern, atomic
+// maximum; sh.umax zeroed before).  A warp per row, lanes across the columns and a
+// shuffle tree, so the sum is a short dependency chain; the maximum is taken on the
+// bit patterns of the non-negative sums, so a NaN row still shows.  Binary32 tiles
+// sum in binary32 rounded upwards (an upper bound), without binary64 instructions.
+template <int TT, typename T>
+__device__ __forceinline__ void tile_norm_max(DagSmem<TT, T>& sh, int mt, int nt) {
+  constexpr int LDY = DagSmem<TT, T>::LDY;
+  const int wq = threadIdx.x >> 5, lq = threadIdx.x & 31;
+  T mx = T(0);
+  for (int r = wq; r < mt; r += kThreads / 32) {
+    T s = T(0);
+    for (int c = lq; c < nt; c += 32) s = add_up(s, fabs(sh.Y[r + c * LDY]));
+    for (int o = 16; o > 0; o >>= 1) s = add_up(s, __shfl_xor_sync(0xffffffffu, s, o));
+    mx = mag_bits(s) > mag_bits(mx) ? s : mx;
+  }
+  if (lq == 0 && mag_bits(mx)) atomicMax(&sh.umax, abs_bits(static_cast<double>(mx)));
+}
+
 template <int TT, typename T, bool ROBUST>
 __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
   static_assert(TT == 32 || TT == 64, "tile capacity");
@@ -1714,11 +1738,7 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
     if (tid == 0) sh.umax = 0ull;
     __syncthreads();
     if (ROBUST) {
-      for (int r = tid; r < mt; r += kThreads) {
-        double s = 0.0;
-        for (int c = 0; c < nt; ++c) s += fabs(static_cast<double>(sh.Y[r + c * LDY]));
-        atomic_max_nonneg(&sh.umax, s);
-      }
+      tile_norm_max<TT, T>(sh, mt, nt);
       __syncthreads();
       if (tid == 0) {
         double nb = __longlong_as_double(static_cast<long long>(sh.umax));
@@ -2112,18 +2132,7 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
     // patterns of the non-negative sums, so a NaN row still reaches the check below.
     if (tid == 0) sh.umax = 0ull;
     __syncthreads();
-    {
-      const int wq = tid >> 5, lq = tid & 31;
-      unsigned long long mxb = 0ull;
-      for (int r = wq; r < mt; r += kThreads / 32) {
-        double s = 0.0;
-        for (int c = lq; c < nt; c += 32) s += fabs(static_cast<double>(sh.Y[r + c * LDY]));
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(s));
-        mxb = b > mxb ? b : mxb;
-      }
-      if (lq == 0 && mxb) atomicMax(&sh.umax, mxb);
-    }
+    tile_norm_max<TT, T>(sh, mt, nt);
     for (int idx = tid; idx < mt * nt; idx += kThreads) {
       const int r = idx % mt, c = idx / mt;
       C[(r0 + r) + (int64_t)(c0 + c) * I.ldc] = sh.Y[r + c * LDY];

@@ -415,8 +415,9 @@ __device__ __forceinline__ DF split_df_mul2(double v, int e) {
     r += 1;
     rem -= 0x20000000;  // the remainder below the rounded-up high part
   }
-  // v 2^e - hi = +-rem 2^(Ef - 150): an integer below 2^29 converted with one rounding
-  const float lo = mul2(static_cast<float>(sign ? -rem : rem), Ef - 150);
+  // v 2^e - hi = +-rem 2^(Ef - 179) (units of the binary64 significand's last bit, 29
+  // below binary32's 2^(Ef - 150)): an integer below 2^29 converted with one rounding
+  const float lo = mul2(static_cast<float>(sign ? -rem : rem), Ef - 179);
   return DF{__uint_as_float(r | sign), lo};
 }
 __device__ __forceinline__ double f64_mul2(float f, int e) {

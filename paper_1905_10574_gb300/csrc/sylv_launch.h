@@ -64,6 +64,8 @@ struct OzBatchEq {
   int64_t ldr;
   unsigned long long* rmax;  // max |R| of the equation (atomic maximum of the bit patterns)
   const int* skip;           // nonzero: the equation is passed over (converged)
+  int32_t active;            // 0: the equation takes another residual (the kernels pass it over)
+  int32_t pad;
 };
 // One 128 x 64 output tile of one equation.
 struct OzTask {

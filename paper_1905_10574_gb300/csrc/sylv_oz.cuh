@@ -659,7 +659,7 @@ __device__ __forceinline__ View oz_view(const OzBatchEq& q, int which) {
 // Per-row exponents of operand `which` of every equation (equation blockIdx.y).
 __global__ void k_oz_rowexp_batched(const OzBatchEq* __restrict__ eqs, int which) {
   const OzBatchEq& q = eqs[blockIdx.y];
-  if (q.skip && ld_volatile(q.skip)) return;
+  if (!q.active || (q.skip && ld_volatile(q.skip))) return;
   const Packed P = oz_packed(q, which);
   oz_rowexp(oz_view(q, which), P.e, P.RB * P.R);
 }
@@ -668,7 +668,7 @@ __global__ void k_oz_rowexp_batched(const OzBatchEq* __restrict__ eqs, int which
 __global__ void __launch_bounds__(256) k_oz_split_batched(const OzBatchEq* __restrict__ eqs, int which) {
   __shared__ double tile[BM * (BK + 1)];
   const OzBatchEq& q = eqs[blockIdx.y];
-  if (q.skip && ld_volatile(q.skip)) return;
+  if (!q.active || (q.skip && ld_volatile(q.skip))) return;
   oz_split(oz_view(q, which), oz_packed(q, which), tile);
 }
 

@@ -36,6 +36,8 @@ struct RefEq {
   double* D;
   unsigned long long* slots;  // [0] max|A|, [1] max|B|, then (max|R|, max|D|, max|X|) per correction
   RefineState* rs;
+  int32_t oz;                 // the first residual runs on the tensor cores (k_oz_gemm_batched)
+  int32_t pad;
 };
 
 __device__ __forceinline__ unsigned long long* ref_slot(const RefEq& E, int it, int k) { return E.slots + 2 + 3 * it + k; }
@@ -125,7 +127,7 @@ __global__ void k_bref_copy_max(const RefEq* __restrict__ eq) {
 __global__ void __launch_bounds__(256) k_bref_residual(const RefEq* __restrict__ eq, int it) {
   const RefEq E = eq[blockIdx.z];
   const int64_t i0 = static_cast<int64_t>(blockIdx.x) * GT, j0 = static_cast<int64_t>(blockIdx.y) * GT;
-  if (i0 >= E.m || j0 >= E.n || ref_done(E)) return;
+  if (i0 >= E.m || j0 >= E.n || ref_done(E) || (it == 1 && E.oz)) return;
   if (it == 1)
     residual_df_tile(E.Ah, E.Al, E.m, E.Bh, E.Bl, E.n, E.C, E.ldc, E.X, E.m, E.R, E.m, E.m, E.n, E.slots,
                      E.slots + 1, ref_slot(E, it - 1, 2), ref_slot(E, it, 0), i0, j0);

@@ -83,7 +83,7 @@ struct DagSmem {
   short astart[TT + 1], bstart[TT + 1];
   short aord[TT], bord[TT];           // blocks grouped by kind for the pair preparation (order_blocks)
   int acnt[3], bcnt[3];               // blocks of each kind: merged pseudo, 2x2, 1x1
-  unsigned apsd, bpsd;                // diagonal solve: blocks that are two merged 1x1 blocks (bit per block)
+  unsigned long long apsd, bpsd;      // diagonal solve: blocks that are two merged 1x1 blocks (bit per block)
   unsigned long long umax;
   unsigned long long stage_bar;        // mbarrier of the bulk-copy staging (packed tiles)
   double nb_acc;
@@ -508,14 +508,14 @@ __device__ inline int scan_blocks(const T* M, int N, short* blk, short* start, i
   return count;
 }
 
-// Pseudo blocks for the diagonal-tile solve (tile capacity <= 32): consecutive 1x1
+// Pseudo blocks for the diagonal-tile solve: consecutive 1x1
 // blocks are merged in pairs, so that the wavefront over the tile's blocks takes about
 // half as many steps (each a chain of dependent FP64 operations and block barriers).
 // A merged pair is solved as one small system whose inverse is composed from the
 // inverses of its parts (pair_quad_prepare, pair_half_prepare), so a near-singular
 // part raises exactly the pivot it raises on its own.  One warp, nblk <= 32; rewrites blk and
 // start in place, returns the new count and sets *pseudo (bit per new block).
-__device__ inline int merge_blocks(short* blk, short* start, int n, int nblk, unsigned* pseudo, int lane) {
+__device__ inline int merge_blocks(short* blk, short* start, int n, int nblk, unsigned long long* pseudo, int lane) {
   const int b = lane;
   const bool valid = b < nblk;
   const int sz = valid ? start[b + 1] - start[b] : 0;
@@ -540,6 +540,42 @@ __device__ inline int merge_blocks(short* blk, short* start, int n, int nblk, un
   if (lane == 0) {
     start[count] = static_cast<short>(n);
     *pseudo = pm;
+  }
+  __syncwarp();
+  return count;
+}
+
+// The same merge for up to 64 blocks (tile capacity 64): lane 0 walks the blocks (a
+// run of 1x1 blocks pairs from its first block, as above) compacting start in place,
+// then the warp renumbers the rows.
+__device__ inline int merge_blocks_long(short* blk, short* start, int n, int nblk, unsigned long long* pseudo,
+                                        int lane) {
+  int count = 0;
+  if (lane == 0) {
+    unsigned long long pm = 0;
+    for (int b = 0; b < nblk;) {
+      const short s0 = start[b];
+      const bool pair = start[b + 1] - s0 == 1 && b + 1 < nblk && start[b + 2] - start[b + 1] == 1;
+      start[count] = s0;  // count <= b: the entries still to be read lie above it
+      if (pair) pm |= 1ull << count;
+      b += pair ? 2 : 1;
+      ++count;
+    }
+    start[count] = static_cast<short>(n);
+    *pseudo = pm;
+  }
+  count = __shfl_sync(0xffffffffu, count, 0);
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {  // the last block starting at or before row i
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (start[mid] <= i)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    blk[i] = static_cast<short>(lo);
   }
   __syncwarp();
   return count;
@@ -680,12 +716,13 @@ __device__ __noinline__ int pair_half_prepare(int ma, int nb, bool pa, CT a0_, C
 // code in turn, which on the 1/64-rate FP64 pipe costs as much as the updates of
 // several producers; with pairs enumerated kind by kind a warp mostly runs one.  One
 // warp; writes ord[0..nblk) and cnt[3].
-__device__ inline void order_blocks(const short* start, int nblk, unsigned pseudo, short* ord, int* cnt, int lane) {
+__device__ inline void order_blocks(const short* start, int nblk, unsigned long long pseudo, short* ord, int* cnt,
+                                    int lane) {
   int n[3] = {0, 0, 0};
   for (int b0 = 0; b0 < nblk; b0 += 32) {
     const int b = b0 + lane;
     const bool v = b < nblk;
-    const bool ps = v && b < 32 && ((pseudo >> b) & 1u);
+    const bool ps = v && b < 64 && ((pseudo >> b) & 1ull);
     const int kind = !v ? 3 : ps ? 0 : (start[b + 1] - start[b] == 2 ? 1 : 2);
 #pragma unroll
     for (int t = 0; t < 3; ++t) n[t] += __popc(__ballot_sync(0xffffffffu, kind == t));
@@ -695,7 +732,7 @@ __device__ inline void order_blocks(const short* start, int nblk, unsigned pseud
   for (int b0 = 0; b0 < nblk; b0 += 32) {
     const int b = b0 + lane;
     const bool v = b < nblk;
-    const bool ps = v && b < 32 && ((pseudo >> b) & 1u);
+    const bool ps = v && b < 64 && ((pseudo >> b) & 1ull);
     const int kind = !v ? 3 : ps ? 0 : (start[b + 1] - start[b] == 2 ? 1 : 2);
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
@@ -746,14 +783,16 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
     sh.bcolmax[i] = 0ull;
   }
   __syncthreads();
-  // Blocks of A_kk and B_ll; for tile capacity 32 consecutive 1x1 blocks are merged in
-  // pairs (merge_blocks).  Without a B term the columns are independent and stay 1x1.
-  constexpr bool kMerge = SYLV_MERGE_DIAG && TT <= 32;
+  // Blocks of A_kk and B_ll; consecutive 1x1 blocks are merged in pairs (merge_blocks,
+  // merge_blocks_long at tile capacity 64).  Without a B term the columns are
+  // independent and stay 1x1.
+  constexpr bool kMerge = SYLV_MERGE_DIAG;
   if (warp == 0) {
     int pb = scan_blocks<T, LDY>(Ak, mt, sh.rowblk, sh.astart, lane);
     if (kMerge) {
       __syncwarp();
-      pb = merge_blocks(sh.rowblk, sh.astart, mt, pb, &sh.apsd, lane);
+      pb = TT <= 32 ? merge_blocks(sh.rowblk, sh.astart, mt, pb, &sh.apsd, lane)
+                    : merge_blocks_long(sh.rowblk, sh.astart, mt, pb, &sh.apsd, lane);
     } else if (lane == 0) {
       sh.apsd = 0;
     }
@@ -762,7 +801,8 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
     int qb = scan_blocks<T, LDY>(Bk, nt, sh.colblk, sh.bstart, lane);
     if (kMerge && B) {
       __syncwarp();
-      qb = merge_blocks(sh.colblk, sh.bstart, nt, qb, &sh.bpsd, lane);
+      qb = TT <= 32 ? merge_blocks(sh.colblk, sh.bstart, nt, qb, &sh.bpsd, lane)
+                    : merge_blocks_long(sh.colblk, sh.bstart, nt, qb, &sh.bpsd, lane);
     } else if (lane == 0) {
       sh.bpsd = 0;
     }
@@ -771,9 +811,9 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
   __syncthreads();
   const int pb = sh.pb, qb = sh.qb;
   if (warp == 0)
-    order_blocks(sh.astart, pb, kMerge ? sh.apsd : 0u, sh.aord, sh.acnt, lane);
+    order_blocks(sh.astart, pb, kMerge ? sh.apsd : 0ull, sh.aord, sh.acnt, lane);
   else if (warp == 1)
-    order_blocks(sh.bstart, qb, kMerge ? sh.bpsd : 0u, sh.bord, sh.bcnt, lane);
+    order_blocks(sh.bstart, qb, kMerge ? sh.bpsd : 0ull, sh.bord, sh.bcnt, lane);
   if (tid == 0) {
     int acc = 0;
     for (int lb = 0; lb < qb; ++lb) {
@@ -849,7 +889,7 @@ __device__ void diag_prepare(DagSmem<TT, T>& sh, const T* A, int64_t lda, const 
         a[i + 2 * j] = (i < ma && j < ma) ? static_cast<FactT>(Ak[(ra + i) + (ra + j) * LDY]) : FactT(0);
         b[i + 2 * j] = (i < nb && j < nb) ? static_cast<FactT>(Bk[(cb0 + i) + (cb0 + j) * LDY]) : FactT(0);
       }
-    const bool psa = kMerge && ((sh.apsd >> kb) & 1u), psb = kMerge && ((sh.bpsd >> lb) & 1u);
+    const bool psa = kMerge && ((sh.apsd >> kb) & 1ull), psb = kMerge && ((sh.bpsd >> lb) & 1ull);
     FactT* fo = fact + pair_offset(sh, kb, lb, ma);
     // Computed in the store's precision (binary32 for the binary32 kernel: an inverse
     // whose norm overflows it is infinite, which sends the pair to the guarded path).
@@ -2102,6 +2142,17 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
             acc[i][j] = t;
             acc_lo[i][j] += e;
           }
+      } else if (packed) {
+        // Producers sit in fixed TT-row slots, zero-padded: each slot's product runs over
+        // its producer's own K extent only, and a thread whose columns lie beyond the
+        // tile (whole warps once nt <= 4 w) skips it: the padding adds only zeros.
+        if (cbase < nt) {
+          const int g = sh.gn;
+          for (int u = 0; u < g; ++u) {
+            const int off = u * TT * DagSmem<TT, T>::LDG;
+            gemm_sub<TT, T, MR, NR>(acc, sh.L + off, sh.R + off, sh.gk[u], rbase, cbase);
+          }
+        }
       } else {
         gemm_sub<TT, T, MR, NR>(acc, sh.L, sh.R, sh.gktot, rbase, cbase);
       }

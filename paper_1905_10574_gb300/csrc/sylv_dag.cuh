@@ -1602,8 +1602,8 @@ __device__ __forceinline__ void gemm_sub(T (&acc)[MR][NR], const T* L, const T* 
 // block in group order (deterministic).  part receives -sum_k L[k, r] R[k, c], as
 // gemm_sub does; the caller's barrier after the accumulation frees kred again.
 template <int TT, typename T>
-__device__ __forceinline__ void gemm_sub_split4(T (&part)[2][2], const T* L, const T* R, int kdim, int rbase,
-                                                int cbase, T* kred) {
+__device__ __forceinline__ void gemm_sub_split4(T (&part)[2][2], const T* L, const T* R, const int* gk, int ng,
+                                                int rbase, int cbase, T* kred) {
   static_assert(sizeof(T) == 4 && TT == 32 && kThreads == 256, "binary32, tile 32, 256 threads");
   constexpr int LDG = DagSmem<TT, T>::LDG;
   static_assert(LDG % 2 == 0, "paired operand reads");
@@ -1615,18 +1615,23 @@ __device__ __forceinline__ void gemm_sub_split4(T (&part)[2][2], const T* L, con
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) p[i][j] = T(0);
+  // producers in TT-row slots: slot u runs over its own K extent gk[u] (TT is a
+  // multiple of 4, so every group keeps its residue of k; the padding adds only zeros)
+  for (int u = 0; u < ng; ++u) {
+    const int k1 = u * TT + gk[u];
 #pragma unroll 2
-  for (int kk = g; kk < kdim; kk += 4) {
-    const float2 a01 = *reinterpret_cast<const float2*>(&L[kk * LDG + r4]);
-    const float2 a23 = *reinterpret_cast<const float2*>(&L[kk * LDG + r4 + 2]);
-    const float2 b01 = *reinterpret_cast<const float2*>(&R[kk * LDG + c4]);
-    const float2 b23 = *reinterpret_cast<const float2*>(&R[kk * LDG + c4 + 2]);
-    const T a[4] = {a01.x, a01.y, a23.x, a23.y};
-    const T b[4] = {b01.x, b01.y, b23.x, b23.y};
+    for (int kk = u * TT + g; kk < k1; kk += 4) {
+      const float2 a01 = *reinterpret_cast<const float2*>(&L[kk * LDG + r4]);
+      const float2 a23 = *reinterpret_cast<const float2*>(&L[kk * LDG + r4 + 2]);
+      const float2 b01 = *reinterpret_cast<const float2*>(&R[kk * LDG + c4]);
+      const float2 b23 = *reinterpret_cast<const float2*>(&R[kk * LDG + c4 + 2]);
+      const T a[4] = {a01.x, a01.y, a23.x, a23.y};
+      const T b[4] = {b01.x, b01.y, b23.x, b23.y};
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) p[i][j] = fma(-a[i], b[j], p[i][j]);
+        for (int j = 0; j < 4; ++j) p[i][j] = fma(-a[i], b[j], p[i][j]);
+    }
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j)
@@ -2128,8 +2133,14 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
         for (int i = 0; i < MR; ++i)
 #pragma unroll
           for (int j = 0; j < NR; ++j) part[i][j] = T(0);
-        if constexpr (DagSmem<TT, T>::kSplitK)
-          gemm_sub_split4<TT, T>(part, sh.L, sh.R, sh.gktot, rbase, cbase, sh.kred);
+        if constexpr (DagSmem<TT, T>::kSplitK) {
+          // packed producers sit in TT-row slots; staged ones back to back (one slot)
+          const int one = sh.gktot;
+          if (packed)
+            gemm_sub_split4<TT, T>(part, sh.L, sh.R, sh.gk, sh.gn, rbase, cbase, sh.kred);
+          else
+            gemm_sub_split4<TT, T>(part, sh.L, sh.R, &one, 1, rbase, cbase, sh.kred);
+        }
         else
           gemm_sub<TT, T, MR, NR>(part, sh.L, sh.R, sh.gktot, rbase, cbase);
 #pragma unroll

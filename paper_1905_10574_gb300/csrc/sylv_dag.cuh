@@ -321,6 +321,28 @@ struct Lim<float> {
   static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
 };
 
+// ||Minv||_inf <= s max |m_eu| (a row holds s entries): the bound the solves' bound
+// test needs, from the entries' bit patterns (binary64 row sums would cost about s^2
+// instructions on the 1/64-rate FP64 pipe); infinite when an entry is not finite.
+template <typename CT>
+struct MagT;
+template <>
+struct MagT<double> {
+  using B = unsigned long long;
+  static constexpr B kInf = 0x7FF0000000000000ull;
+  static __device__ __forceinline__ double val(B b) { return __longlong_as_double(static_cast<long long>(b)); }
+};
+template <>
+struct MagT<float> {
+  using B = unsigned;
+  static constexpr B kInf = 0x7F800000u;
+  static __device__ __forceinline__ float val(B b) { return __uint_as_float(b); }
+};
+template <typename CT>
+__device__ __forceinline__ CT inv_norm_bound(typename MagT<CT>::B mb, int s) {
+  return mb >= MagT<CT>::kInf ? Lim<CT>::inf() : MagT<CT>::val(mb) * static_cast<CT>(s);
+}
+
 // The factorization of pair_factor for a compile-time block shape (MA x MA with
 // NB x NB), in registers, followed by the inverse: column k of Minv solves
 // M x = e_k with the same interchanges, multipliers and reciprocals.  Writes Minv
@@ -337,7 +359,7 @@ __device__ __forceinline__ int pair_prepare(const CT (&a)[4], const CT (&b)[4], 
   for (int u = 0; u < S; ++u)
 #pragma unroll
     for (int v = 0; v < S; ++v) {
-      CT e = CT(0);
+      CT e = -CT(0);  // -0 + x folds to x: only the diagonal entries take an addition
       if (u / MA == v / MA) e += a[(u % MA) + 2 * (v % MA)];
       if (u % MA == v % MA) e += b[(v / MA) + 2 * (u / MA)];
       M[u][v] = e;
@@ -433,20 +455,15 @@ __device__ __forceinline__ int pair_prepare(const CT (&a)[4], const CT (&b)[4], 
       for (int t = 0; t < S; ++t)
         if (cperm[u] == t) inv[t][k] = r[u];
   }
-  CT nrm = CT(0);
-  bool finite = true;
+  typename MagT<CT>::B mb = 0;
 #pragma unroll
-  for (int e = 0; e < S; ++e) {
-    CT rs = CT(0);
+  for (int e = 0; e < S; ++e)
 #pragma unroll
     for (int u = 0; u < S; ++u) {
       out[e * S + u] = inv[e][u];
-      rs += fabs(inv[e][u]);
+      mb = max(mb, mag_bits(inv[e][u]));
     }
-    finite = finite && (rs <= Lim<CT>::big());
-    nrm = rs > nrm ? rs : nrm;
-  }
-  out[S * S] = finite ? nrm : Lim<CT>::inf();
+  out[S * S] = inv_norm_bound<CT>(mb, S);
   return pack;
 }
 
@@ -618,20 +635,13 @@ __device__ __forceinline__ int pair_quad_prepare(const CT (&a)[4], const CT (&b)
                         -b12 * i11 * i10,
                         CT(0),
                         i11};
-  CT nrm = CT(0);
-  bool finite = true;
+  typename MagT<CT>::B mb = 0;
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    CT rs = CT(0);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      out[e * 4 + u] = m[e * 4 + u];
-      rs += fabs(m[e * 4 + u]);
-    }
-    finite = finite && (rs <= Lim<CT>::big());
-    nrm = rs > nrm ? rs : nrm;
+  for (int e = 0; e < 16; ++e) {
+    out[e] = m[e];
+    mb = max(mb, mag_bits(m[e]));
   }
-  out[16] = finite ? nrm : Lim<CT>::inf();
+  out[16] = inv_norm_bound<CT>(mb, 4);
   return flag;
 }
 
@@ -691,22 +701,18 @@ __device__ __noinline__ int pair_half_prepare(int ma, int nb, bool pa, CT a0_, C
       else
         m[e1][u0] = -cpl * c;  // right column element from the left right-hand side
     }
-  CT nrm = CT(0);
-  bool finite = true;
+  typename MagT<CT>::B mb = 0;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     if (e >= s) continue;
-    CT rs = CT(0);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (u >= s) continue;
       out[e * s + u] = m[e][u];
-      rs += fabs(m[e][u]);
+      mb = max(mb, mag_bits(m[e][u]));
     }
-    finite = finite && (rs <= Lim<CT>::big());
-    nrm = rs > nrm ? rs : nrm;
   }
-  out[s * s] = finite ? nrm : Lim<CT>::inf();
+  out[s * s] = inv_norm_bound<CT>(mb, s);
   return flags & (1 << 16);
 }
 
@@ -1119,6 +1125,8 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
     // The binary64 kernels read all of it after the barrier (registers: the prefetch
     // would spill in them, and their steps are bound by the FP64 pipe, not latency).
     constexpr bool kPreF = sizeof(T) == 4;
+    constexpr bool kTab = kPreF && DagSmem<TT, T>::kSplitK && TT <= 32;
+    unsigned* etab = reinterpret_cast<unsigned*>(sh.kred);
     auto load_inv = [&](Meta& m) {
       const FactT* f = fact + m.fo;
 #pragma unroll
@@ -1148,19 +1156,54 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
         m.r = code & 63;
         m.c = (code >> 6) & 63;
         m.ev = code >> 12;
-        const int kb = sh.rowblk[m.r], lb = sh.colblk[m.c];
-        const int ra = sh.astart[kb];
-        const int ma = sh.astart[kb + 1] - ra;
-        const int cb0 = sh.bstart[lb];
-        m.sz = ma * (sh.bstart[lb + 1] - cb0);
-        m.ka0 = ra + ma;
-        m.Ka = mt - m.ka0;
-        m.Kt = m.Ka + lw * cb0;
-        m.fo = pair_offset(sh, kb, lb, ma);
+        if constexpr (kTab) {
+          const unsigned wd = etab[e0 + m.g];
+          m.fo = static_cast<int>(wd & 0xffffu);
+          m.ka0 = static_cast<int>((wd >> 16) & 63u);
+          m.Kt = static_cast<int>((wd >> 22) & 127u);
+          m.sz = static_cast<int>((wd >> 29) & 3u) + 1;
+          m.nr = (wd >> 31) != 0;
+          m.Ka = mt - m.ka0;
+        } else {
+          const int kb = sh.rowblk[m.r], lb = sh.colblk[m.c];
+          const int ra = sh.astart[kb];
+          const int ma = sh.astart[kb + 1] - ra;
+          const int cb0 = sh.bstart[lb];
+          m.sz = ma * (sh.bstart[lb + 1] - cb0);
+          m.ka0 = ra + ma;
+          m.Ka = mt - m.ka0;
+          m.Kt = m.Ka + lw * cb0;
+          m.fo = pair_offset(sh, kb, lb, ma);
+          m.nr = (factp[kb * TT + lb] & (1 << 16)) != 0;
+        }
         if constexpr (kPreF) load_inv(m);
-        m.nr = (factp[kb * TT + lb] & (1 << 16)) != 0;
       }
     };
+    // The binary32 tile-32 kernel packs each element's bookkeeping into one word per
+    // position of the element order, in the split-K buffer (idle during the diagonal
+    // solve), so that a step reads it in one round trip instead of a chain of
+    // dependent shared-memory loads: the pair's factor-store offset (bits 0-15), the
+    // first row below the block (16-21), the number of terms (22-28), the block size
+    // minus one (29-30) and whether a pivot was raised (31).
+    if constexpr (kTab) {
+      if (s0 > 0) {
+        const int ne = sh.sstart[nsteps];
+        for (int e = tid; e < ne; e += kThreads) {
+          const unsigned code = sh.eord[e];
+          const int r = code & 63, c = (code >> 6) & 63;
+          const int kb = sh.rowblk[r], lb = sh.colblk[c];
+          const int ra = sh.astart[kb], ma = sh.astart[kb + 1] - ra;
+          const int cb0 = sh.bstart[lb];
+          const int sz = ma * (sh.bstart[lb + 1] - cb0);
+          const int ka0 = ra + ma;
+          const int Kt = (mt - ka0) + lw * cb0;
+          const unsigned nr = (static_cast<unsigned>(factp[kb * TT + lb]) >> 16) & 1u;
+          etab[e] = static_cast<unsigned>(pair_offset(sh, kb, lb, ma)) | (static_cast<unsigned>(ka0) << 16) |
+                    (static_cast<unsigned>(Kt) << 22) | (static_cast<unsigned>(sz - 1) << 29) | (nr << 31);
+        }
+        __syncthreads();
+      }
+    }
     Meta m;
     if (kPreF && s0 > 0) meta(0, m);
     for (int s = 0; s < s0; ++s) {
@@ -1602,8 +1645,8 @@ __device__ __forceinline__ void gemm_sub(T (&acc)[MR][NR], const T* L, const T* 
 // block in group order (deterministic).  part receives -sum_k L[k, r] R[k, c], as
 // gemm_sub does; the caller's barrier after the accumulation frees kred again.
 template <int TT, typename T>
-__device__ __forceinline__ void gemm_sub_split4(T (&part)[2][2], const T* L, const T* R, const int* gk, int ng,
-                                                int rbase, int cbase, T* kred) {
+__device__ __forceinline__ void gemm_sub_split4(T (&part)[2][2], const T* L, const T* R, int kdim, int rbase,
+                                                int cbase, T* kred) {
   static_assert(sizeof(T) == 4 && TT == 32 && kThreads == 256, "binary32, tile 32, 256 threads");
   constexpr int LDG = DagSmem<TT, T>::LDG;
   static_assert(LDG % 2 == 0, "paired operand reads");
@@ -1615,23 +1658,18 @@ __device__ __forceinline__ void gemm_sub_split4(T (&part)[2][2], const T* L, con
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) p[i][j] = T(0);
-  // producers in TT-row slots: slot u runs over its own K extent gk[u] (TT is a
-  // multiple of 4, so every group keeps its residue of k; the padding adds only zeros)
-  for (int u = 0; u < ng; ++u) {
-    const int k1 = u * TT + gk[u];
 #pragma unroll 2
-    for (int kk = u * TT + g; kk < k1; kk += 4) {
-      const float2 a01 = *reinterpret_cast<const float2*>(&L[kk * LDG + r4]);
-      const float2 a23 = *reinterpret_cast<const float2*>(&L[kk * LDG + r4 + 2]);
-      const float2 b01 = *reinterpret_cast<const float2*>(&R[kk * LDG + c4]);
-      const float2 b23 = *reinterpret_cast<const float2*>(&R[kk * LDG + c4 + 2]);
-      const T a[4] = {a01.x, a01.y, a23.x, a23.y};
-      const T b[4] = {b01.x, b01.y, b23.x, b23.y};
+  for (int kk = g; kk < kdim; kk += 4) {
+    const float2 a01 = *reinterpret_cast<const float2*>(&L[kk * LDG + r4]);
+    const float2 a23 = *reinterpret_cast<const float2*>(&L[kk * LDG + r4 + 2]);
+    const float2 b01 = *reinterpret_cast<const float2*>(&R[kk * LDG + c4]);
+    const float2 b23 = *reinterpret_cast<const float2*>(&R[kk * LDG + c4 + 2]);
+    const T a[4] = {a01.x, a01.y, a23.x, a23.y};
+    const T b[4] = {b01.x, b01.y, b23.x, b23.y};
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) p[i][j] = fma(-a[i], b[j], p[i][j]);
-    }
+      for (int j = 0; j < 4; ++j) p[i][j] = fma(-a[i], b[j], p[i][j]);
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j)
@@ -1944,23 +1982,31 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
             const int v = __shfl_up_sync(0xffffffffu, ko, o);
             if (lane >= o) ko += v;
           }
-          // Packed tiles are zero-padded to TT rows of k and staged in fixed slots.
-          const int ktot = packed ? g * TT : __shfl_sync(0xffffffffu, ko, g - 1);
+          // Packed tiles are zero-padded to TT rows of k.  The binary64 kernels stage
+          // each producer's own kdim rows back to back (a row of LDG doubles is a
+          // multiple of 16 bytes, as bulk copies require), so the group product runs
+          // over no padding rows; the binary32 kernels stage whole slots (a binary32 row
+          // is not a multiple of 16 bytes).
+          constexpr bool kTight = sizeof(T) == 8;
+          const bool slots = packed && !kTight;
+          const int ktot = slots ? g * TT : __shfl_sync(0xffffffffu, ko, g - 1);
           if (lane < g) {
             sh.gside[lane] = side;
             sh.gprod[lane] = prod;
             sh.gk[lane] = kdim;
-            sh.goff[lane] = packed ? lane * TT : ko - kdim;
+            sh.goff[lane] = slots ? lane * TT : ko - kdim;
           }
           if (packed) {
             // The group is staged by bulk copies (async proxy): lane 0 sets the
             // transaction count, then every member's lane issues its own two copies,
             // after its own flag acquire and proxy fences, so the issue runs in
             // parallel instead of 2g copies in a row on one lane.
-            const uint32_t bytes = static_cast<uint32_t>(w.pack_slot);
+            constexpr uint32_t kRow = DagSmem<TT, T>::LDG * sizeof(T);
+            const uint32_t bytes = kTight ? static_cast<uint32_t>(kdim) * kRow : static_cast<uint32_t>(w.pack_slot);
+            const uint32_t total = kTight ? 2u * static_cast<uint32_t>(ktot) * kRow : 2u * g * bytes;
             const uint32_t bar = smem_addr(&sh.stage_bar);
             if (lane == 0)
-              asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2u * g * bytes)
+              asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(total)
                            : "memory");
             __syncwarp();
             if (lane < g) {
@@ -1976,8 +2022,9 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
                 sl = pack_yl(I, k, j);
                 sr = pack_b(I, j, l);
               }
-              bulk_copy_g2s(sh.L + lane * TT * DagSmem<TT, T>::LDG, w.pack + sl * w.pack_slot, bytes, bar);
-              bulk_copy_g2s(sh.R + lane * TT * DagSmem<TT, T>::LDG, w.pack + sr * w.pack_slot, bytes, bar);
+              const int dk = slots ? lane * TT : ko - kdim;  // first staged row of this member
+              bulk_copy_g2s(sh.L + dk * DagSmem<TT, T>::LDG, w.pack + sl * w.pack_slot, bytes, bar);
+              bulk_copy_g2s(sh.R + dk * DagSmem<TT, T>::LDG, w.pack + sr * w.pack_slot, bytes, bar);
             }
           }
           if (lane == 0) {
@@ -2133,14 +2180,8 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
         for (int i = 0; i < MR; ++i)
 #pragma unroll
           for (int j = 0; j < NR; ++j) part[i][j] = T(0);
-        if constexpr (DagSmem<TT, T>::kSplitK) {
-          // packed producers sit in TT-row slots; staged ones back to back (one slot)
-          const int one = sh.gktot;
-          if (packed)
-            gemm_sub_split4<TT, T>(part, sh.L, sh.R, sh.gk, sh.gn, rbase, cbase, sh.kred);
-          else
-            gemm_sub_split4<TT, T>(part, sh.L, sh.R, &one, 1, rbase, cbase, sh.kred);
-        }
+        if constexpr (DagSmem<TT, T>::kSplitK)
+          gemm_sub_split4<TT, T>(part, sh.L, sh.R, sh.gktot, rbase, cbase, sh.kred);
         else
           gemm_sub<TT, T, MR, NR>(part, sh.L, sh.R, sh.gktot, rbase, cbase);
 #pragma unroll
@@ -2153,17 +2194,6 @@ __global__ void __launch_bounds__(kThreads, 2) dag_kernel(Work w) {
             acc[i][j] = t;
             acc_lo[i][j] += e;
           }
-      } else if (packed) {
-        // Producers sit in fixed TT-row slots, zero-padded: each slot's product runs over
-        // its producer's own K extent only, and a thread whose columns lie beyond the
-        // tile (whole warps once nt <= 4 w) skips it: the padding adds only zeros.
-        if (cbase < nt) {
-          const int g = sh.gn;
-          for (int u = 0; u < g; ++u) {
-            const int off = u * TT * DagSmem<TT, T>::LDG;
-            gemm_sub<TT, T, MR, NR>(acc, sh.L + off, sh.R + off, sh.gk[u], rbase, cbase);
-          }
-        }
       } else {
         gemm_sub<TT, T, MR, NR>(acc, sh.L, sh.R, sh.gktot, rbase, cbase);
       }

@@ -684,10 +684,13 @@ def run_batched(args):
     e1.record(cur)
     torch.cuda.synchronize()
     seq_ms = e0.elapsed_time(e1) * count / len(sample)
-    # FP32 + refinement on the same equations and tiles, at the 1e-12 forward-error
-    # target (MIXED_TOL), graph-captured the same way; its solutions are compared with
-    # the FP64 batch's (Cs holds them after the last replay).
+    # FP32 + refinement on the same equations at the 1e-12 forward-error target
+    # (MIXED_TOL), with tiles tuned for it (its latency-bound binary32 tiles favour
+    # other sizes than FP64), graph-captured the same way; its solutions are compared
+    # with the FP64 batch's (Cs holds them after the last replay).
     Cr = [c.clone() for c in C0s]
+    rtiles = [args.tile] * count if args.tile else autotune.tune_batch(As, Bs, Cr, precision="fp32_refine",
+                                                                       tol=MIXED_TOL)
     rstream = torch.cuda.Stream(dev)
     torch.cuda.synchronize()
     with torch.cuda.stream(rstream):
@@ -695,7 +698,7 @@ def run_batched(args):
         rplan = sylv.sylv_batch_create([m for m, _ in shapes], [n for _, n in shapes], [a.data_ptr() for a in As],
                                        [a.stride(1) for a in As], [b.data_ptr() for b in Bs],
                                        [b.stride(1) for b in Bs], [c.data_ptr() for c in Cr],
-                                       [c.stride(1) for c in Cr], ropts, tiles=tiles)
+                                       [c.stride(1) for c in Cr], ropts, tiles=rtiles)
         rrc = sylv.sylv_batch_execute(rplan, rstream.cuda_stream)
         rstream.synchronize()
         rgraph = torch.cuda.CUDAGraph()
@@ -722,6 +725,7 @@ def run_batched(args):
     refined = {"solves_per_s": count / (rms / 1000), "ms_per_step": rms, "tol": MIXED_TOL, "accuracy_target": 1e-12,
                "worst_info": max(r.info for r in rres), "iters_max": max(r.iters for r in rres),
                "iters_mean": sum(r.iters for r in rres) / count,
+               "tile_mix": {str(t): rtiles.count(t) for t in sorted(set(rtiles))},
                "max_rel_err_vs_fp64_batch": max(errs), "speedup_vs_fp64_batch": ms / rms}
     del Cr
     line = {"metric": "batched solves/s", "value": count / (ms / 1000), "unit": "solves/s", "n_gpus": 1,

@@ -59,9 +59,9 @@ def _save_cache(c: dict) -> None:
         pass
 
 
-def _time_plan(sy, torch, shapes, As, Bs, Cs, C0s, tiles, reps=3) -> float:
+def _time_plan(sy, torch, shapes, As, Bs, Cs, C0s, tiles, reps=3, precision="fp64", tol=0.0) -> float:
     stream = torch.cuda.current_stream()
-    o = sy.make_opts(stream=stream.cuda_stream)
+    o = sy.make_opts(stream=stream.cuda_stream, precision=precision, tol=tol)
     plan = sy.sylv_batch_create([m for m, _ in shapes], [n for _, n in shapes], [a.data_ptr() for a in As],
                                 [a.stride(1) for a in As], [b.data_ptr() for b in Bs], [b.stride(1) for b in Bs],
                                 [c.data_ptr() for c in Cs], [c.stride(1) for c in Cs], o, tiles=tiles)
@@ -86,14 +86,16 @@ def _time_plan(sy, torch, shapes, As, Bs, Cs, C0s, tiles, reps=3) -> float:
     return ts[len(ts) // 2]
 
 
-def tune_batch(As, Bs, Cs, *, use_cache=True, reps=3, log=None):
+def tune_batch(As, Bs, Cs, *, precision="fp64", tol=0.0, use_cache=True, reps=3, log=None):
     """Tile size per equation for this batch (lists of column-major float64 CUDA
-    tensors; Cs are overwritten during tuning and restored at the end)."""
+    tensors; Cs are overwritten during tuning and restored at the end), tuned for the
+    given precision ("fp64" or "fp32_refine" at stop tolerance tol): the binary32
+    correction solves favour other tiles than the FP64 solve."""
     import torch
 
     from . import sylv as sy
     shapes = [(int(c.shape[0]), int(c.shape[1])) for c in Cs]
-    key = f"{torch.cuda.get_device_name()}|fp64|{signature(shapes)}"
+    key = f"{torch.cuda.get_device_name()}|{precision}|{tol!r}|{signature(shapes)}"
     cache = _load_cache() if use_cache else {}
     if key in cache:
         per_bucket = cache[key]["per_bucket"]
@@ -101,7 +103,7 @@ def tune_batch(As, Bs, Cs, *, use_cache=True, reps=3, log=None):
     C0s = [c.clone() for c in Cs]
     best_t, best_ms = None, float("inf")
     for t in CANDIDATES:
-        ms = _time_plan(sy, torch, shapes, As, Bs, Cs, C0s, [t] * len(shapes), reps)
+        ms = _time_plan(sy, torch, shapes, As, Bs, Cs, C0s, [t] * len(shapes), reps, precision, tol)
         if log:
             log(f"all t={t}: {ms:.2f} ms")
         if ms < best_ms:
@@ -114,7 +116,8 @@ def tune_batch(As, Bs, Cs, *, use_cache=True, reps=3, log=None):
                 continue
             trial = list(per_bucket)
             trial[b] = t
-            ms = _time_plan(sy, torch, shapes, As, Bs, Cs, C0s, [trial[bucket_of(m, n)] for m, n in shapes], reps)
+            ms = _time_plan(sy, torch, shapes, As, Bs, Cs, C0s, [trial[bucket_of(m, n)] for m, n in shapes], reps,
+                            precision, tol)
             if log:
                 log(f"bucket {b} t={t}: {ms:.2f} ms")
             if ms < best_ms * 0.98:

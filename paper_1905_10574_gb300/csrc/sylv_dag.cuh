@@ -171,12 +171,25 @@ __device__ __forceinline__ int guard_division(double r, double d, double rcp, do
 // pair_factor's layout: multipliers below the diagonal, U on and above it, 1/pivot
 // after the s*s entries; the row/column interchanges in a packed int (2 bits each;
 // bit 16: a pivot was raised).
-__device__ inline int pair_factor(int ma, int nb, const double* a, const double* b, double smin, double* out) {
+// A pseudo block (two 1x1 blocks merged, psa / psb) makes the system block
+// triangular: with level(i, j) = (psa ? 1 - i : 0) + (psb ? j : 0), an element
+// depends only on elements of lower levels (the bottom row of a pseudo A block and
+// the left column of a pseudo B block come first).  The pivots are searched within
+// the lowest level not yet eliminated, so that no interchange mixes levels: the
+// factors keep the structure's exact zeros and the solve is the substitution of the
+// 1x1 and 2x2 parts one after another (each part's pivots are those it has alone).
+// Complete pivoting over the whole system would instead pivot on a large coupling
+// entry and lose the small elements of the block (componentwise), which the
+// substitution of Algorithm 2 over the unmerged blocks keeps.
+__device__ inline int pair_factor(int ma, int nb, bool psa, bool psb, const double* a, const double* b, double smin,
+                                  double* out) {
   const int s = ma * nb;
   double M[4][4];
   int pack = 0;
+  int rlev[4], clev[4];  // level of the equation in row position u / unknown in column v
   for (int u = 0; u < s; ++u) {
     const int i = u % ma, j = u / ma;
+    rlev[u] = clev[u] = (psa ? 1 - i : 0) + (psb ? j : 0);
     for (int v = 0; v < s; ++v) {
       const int i2 = v % ma, j2 = v / ma;
       double e = 0.0;
@@ -187,11 +200,14 @@ __device__ inline int pair_factor(int ma, int nb, const double* a, const double*
   }
   int cperm[4] = {0, 1, 2, 3};
   for (int st = 0; st < s; ++st) {
+    int lev = 3;
+    for (int u = st; u < s; ++u) lev = min(lev, rlev[u]);
     int pr = st, pc = st;
     unsigned long long best = 0;
     bool first = true;
     for (int u = st; u < s; ++u)
       for (int v = st; v < s; ++v) {
+        if (rlev[u] != lev || clev[v] != lev) continue;
         const unsigned long long mag = abs_bits(M[u][v]);
         if (first || mag > best) {
           best = mag;
@@ -200,18 +216,26 @@ __device__ inline int pair_factor(int ma, int nb, const double* a, const double*
           first = false;
         }
       }
-    if (pr != st)
+    if (pr != st) {
       for (int v = 0; v < s; ++v) {
         const double tmp = M[st][v];
         M[st][v] = M[pr][v];
         M[pr][v] = tmp;
       }
-    if (pc != st)
+      const int lt = rlev[st];
+      rlev[st] = rlev[pr];
+      rlev[pr] = lt;
+    }
+    if (pc != st) {
       for (int u = 0; u < s; ++u) {
         const double tmp = M[u][st];
         M[u][st] = M[u][pc];
         M[u][pc] = tmp;
       }
+      const int lt = clev[st];
+      clev[st] = clev[pc];
+      clev[pc] = lt;
+    }
     const int ct = cperm[st];
     cperm[st] = cperm[pc];
     cperm[pc] = ct;
@@ -1417,7 +1441,9 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
             b[i + 2 * jj] = (i < nb && jj < nb) ? static_cast<double>(Bk[(c0 + i) + (c0 + jj) * LDY]) : 0.0;
           }
         double lu[20];
-        const int pack = pair_factor(ma, nb, a, b, smin, lu);
+        const bool psa = SYLV_MERGE_DIAG && ((sh.apsd >> kb) & 1ull);
+        const bool psb = SYLV_MERGE_DIAG && ((sh.bpsd >> lb) & 1ull);
+        const int pack = pair_factor(ma, nb, psa, psb, a, b, smin, lu);
         double rg[4] = {rv[0], rv[1], rv[2], rv[3]};  // the guarded solve takes its own copy
         if (sz == 1)
           eb = pair_solve_guarded<1>(lu, pack, rg, omh, eo, true);
@@ -1482,7 +1508,6 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
           const int gg = emin + z1 + z2;
           sh.e_diag += gg;
           sh.g = gg;
-          sh.slow = 0;
           if (gg != 0) ++local_scale_events;
         }
         __syncwarp();
@@ -1503,6 +1528,9 @@ __device__ void diag_solve(DagSmem<TT, T>& sh, int mt, int nt, double omega, dou
       }
       __syncthreads();
       g = sh.g;
+      // Every thread has read the flag before the barrier above; clearing it earlier
+      // (in warp 0) would let a later warp skip this phase and its barrier.
+      if (tid == 0) sh.slow = 0;
     }
     // Phase C: every owned unsolved element takes the scale and this step's
     // contributions: the block solved in its column block below it (A side) and the

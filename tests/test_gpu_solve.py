@@ -165,6 +165,44 @@ def test_robust_where_plain_overflows(orc, sy, m, upper, tile):
     assert res_nr.info == sy.SYLV_OVERFLOWED
 
 
+@pytest.mark.parametrize("m,n,tile,upper,seed", [(32, 32, 32, 1e10, 7), (20, 28, 32, 1e12, 7), (17, 31, 32, 1e13, 9),
+                                                 (64, 64, 64, 1e6, 7)])
+def test_single_tile_growth_hands_over_to_scaling(orc, sy, m, n, tile, upper, seed):
+    """One diagonal tile whose own substitution grows past the binary64 range: its
+    left-looking steps (which never scale) must hand over to the scaled right-looking
+    steps partway through the tile (scale_events > 0 on a single tile), whose tile-wide
+    factors (ProtectUpdate, Sec. 2.1) every warp must apply.  alpha < 1 and
+    representable, every entry finite and <= Omega, the eq. (9) residual tiny, and
+    Y/alpha equal to the oracle's entry by entry.  The solutions span ~440 decades, so
+    the normwise residual cannot see errors in the small entries (wrong entries of
+    size 1e-60 relative to max|Y| leave it near 1e-17).  The problems are well
+    conditioned componentwise (relative perturbations of 1e-15 in A and B move no
+    entry of X by more than ~1e-11), so every entry must agree; all entries stay
+    normal on both sides (the smallest is ~1e-166 of the largest)."""
+    A, B, C = inputs.problem(m, n, seed, kind="growth", upper=upper)
+    ref = orc.trsyl(A, B, C)
+    assert -1074 < ref["log2scale"] < 0 and ref["info"] == 0
+    Y, res = gpu_solve(sy, A, B, C, tile=tile)
+    assert res.info == 0 and -1074 < res.log2scale < 0 and res.scale_events > 0
+    assert np.all(np.isfinite(Y)) and np.max(np.abs(Y)) <= 2.0 ** 1020
+    assert orc.residual(A, B, Y, C, res.log2scale) <= RESID_TOL
+    Yr = shifted(Y, res.log2scale, ref["log2scale"])
+    Yo = ref["Y"]
+    assert np.min(np.abs(Yo)) > 2.0 ** -900 and np.min(np.abs(Yr)) > 2.0 ** -900
+    cw = np.abs(Yr - Yo) / np.abs(Yo)
+    assert float(np.max(cw)) <= 1e-10, (np.unravel_index(np.argmax(cw), cw.shape), float(np.max(cw)))
+
+
+@pytest.mark.parametrize("m,n,tile", [(32, 32, 32), (29, 18, 32), (64, 40, 64)])
+def test_right_hand_side_near_omega_starts_right_looking(orc, sy, m, n, tile):
+    """Entries of C near 2^1018: the diagonal tile's bound test fails before its first
+    step, so the tile is solved by the scaled right-looking steps from the start; the
+    result must still match the oracle."""
+    A, B, C = inputs.problem(m, n, 5, kind="benign")
+    C = np.ldexp(C, 1018)
+    check_against_oracle(orc, sy, A, B, C, tile=tile)
+
+
 @pytest.mark.parametrize("m,n,tile,kind,upper", [(1, 1, 0, "benign", 1.0), (33, 31, 32, "benign", 1.0),
                                                  (129, 200, 32, "benign", 1.0), (200, 129, 64, "benign", 1.0),
                                                  (257, 95, 0, "benign", 1.0), (300, 300, 32, "growth", 30.0)])

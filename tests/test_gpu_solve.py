@@ -193,6 +193,25 @@ def test_single_tile_growth_hands_over_to_scaling(orc, sy, m, n, tile, upper, se
     assert float(np.max(cw)) <= 1e-10, (np.unravel_index(np.argmax(cw), cw.shape), float(np.max(cw)))
 
 
+@pytest.mark.parametrize("m,n,upper,seed,tile", [(100, 100, 1e3, 3, 32), (160, 96, 1e4, 5, 32), (160, 96, 1e4, 5, 64),
+                                                 (200, 200, 30.0, 7, 32)])
+def test_multi_tile_growth_entrywise(orc, sy, m, n, upper, seed, tile):
+    """Growth inputs over several tiles (solutions spanning up to ~560 decades; the
+    160 x 96 case needs alpha = 2^-839 in the oracle): besides the normwise checks,
+    Y/alpha must match the oracle entry by entry wherever both sides hold a normal
+    number.  Relative perturbations of 1e-15 in A and B move no entry of these
+    solutions by more than ~1e-9, so 1e-7 leaves a factor 100 for rounding while any
+    wrong factor, sign or dropped term in a small entry fails."""
+    A, B, C = inputs.problem(m, n, seed, kind="growth", upper=upper)
+    Y, res, ref = check_against_oracle(orc, sy, A, B, C, tile=tile)
+    Yr = shifted(Y, res.log2scale, ref["log2scale"])
+    Yo = ref["Y"]
+    mask = (np.abs(Yo) > 2.0 ** -900) & (np.abs(Yr) > 2.0 ** -900)
+    assert mask.mean() > 0.99
+    cw = np.abs(Yr - Yo)[mask] / np.abs(Yo)[mask]
+    assert float(np.max(cw)) <= 1e-7, float(np.max(cw))
+
+
 @pytest.mark.parametrize("m,n,tile", [(32, 32, 32), (29, 18, 32), (64, 40, 64)])
 def test_right_hand_side_near_omega_starts_right_looking(orc, sy, m, n, tile):
     """Entries of C near 2^1018: the diagonal tile's bound test fails before its first

@@ -21,6 +21,13 @@ Contents, each written from the paper (Schwarz & Kjelgaard Mikkelsen 2019):
   * ``residual_matrix`` -- R = C - (A X + X B) from its definition (eq. (7) with
                       alpha = 1) in extended precision, and ``residual_matrix_exact``
                       in exact rational arithmetic for tiny cases.
+  * ``solve_decimal`` -- the unscaled solution X of eq. (2) by plain block
+                      substitution (Algorithm 1's order) in decimal arithmetic with
+                      50 significant digits and an exponent range no solution here
+                      can leave, so nothing over- or underflows and no scaling is
+                      needed; ``decimal_scaled`` rounds alpha X to binary64.  The
+                      reference where alpha < 2^-1074: there Algorithm 2's single
+                      factor flushes right-hand sides it has not reached yet.
 """
 from __future__ import annotations
 
@@ -308,3 +315,107 @@ def schur_solve(U, TA, V, TB, C, isgn: int = 1):
     Ct = U.T @ C @ V
     out = trsyl(TA, TB if isgn >= 0 else -TB, Ct)
     return U @ out["Y"] @ V.T, out["log2scale"]
+
+
+def _decimal_blocks(T) -> list[tuple[int, int]]:
+    """(start, size) of the diagonal blocks of an upper quasi-triangular T: a nonzero
+    T[i+1, i] starts a 2x2 block at i."""
+    n = T.shape[0]
+    out, i = [], 0
+    while i < n:
+        size = 2 if (i + 1 < n and T[i + 1, i] != 0.0) else 1
+        out.append((i, size))
+        i += size
+    return out
+
+
+def _decimal_gauss(M, r):
+    """Gaussian elimination with partial pivoting on a small dense Decimal system."""
+    n = len(r)
+    M = [row[:] for row in M]
+    r = list(r)
+    for k in range(n):
+        p = max(range(k, n), key=lambda i: abs(M[i][k]))
+        M[k], M[p] = M[p], M[k]
+        r[k], r[p] = r[p], r[k]
+        for i in range(k + 1, n):
+            f = M[i][k] / M[k][k]
+            for j in range(k, n):
+                M[i][j] -= f * M[k][j]
+            r[i] -= f * r[k]
+    x = [None] * n
+    for i in range(n - 1, -1, -1):
+        acc = r[i]
+        for j in range(i + 1, n):
+            acc -= M[i][j] * x[j]
+        x[i] = acc / M[i][i]
+    return x
+
+
+def solve_decimal(A, B, C, transa: bool = False, transb: bool = False, digits: int = 50):
+    """X with op(A) X + X op(B) = C (eq. (2), no scaling) as a list of rows of
+    ``decimal.Decimal``.  Block substitution in Algorithm 1's order: for each diagonal
+    block of B from the left and each diagonal block of A from the bottom, the block's
+    right-hand side C_kl - sum_{i>k} A_ki X_il - sum_{j<l} X_kj B_jl (eq. (6)) and the
+    small system of eq. (2) for the block pair, by Gaussian elimination.  The binary64
+    inputs are exact decimals; every operation keeps `digits` significant digits and
+    the exponent range is unbounded for these sizes.  Transposes as in ``trsyl``."""
+    import decimal
+    A = quasi_tri(A)
+    B = quasi_tri(B)
+    C = np.asarray(C, dtype=np.float64)
+    if transa:
+        A = anti_transpose(A)
+        C = np.flip(C, 0)
+    if transb:
+        B = anti_transpose(B)
+        C = np.flip(C, 1)
+    m, n = C.shape
+    ctx = decimal.Context(prec=digits, Emax=decimal.MAX_EMAX, Emin=decimal.MIN_EMIN)
+    with decimal.localcontext(ctx):
+        D = decimal.Decimal
+        Ad = [[D(float(A[i, j])) for j in range(m)] for i in range(m)]
+        Bd = [[D(float(B[i, j])) for j in range(n)] for i in range(n)]
+        X = [[None] * n for _ in range(m)]
+        ablk, bblk = _decimal_blocks(A), _decimal_blocks(B)
+        for c0, nb in bblk:
+            for r0, ma in reversed(ablk):
+                idx = [(ii, jj) for jj in range(nb) for ii in range(ma)]  # vec order
+                rhs = []
+                for ii, jj in idx:
+                    i, j = r0 + ii, c0 + jj
+                    acc = D(float(C[i, j]))
+                    for k in range(r0 + ma, m):
+                        if Ad[i][k]:
+                            acc -= Ad[i][k] * X[k][j]
+                    for k in range(c0):
+                        if Bd[k][j]:
+                            acc -= X[i][k] * Bd[k][j]
+                    rhs.append(acc)
+                M = [[D(0)] * len(idx) for _ in idx]
+                for u, (i, j) in enumerate(idx):
+                    for v, (i2, j2) in enumerate(idx):
+                        e = D(0)
+                        if j == j2:
+                            e += Ad[r0 + i][r0 + i2]
+                        if i == i2:
+                            e += Bd[c0 + j2][c0 + j]
+                        M[u][v] = e
+                z = _decimal_gauss(M, rhs)
+                for u, (i, j) in enumerate(idx):
+                    X[r0 + i][c0 + j] = z[u]
+    if transa:
+        X = X[::-1]
+    if transb:
+        X = [row[::-1] for row in X]
+    return X
+
+
+def decimal_scaled(X, log2scale: int) -> np.ndarray:
+    """alpha X = X * 2^log2scale rounded to binary64 (0 where it underflows)."""
+    import decimal
+    ctx = decimal.Context(prec=60, Emax=decimal.MAX_EMAX, Emin=decimal.MIN_EMIN)
+    with decimal.localcontext(ctx):
+        two = decimal.Decimal(2) ** int(log2scale)
+        rows = [[float(v * two) for v in row] for row in X]
+    return np.array(rows, dtype=np.float64).reshape(len(X), len(X[0]) if X else 0)

@@ -212,6 +212,31 @@ def test_multi_tile_growth_entrywise(orc, sy, m, n, upper, seed, tile):
     assert float(np.max(cw)) <= 1e-7, float(np.max(cw))
 
 
+@pytest.mark.parametrize("m,n,seed,tile", [(184, 10, 936395, 32), (185, 48, 900660, 0), (189, 45, 237710, 0)])
+def test_alpha_below_binary64_against_decimal_solution(orc, sy, m, n, seed, tile):
+    """Growth inputs (strictly-upper entries up to 1e6) whose solutions need
+    alpha = 2^-1270 ... 2^-1978, below the binary64 range (status SCALE_UNDERFLOW).
+    Algorithm 2's single factor scales right-hand sides it has not reached yet, and
+    once alpha < 2^-1074 they underflow to zero: on these inputs the oracle's Y/alpha
+    is 15-100% off the true solution (normwise).  The tile kernel's per-tile factors
+    scale a tile's right-hand side only together with its own updates, so its result
+    is compared with the solution computed in 50-digit decimal arithmetic (no
+    scaling, unbounded exponent range; pinned on the CPU against the Kronecker solve
+    and the exact rational residual): measured 2e-16 ... 4e-15 normwise and at most
+    5e-12 relative in any entry that is a normal binary64 number."""
+    A, B, C = inputs.problem(m, n, seed, kind="growth", upper=1e6)
+    Y, res = gpu_solve(sy, A, B, C, tile=tile, check=False)
+    assert res.info == sy.SYLV_SCALE_UNDERFLOW and res.log2scale < -1074
+    assert np.all(np.isfinite(Y)) and np.max(np.abs(Y)) <= 2.0 ** 1020
+    assert orc.residual(A, B, Y, C, res.log2scale) <= RESID_TOL
+    X = orc.decimal_scaled(orc.solve_decimal(A, B, C), res.log2scale)
+    assert rel(Y, X) <= 1e-13
+    mask = np.abs(X) > 2.0 ** -1000
+    assert mask.mean() > 0.5
+    cw = np.abs(Y - X)[mask] / np.abs(X)[mask]
+    assert float(np.max(cw)) <= 1e-10, float(np.max(cw))
+
+
 @pytest.mark.parametrize("m,n,tile", [(32, 32, 32), (29, 18, 32), (64, 40, 64)])
 def test_right_hand_side_near_omega_starts_right_looking(orc, sy, m, n, tile):
     """Entries of C near 2^1018: the diagonal tile's bound test fails before its first

@@ -396,3 +396,49 @@ def test_schur_solve_against_dense_sylvester(orc):
     assert np.allclose(X, sla.solve_sylvester(A, B, C), rtol=0, atol=1e-12)
     Xm, _ = orc.schur_solve(U, TA, V, -TB, C, isgn=-1)
     assert np.allclose(Xm, X, rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- the decimal reference solution
+@pytest.mark.parametrize("ta,tb", [(False, False), (False, True), (True, False), (True, True)])
+def test_decimal_solution_matches_kronecker(orc, ta, tb):
+    """eq. (2): the decimal block substitution against the textbook Kronecker solve
+    (dense LU, a different method), with 2x2 blocks on both sides and transposes."""
+    A, B, C = inputs.problem(11, 9, 4, kind="benign")
+    X = orc.decimal_scaled(orc.solve_decimal(A, B, C, ta, tb), 0)
+    K = orc.kron_solve(A, B, C, ta, tb)
+    assert np.linalg.norm(X - K) / np.linalg.norm(K) <= 1e-13
+
+
+def test_decimal_solution_beyond_binary64_satisfies_equation_exactly(orc):
+    """A growth input whose solution leaves the binary64 range (max|X| ~ 1e400): the
+    decimal solution, converted exactly to rationals, satisfies A X + X B = C
+    entry by entry to ~1e-45 relative to |A||X| + |X||B| (exact rational residual), so
+    neither an exponent limit nor a dropped term can hide in it."""
+    A, B, C = inputs.problem(8, 7, 2, kind="growth", upper=1e60)
+    A, B = np.triu(A, -1), np.triu(B, -1)
+    X = orc.solve_decimal(A, B, C)
+    F = [[Fraction(v) for v in row] for row in X]
+    m, n = C.shape
+    Af = [[Fraction(float(A[i, j])) for j in range(m)] for i in range(m)]
+    Bf = [[Fraction(float(B[i, j])) for j in range(n)] for i in range(n)]
+    big = max(abs(v) for row in F for v in row)
+    assert big > Fraction(10) ** 400
+    for i in range(m):
+        for j in range(n):
+            r = Fraction(float(C[i, j])) - sum(Af[i][k] * F[k][j] for k in range(m)) \
+                - sum(F[i][k] * Bf[k][j] for k in range(n))
+            s = sum(abs(Af[i][k] * F[k][j]) for k in range(m)) + sum(abs(F[i][k] * Bf[k][j]) for k in range(n))
+            assert abs(r) <= s * Fraction(1, 10 ** 45)
+
+
+def test_decimal_scaled_agrees_with_algorithm2_without_scaling(orc):
+    """Where Algorithm 2 needs no scaling (alpha = 1), its binary64 result and the
+    rounded decimal solution agree to rounding; decimal_scaled applies 2^log2scale
+    exactly (a power of two moves no significand)."""
+    A, B, C = inputs.problem(40, 30, 6, kind="benign")
+    ref = orc.trsyl(A, B, C)
+    assert ref["log2scale"] == 0
+    X = orc.solve_decimal(A, B, C)
+    Y = orc.decimal_scaled(X, 0)
+    assert np.linalg.norm(Y - ref["Y"]) / np.linalg.norm(Y) <= 1e-13
+    assert np.array_equal(orc.decimal_scaled(X, -300), np.ldexp(Y, -300))

@@ -51,7 +51,10 @@ extern "C" {
 #define SYLV_SCALE_UNDERFLOW 2 /* alpha < 2^-1074: the double `scale` is 0, use log2scale */
 #define SYLV_NOT_CONVERGED 3   /* FP32 + refinement did not reach opts->tol */
 #define SYLV_OVERFLOWED 4      /* Inf/NaN in an output: the non-robust mode overflowed (Algorithm 1), or a
-                                  gradient of the adjoint lies beyond the binary64 range */
+                                  gradient of the adjoint lies beyond the binary64 range; or
+                                  FP32 + refinement (which returns alpha = 1) met a solution beyond
+                                  the binary64 range: C is then left holding the right-hand side, and
+                                  a synchronous single solve repeats the solve with SYLV_FP64 itself */
 #define SYLV_ERR_STRUCTURE_A 101 /* A has two consecutive nonzero subdiagonal entries */
 #define SYLV_ERR_STRUCTURE_B 102 /* B has two consecutive nonzero subdiagonal entries */
 #define SYLV_ERR_NONFINITE 103   /* NaN or Inf in A, B or C */
@@ -65,7 +68,12 @@ extern "C" {
 #define SYLV_FP64 0            /* robust tiled solve in binary64 (Algorithm 4) */
 #define SYLV_FP64_NONROBUST 1  /* same tiling, no scaling at all (Algorithm 1 per tile) */
 #define SYLV_FP32_REFINE 2     /* robust solve in binary32 + residual refinement in
-                                  binary64-accurate arithmetic (not in the paper) */
+                                  binary64-accurate arithmetic (not in the paper); the result has
+                                  alpha = 1.  A solution beyond the binary64 range ends the
+                                  refinement with SYLV_OVERFLOWED and C unchanged; a synchronous
+                                  single solve (opts->sync) then solves again with SYLV_FP64 and
+                                  returns that result (iters = 0, alpha <= 1), unless a caller
+                                  workspace is too small for it */
 
 typedef struct sylv_opts {
   int32_t transa;          /* 0: op(A) = A, 1: op(A) = A^T */
@@ -152,7 +160,9 @@ size_t sylv_workspace_size(int64_t m, int64_t n, const sylv_opts* opts);
  * launch per correction; binary64-accurate residuals in double-float arithmetic on
  * the binary32 pipes); each equation stops on its own tolerance test, after which
  * its work is skipped, and results[i].iters / last_update report it.  The launch
- * sequence is the same whatever converges, so it stays capturable.
+ * sequence is the same whatever converges, so it stays capturable.  An equation
+ * whose solution lies beyond the binary64 range reports SYLV_OVERFLOWED and keeps
+ * its right-hand side in C_i (solve it again with SYLV_FP64).
  *
  * sylv_batch_create builds a plan: it validates the HOST arrays m[i], n[i],
  * lda[i], ldb[i], ldc[i] and the device pointers A[i], B[i], C[i] (HOST arrays of

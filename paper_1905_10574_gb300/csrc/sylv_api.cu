@@ -372,6 +372,7 @@ struct Opts {
   int max_sms;  // 0: all SMs
   int nob;      // 1: no B term (the robust triangular solve op(A) X = alpha C)
   double omega, tol;
+  double omega_req;  // the caller's omega (0: the precision's default)
   int64_t timeout_ns;
   cudaStream_t stream;
   void* ws;
@@ -394,6 +395,7 @@ int read_opts(const sylv_opts* o, Opts* out) {
   out->tile = o->tile;
   out->maxit = o->maxit > 0 ? o->maxit : 6;
   out->sync = o->sync;
+  out->omega_req = o->omega > 0 ? o->omega : 0.0;
   out->omega = o->omega > 0 ? o->omega : (o->precision == SYLV_FP32_REFINE ? 0x1p124 : 0x1p1020);
   if (o->precision == SYLV_FP32_REFINE && out->omega > 0x1p124) out->omega = 0x1p124;  // binary32 tiles
   out->tol = o->tol > 0 ? o->tol : 0x1p-43;  // ~1.1e-13: a 9x margin under a 1e-12 forward-error target
@@ -604,7 +606,7 @@ int enqueue_refine(const SolvePlan& P, char* ws, const double* A, int64_t lda, c
                                                                                    dmax, xmax, &rs->conv);
     k_refine_check<<<1, 1, 0, s>>>(rs, dmax, xmax, it > 0 ? dmax - 3 : nullptr, o.tol, w);
   }
-  k_copy<<<grid_for(m * n), 256, 0, s>>>(X, m, C, ldc, m, n);
+  k_refine_copy_out<<<grid_for(m * n), 256, 0, s>>>(X, m, C, ldc, m, n, rs);
   k_refine_result<<<1, 1, 0, s>>>(rs, w.res, o.maxit);
   if (dres && cudaMemcpyAsync(dres, w.res, sizeof(sylv_result), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return SYLV_ERR_CUDA;
@@ -671,6 +673,20 @@ int solve_impl(int64_t m, int64_t n, const double* A, int64_t lda, const double*
     if (cudaMemcpyAsync(&r, res_dev, sizeof(r), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SYLV_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SYLV_ERR_CUDA;
     if (hres) *hres = r;
+    if (o.precision == SYLV_FP32_REFINE && r.info == SYLV_OVERFLOWED) {
+      // The solution lies beyond the binary64 range, which the refined solve (alpha = 1)
+      // cannot return; C still holds the right-hand side: solve again with the robust
+      // FP64 path, which scales (alpha < 1).  A caller workspace sized for the refined
+      // solve may be too small for it: the overflow status stands then.
+      Opts o64 = o;
+      o64.precision = SYLV_FP64;
+      o64.omega = o.omega_req > 0 ? o.omega_req : 0x1p1020;
+      sylv_result r64{};
+      const int rc64 = solve_impl(m, n, A, lda, B, ldb, C, ldc, o64, &r64, dres);
+      if (rc64 == SYLV_ERR_WORKSPACE) return r.info;
+      if (hres) *hres = r64;
+      return rc64;
+    }
     return r.info;
   }
   return SYLV_OK;

@@ -283,6 +283,15 @@ __device__ __forceinline__ void refine_check_one(RefineState* rs, const unsigned
   const double d = __longlong_as_double(static_cast<long long>(*dmax));
   const double x = __longlong_as_double(static_cast<long long>(*xmax));
   rs->iters += 1;
+  // The refined solution is returned at alpha = 1: a correction or a solution beyond
+  // the binary64 range (infinite or NaN maximum) ends the loop with SYLV_OVERFLOWED,
+  // and the equation's C is left as it was (the robust FP64 solve scales instead).
+  if (!(d <= 1.7976931348623157e308) || !(x <= 1.7976931348623157e308)) {
+    rs->err = SYLV_OVERFLOWED;
+    rs->conv = 1;
+    rs->last = 0.0;
+    return;
+  }
   rs->last = (x > 0.0) ? d / x : (d > 0.0 ? 1.0 : 0.0);
   bool conv = d <= tol * x;
   if (!conv && dprev) {
@@ -319,6 +328,17 @@ __device__ __forceinline__ void refine_result_one(const RefineState* rs, sylv_re
 }
 
 __global__ void k_refine_result(const RefineState* rs, sylv_result* res, int maxit) { refine_result_one(rs, res); }
+
+// C (m x n, ldc) <- X, unless the refinement overflowed (C keeps the right-hand side).
+__global__ void k_refine_copy_out(const double* __restrict__ X, int64_t ldx, double* __restrict__ C, int64_t ldc,
+                                  int64_t m, int64_t n, const RefineState* rs) {
+  if (rs->err == SYLV_OVERFLOWED) return;
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < m * n;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t % m, c = t / m;
+    C[r + c * ldc] = X[r + c * ldx];
+  }
+}
 
 // Y (m x n, ldy) <- X.
 __global__ void k_copy(const double* __restrict__ X, int64_t ldx, double* __restrict__ Y, int64_t ldy, int64_t m,

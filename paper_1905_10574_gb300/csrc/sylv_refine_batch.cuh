@@ -214,10 +214,12 @@ __global__ void k_bref_check(const RefEq* __restrict__ eq, int count, int it, do
   }
 }
 
-// C = X and the result record of each equation (equation blockIdx.y).
+// C = X and the result record of each equation (equation blockIdx.y); an equation
+// whose refinement overflowed keeps its right-hand side in C.
 __global__ void k_bref_finish(const RefEq* __restrict__ eq, sylv_result* res) {
   const RefEq E = eq[blockIdx.y];
-  for_each_rc(
+  if (E.rs->err != SYLV_OVERFLOWED)
+    for_each_rc(
       E.m, E.n, [&](int64_t r, int64_t c) { return E.X[r + c * E.m]; },
       [&](int64_t r, int64_t c, double v) { E.C[r + c * E.ldc] = v; });
   if (blockIdx.x == 0 && threadIdx.x == 0) refine_result_one(E.rs, res + blockIdx.y);

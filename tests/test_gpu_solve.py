@@ -382,6 +382,56 @@ def test_fp32_refine_reaches_fp64_accuracy(orc, sy, m, n):
     assert orc.residual(A, B, Y, C, 0) <= RESID_TOL
 
 
+@pytest.mark.parametrize("transa", [False, True])
+def test_fp32_refine_beyond_binary64_solves_with_fp64(orc, sy, transa):
+    """A growth input whose solution needs alpha = 2^-199: FP32 + refinement returns
+    alpha = 1 and cannot hold it (its first correction is infinite).  The synchronous
+    solve sees SYLV_OVERFLOWED, finds C untouched and solves again on the robust FP64
+    path: iters = 0, alpha < 1, Y/alpha as the oracle's."""
+    A, B, C = inputs.problem(160, 96, 5, kind="growth", upper=1e3)
+    ref = orc.trsyl(A, B, C, transa=transa)
+    assert ref["log2scale"] < 0
+    Y, res = gpu_solve(sy, A, B, C, precision="fp32_refine", tile=32, transa=transa)
+    assert res.info == 0 and res.iters == 0 and res.log2scale < 0, res
+    assert np.all(np.isfinite(Y))
+    assert orc.residual(A, B, Y, C, res.log2scale, transa, False) <= RESID_TOL
+    assert rel(shifted(Y, res.log2scale, ref["log2scale"]), ref["Y"]) <= FWD_TOL
+
+
+def test_fp32_refine_beyond_binary64_async_reports_overflow(sy):
+    """The same input without synchronization (result written to device memory):
+    status SYLV_OVERFLOWED, and C still holds the right-hand side bit for bit."""
+    import ctypes
+    A, B, C = inputs.problem(160, 96, 5, kind="growth", upper=1e3)
+    Ad, Bd, Cd = dev(A), dev(B), dev(C)
+    stream = torch.cuda.current_stream()
+    o = sy.make_opts(precision="fp32_refine", tile=32, stream=stream.cuda_stream, sync=False)
+    rbuf = torch.zeros(ctypes.sizeof(sy.sylv_result), dtype=torch.uint8, device="cuda")
+    rc = sy.sylv_tri_solve_ex(160, 96, Ad.data_ptr(), Ad.stride(1), Bd.data_ptr(), Bd.stride(1), Cd.data_ptr(),
+                              Cd.stride(1), o, rbuf.data_ptr())
+    torch.cuda.synchronize()
+    assert rc == 0
+    r = sy.sylv_result.from_buffer_copy(bytes(rbuf.cpu().numpy()))
+    assert r.info == sy.SYLV_OVERFLOWED
+    assert np.array_equal(host(Cd), C)
+
+
+def test_batched_refine_beyond_binary64_reports_overflow(orc, sy):
+    """In a refined batch, the equation whose solution lies beyond the binary64 range
+    reports SYLV_OVERFLOWED and keeps its right-hand side; the others are solved."""
+    probs = [inputs.problem(60, 50, 11, kind="wellcond"), inputs.problem(160, 96, 5, kind="growth", upper=1e3),
+             inputs.problem(90, 130, 12, kind="benign")]
+    Ys, rs = sy.batch_solve([dev(p[0]) for p in probs], [dev(p[1]) for p in probs], [dev(p[2]) for p in probs],
+                            tile=32, precision="fp32_refine")
+    torch.cuda.synchronize()
+    assert rs[1].info == sy.SYLV_OVERFLOWED
+    assert np.array_equal(host(Ys[1]), probs[1][2])
+    for i in (0, 2):
+        A, B, C = probs[i]
+        assert rs[i].info == 0
+        assert rel(host(Ys[i]), orc.trsyl(A, B, C)["Y"]) <= REFINE_TOL
+
+
 def test_batched_uneven(orc, sy):
     shapes = inputs.batch_shapes(24, 16, 300, seed=5)
     probs = [inputs.problem(m, n, 100 + i, kind="benign") for i, (m, n) in enumerate(shapes)]

@@ -218,7 +218,10 @@ int sylv_tri_solve_batched(int32_t count, const int64_t* m, const int64_t* n,
  * scaling (the exponent is read from the device result record, so the call does not
  * wait for the host); an output entry that leaves the binary64 range on the way
  * becomes +-Inf and the status is SYLV_OVERFLOWED.  result->log2scale still
- * reports alpha_G.  Y and G are device pointers.
+ * reports alpha_G.  Y and G are device pointers.  With SYLV_FP32_REFINE the adjoint
+ * solve returns alpha_G = 1: if Gamma lies beyond the binary64 range the status is
+ * SYLV_OVERFLOWED and the three outputs are not gradients (call again with
+ * SYLV_FP64, which scales).
  */
 int sylv_tri_solve_backward(int64_t m, int64_t n, const double* A, int64_t lda, const double* B,
                             int64_t ldb, const double* Y, int64_t ldy, int64_t log2scale,
